@@ -1,0 +1,323 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each check compares the oracle with a closed form, an independent construction
+(Kronecker powers, Lucas's theorem, a library convolution), brute force on tiny
+levels, or a value printed in / worked by hand from the paper.  Together they
+are chosen so that a dropped level, a swapped axis, an off-by-one digit or a
+wrong rule bit in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.signal import convolve2d
+
+import oracle
+from conftest import read_golden
+from paper_2201_00613_gb300 import inputs as I
+
+ALL = [I.TRIANGLE, I.TRIANGLE_PAPER, I.CARPET, I.VICSEK, I.FULL2, I.SINGLE]
+
+
+def _popcount(v):
+    return bin(v).count("1")
+
+
+# --------------------------------------------------------------------------
+# Membership: closed forms and independent constructions.
+
+@pytest.mark.parametrize("r", range(0, 11))
+def test_triangle_membership_closed_form(r):
+    m = oracle.member_grid(I.TRIANGLE, r)
+    n = 2 ** r
+    y, x = np.mgrid[0:n, 0:n]
+    assert np.array_equal(m, ((x & y) == 0).astype(np.uint8))
+    assert int(m.sum()) == 3 ** r
+    rows = m.sum(axis=1)
+    for yy in range(n):
+        assert rows[yy] == 2 ** (r - _popcount(yy))
+
+
+@pytest.mark.parametrize("r", range(0, 7))
+def test_triangle_is_pascal_mod_2(r):
+    # Lucas: C(x+y, x) is odd iff x & y == 0.
+    m = oracle.member_grid(I.TRIANGLE, r)
+    n = 2 ** r
+    for y in range(n):
+        for x in range(n):
+            assert m[y, x] == (math.comb(x + y, x) % 2)
+
+
+@pytest.mark.parametrize("r", range(0, 9))
+def test_paper_orientation_triangle(r):
+    m = oracle.member_grid(I.TRIANGLE_PAPER, r)
+    n = 2 ** r
+    y, x = np.mgrid[0:n, 0:n]
+    assert np.array_equal(m, ((x & ~y) == 0).astype(np.uint8))
+
+
+def _kron_power(f, r):
+    base = np.zeros((f.s, f.s), dtype=np.uint8)
+    for tx, ty in f.offsets:
+        base[ty, tx] = 1
+    g = np.ones((1, 1), dtype=np.uint8)
+    for _ in range(r):
+        g = np.kron(g, base)
+    return g
+
+
+@pytest.mark.parametrize("f", [I.TRIANGLE, I.TRIANGLE_PAPER, I.CARPET, I.VICSEK, I.FULL2, I.SINGLE],
+                         ids=lambda f: f.name)
+@pytest.mark.parametrize("r", range(0, 6))
+def test_membership_equals_kronecker_power(f, r):
+    if f.s ** r > 729:
+        pytest.skip("box too large for this check")
+    m = oracle.member_grid(f, r)
+    assert np.array_equal(m, _kron_power(f, r))
+    assert int(m.sum()) == f.k ** r
+
+
+def test_carpet_and_vicsek_digit_rules():
+    r = 4
+    n = 3 ** r
+    mc = oracle.member_grid(I.CARPET, r)
+    mv = oracle.member_grid(I.VICSEK, r)
+    for y in range(n):
+        for x in range(n):
+            dx = [(x // 3 ** j) % 3 for j in range(r)]
+            dy = [(y // 3 ** j) % 3 for j in range(r)]
+            carpet = all(not (a == 1 and b == 1) for a, b in zip(dx, dy))
+            vicsek = all(a == 1 or b == 1 for a, b in zip(dx, dy))
+            assert mc[y, x] == carpet
+            assert mv[y, x] == vicsek
+
+
+def test_memory_table_and_mrf():
+    """Compact sizes reproduce the paper's Table 'memory' and the 315x figure."""
+    g = read_golden("memory_table_r16.txt")
+    gib = float(2 ** 30)
+    for rho, bb_gb, sq_gb, mrf in g["row"]:
+        rho = int(rho)
+        sq = oracle.state_bytes(I.TRIANGLE, 16, rho, cell_bytes=4)
+        bb = oracle.box_bytes(I.TRIANGLE, 16, cell_bytes=4)
+        assert round(bb / gib) == int(bb_gb)
+        # printed to two decimals, rounded in some rows and truncated in others
+        assert abs(sq / gib - float(sq_gb)) < 0.01
+        assert abs(bb / sq - float(mrf)) < 0.06
+    mrf20 = oracle.box_bytes(I.TRIANGLE, 20) / oracle.state_bytes(I.TRIANGLE, 20)
+    assert round(mrf20) == int(g["r20_mrf"][0][0])
+    assert round(oracle.box_bytes(I.TRIANGLE, 20, 4) / gib) == int(g["r20_bb_gb"][0][0])
+
+
+@pytest.mark.parametrize("r", range(0, 9))
+def test_compact_shape(r):
+    for f in ALL:
+        h, w = oracle.compact_shape(f, r)
+        assert h * w == f.k ** r
+        assert w == f.k ** ((r + 1) // 2)
+
+
+# --------------------------------------------------------------------------
+# lambda / nu: worked example and brute force.
+
+def test_worked_lambda_nu_r3():
+    g = read_golden("lambda_nu_worked_r3.txt")
+    off = [int(v) for v in g["offsets"][0]]
+    f = I.Fractal("t", 2, 3, tuple(zip(off[0::2], off[1::2])))
+    r = int(g["r"][0][0])
+    wx, wy = (int(v) for v in g["omega_xy"][0])
+    ex, ey = (int(v) for v in g["expanded_xy"][0])
+    h, w = oracle.compact_shape(f, r)
+    assert (h, w) == (3, 9)
+    xy = oracle.lam(f, r, [wy * w + wx])
+    assert tuple(xy[0]) == (ex, ey)
+    assert int(oracle.nu(f, r, [[ex, ey]])[0]) == wy * w + wx
+
+
+def test_compact_layout_r2():
+    g = read_golden("compact_layout_r2.txt")
+    f = I.TRIANGLE
+    xy = oracle.lam(f, 2, np.arange(9))
+    for row in range(3):
+        vals = [int(v) for v in g["row%d" % row][0]]
+        expect = list(zip(vals[0::2], vals[1::2]))
+        assert [tuple(p) for p in xy[3 * row: 3 * row + 3]] == expect
+
+
+@pytest.mark.parametrize("f", ALL, ids=lambda f: f.name)
+def test_lambda_nu_bijection_brute_force(f):
+    for r in range(0, 9):
+        if f.k ** r > 300000 or f.s ** r > 1024:
+            break
+        cells = f.k ** r
+        n = f.s ** r
+        xy = oracle.lam(f, r, np.arange(cells))
+        m = oracle.member_grid(f, r)
+        # lambda lands on fractal cells, injectively, and covers the fractal.
+        assert np.all(m[xy[:, 1], xy[:, 0]] == 1)
+        flat = xy[:, 1] * n + xy[:, 0]
+        assert np.unique(flat).size == cells
+        assert int(m.sum()) == cells
+        # nu(lambda(w)) = w
+        assert np.array_equal(oracle.nu(f, r, xy), np.arange(cells, dtype=np.uint64))
+        # lambda(nu(p)) = p on the fractal; nu(hole) = sentinel.
+        yy, xx = np.mgrid[0:n, 0:n]
+        pts = np.stack([xx.ravel(), yy.ravel()], axis=1)
+        om = oracle.nu(f, r, pts)
+        hole = m.ravel() == 0
+        assert np.all(om[hole] == np.uint64(2 ** 64 - 1))
+        back = oracle.lam(f, r, om[~hole])
+        assert np.array_equal(back, pts[~hole])
+
+
+def test_nu_outside_box_and_lambda_out_of_range():
+    f = I.TRIANGLE
+    r = 5
+    n = 32
+    pts = [[-1, 0], [0, -1], [n, 0], [0, n], [-1, -1], [n, n]]
+    assert np.all(oracle.nu(f, r, pts) == np.uint64(2 ** 64 - 1))
+    xy = oracle.lam(f, r, [3 ** r, 3 ** r + 7])
+    assert np.all(xy == -1)
+
+
+def test_replica_order_invariance():
+    """Permuting the replica ids changes the compact order, not the fractal."""
+    rng = np.random.default_rng(0)
+    f = I.CARPET
+    perm = rng.permutation(f.k)
+    g = I.Fractal("carpet_perm", f.s, f.k, tuple(f.offsets[i] for i in perm))
+    r = 3
+    c = I.bernoulli_bytes(7, f.k ** r)
+    box_f = oracle.compact_to_box(f, r, c)
+    m = oracle.member_grid(f, r)
+    assert np.array_equal(m, oracle.member_grid(g, r))
+    out_f = oracle.box_run(m, box_f, 5)
+    c_g = oracle.box_to_compact(g, r, box_f)
+    out_g = oracle.run_compact(g, r, c_g, 5)
+    assert np.array_equal(oracle.box_to_compact(g, r, out_f), out_g)
+
+
+# --------------------------------------------------------------------------
+# The automaton: textbook Life, hand-worked steps, degenerate cases.
+
+def _textbook_life(grid, steps):
+    k = np.ones((3, 3), dtype=np.int32)
+    k[1, 1] = 0
+    g = grid.astype(np.int32)
+    for _ in range(steps):
+        c = convolve2d(g, k, mode="same", boundary="fill", fillvalue=0)
+        g = ((c == 3) | ((g == 1) & (c == 2))).astype(np.int32)
+    return g.astype(np.uint8)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_full_box_equals_textbook_life(steps):
+    f = I.FULL2
+    r = 5
+    m = oracle.member_grid(f, r)
+    assert m.all()
+    box = I.bernoulli_bytes(11 + steps, 32 * 32, 0.4).reshape(32, 32)
+    assert np.array_equal(oracle.box_run(m, box, steps), _textbook_life(box, steps))
+
+
+def test_full_box_patterns():
+    f = I.FULL2
+    r = 4
+    m = oracle.member_grid(f, r)
+    block = np.zeros((16, 16), np.uint8)
+    block[5:7, 5:7] = 1
+    assert np.array_equal(oracle.box_run(m, block, 3), block)
+    blinker = np.zeros((16, 16), np.uint8)
+    blinker[8, 7:10] = 1
+    one = oracle.box_run(m, blinker, 1)
+    assert one[7:10, 8].all() and one.sum() == 3
+    assert np.array_equal(oracle.box_run(m, blinker, 2), blinker)
+    glider = np.zeros((16, 16), np.uint8)
+    for yy, xx in [(1, 2), (2, 3), (3, 1), (3, 2), (3, 3)]:
+        glider[yy, xx] = 1
+    moved = np.roll(np.roll(glider, 1, axis=0), 1, axis=1)
+    assert np.array_equal(oracle.box_run(m, glider, 4), moved)
+
+
+def test_hand_worked_r2_steps():
+    g = read_golden("step_worked_r2.txt")
+    f = I.TRIANGLE
+    for case, steps in (("A", (1, 2)), ("B", (1,))):
+        c0 = np.array([int(v) for v in g[case + "_step0"][0]], np.uint8)
+        for t in steps:
+            expect = np.array([int(v) for v in g["%s_step%d" % (case, t)][0]], np.uint8)
+            assert np.array_equal(oracle.run_compact(f, 2, c0, t), expect), (case, t)
+
+
+def test_single_cell_dies():
+    f = I.SINGLE
+    for r in range(0, 4):
+        c = np.ones(1, np.uint8)
+        assert oracle.run_compact(f, r, c, 1)[0] == 0
+
+
+def test_rule_masks_are_used():
+    # With birth on 0 neighbours an isolated dead cell is born.
+    f = I.SINGLE
+    c = np.zeros(1, np.uint8)
+    assert oracle.run_compact(f, 3, c, 1, rule=(1, 0))[0] == 1
+
+
+# --------------------------------------------------------------------------
+# Initial states and the light cone.
+
+def test_splitmix64_reference_outputs():
+    g = read_golden("splitmix64_seed0.txt")
+    seed = int(g["seed"][0][0])
+    for i in range(3):
+        assert oracle.splitmix64(seed, i) == int(g["out%d" % i][0][0], 16)
+
+
+def test_bernoulli_density():
+    f = I.TRIANGLE
+    r = 10
+    for p in (0.3, 0.5):
+        c = oracle.compact_init(f, r, 1, I.p_q24(p))
+        n = c.size
+        sigma = math.sqrt(n * p * (1 - p))
+        assert abs(int(c.sum()) - n * p) < 5 * sigma
+        assert set(np.unique(c)) <= {0, 1}
+
+
+def test_bernoulli_keyed_by_expanded_position():
+    # The same expanded cell gets the same draw whatever the replica order.
+    f = I.CARPET
+    perm = tuple(f.offsets[i] for i in (3, 1, 7, 0, 2, 6, 5, 4))
+    g = I.Fractal("carpet_perm", f.s, f.k, perm)
+    assert np.array_equal(oracle.box_init(f, 3, 9, I.p_q24(0.5)),
+                          oracle.box_init(g, 3, 9, I.p_q24(0.5)))
+
+
+@pytest.mark.parametrize("f,r,T", [(I.TRIANGLE, 7, 6), (I.CARPET, 4, 5), (I.VICSEK, 4, 4)],
+                         ids=["triangle", "carpet", "vicsek"])
+def test_lightcone_matches_full_run(f, r, T):
+    seed, pq = 3, I.p_q24(0.5)
+    m = oracle.member_grid(f, r)
+    full = oracle.box_run(m, oracle.box_init(f, r, seed, pq), T)
+    om = I.random_ints(5, 200, f.k ** r)
+    om[:3] = [0, f.k ** r - 1, f.k ** (r // 2)]
+    xy = oracle.lam(f, r, om)
+    got = oracle.lightcone(f, r, seed, pq, T, xy)
+    assert np.array_equal(got, full[xy[:, 1], xy[:, 0]])
+
+
+def test_light_cone_locality_of_box_step():
+    f = I.TRIANGLE
+    r = 7
+    m = oracle.member_grid(f, r)
+    a = oracle.box_init(f, r, 4, I.p_q24(0.5))
+    ys, xs = np.nonzero(m)
+    i = len(xs) // 2
+    b = a.copy()
+    b[ys[i], xs[i]] ^= 1
+    T = 5
+    da = oracle.box_run(m, a, T)
+    db = oracle.box_run(m, b, T)
+    yy, xx = np.nonzero(da != db)
+    if yy.size:
+        assert np.max(np.maximum(np.abs(yy - ys[i]), np.abs(xx - xs[i]))) <= T
