@@ -1,0 +1,364 @@
+"""Benchmark: compact-fractal B3/S23 steps on the Sierpinski triangle, level 20.
+
+One bench step = one run of the workload: 100 synchronous B3/S23 steps over
+the 3,486,784,401-cell compact state (Bernoulli(0.5), seed 3).  Each CA step
+is one launch of the bit-sliced tile kernel.  The state (2 x 3.49 GB) is far
+larger than L2, so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): value = fractal cell-updates/s over all
+ranks; the roofline of the step kernel against the measured HBM copy
+bandwidth; the end-to-end rate through the C ABI from and to pinned host
+memory; the same-GPU bounding-box comparison at level 16; the CPU oracle on a
+bounded sample; SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl squeeze|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_00613_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = I.TRIANGLE_R20
+COMPARE = I.TRIANGLE_R16
+METRIC = "cell-updates/s"
+STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2201_00613_gb300", "csrc", "step_tiled.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+CPU_SAMPLE_LEVEL = 13   # oracle sample: the level-13 top-left sub-replica of the r = 20 box
+CPU_SAMPLE_STEPS = 200
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="squeeze", choices=["squeeze", "reference"])
+    p.add_argument("--no-compare", action="store_true", help="skip the level-16 BB comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        if d.get("source_sha") != file_sha(STEP_KERNEL_SRC):
+            return None
+        return float(d["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_baseline(seconds_hint=True):
+    """The oracle as it stands, on all host cores, on a bounded sample of the
+    workload: the level-13 top-left sub-replica of the level-20 box with the
+    same seeded start, CPU_SAMPLE_STEPS box steps."""
+    import oracle
+    f, r = WORKLOAD.fractal, CPU_SAMPLE_LEVEL
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, WORKLOAD.seed, I.p_q24(WORKLOAD.p))
+    t0 = time.perf_counter()
+    oracle.box_run(m, box, CPU_SAMPLE_STEPS)
+    dt = time.perf_counter() - t0
+    cells = f.k ** r
+    return {"value": cells * CPU_SAMPLE_STEPS / dt, "unit": METRIC, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": "bounding-box oracle, top-left level-%d sub-replica of the level-20 triangle "
+                      "(%d fractal cells, %d^2 box), same seed, %d steps, %.2f s"
+                      % (r, cells, 2 ** r, CPU_SAMPLE_STEPS, dt)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_baseline()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_baseline())
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD.name, "fractal": "sierpinski_triangle s=2 k=3",
+                       "r": WORKLOAD.r, "cells": WORKLOAD.cells, "ca_steps_per_step": 1,
+                       "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_00613_gb300 as sq
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = WORKLOAD
+    pq = I.p_q24(w.p)
+    h = sq.Handle(w.fractal, w.r)
+    cells = h.cells
+    a = torch.empty(cells, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    sq.squeeze_init_bernoulli(h.h, a, w.seed, pq)
+    stream = torch.cuda.current_stream(dev)
+    kind = sq.SQUEEZE_STEP_TILED
+    level = sq.squeeze_tiled_level(h.h)
+
+    # ---- device-resident timed region --------------------------------------
+    for _ in range(args.warmup):
+        sq.squeeze_step(h.h, a, b, w.n_steps, kind, stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            sq.squeeze_step(h.h, a, b, w.n_steps, kind, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    clocks = clk.summary()
+    status = sq.squeeze_device_status(h.h)
+    launches = args.steps * w.n_steps
+    ms_per_step = ms / args.steps
+    value = world * cells * w.n_steps * args.steps / (ms / 1e3)
+    launch_s = ms / 1e3 / launches
+    algo_bytes = 2 * cells  # own state read once + new state written once
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / launch_s / 1e9
+    traffic = traffic_per_launch()
+
+    # ---- end to end through the C ABI from pinned host memory ---------------
+    hin = torch.empty(cells, dtype=torch.uint8, pin_memory=True)
+    hout = torch.empty(cells, dtype=torch.uint8, pin_memory=True)
+    hin.copy_(a.cpu())
+    e2e_steps = max(1, min(args.steps, 3))
+    sq.squeeze_step_host(h.h, hin, hout, a, b, w.n_steps, kind, stream)  # warm
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sq.squeeze_step_host(h.h, hin, hout, a, b, w.n_steps, kind, stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * cells * w.n_steps * e2e_steps / e2e_s
+    del hin, hout
+    h.close()
+    del a, b
+    torch.cuda.empty_cache()
+
+    # ---- same-GPU bounding box at level 16 ----------------------------------
+    compare = None
+    if not args.no_compare:
+        compare = bb_compare(sq, torch, dev, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w.name, "fractal": "sierpinski_triangle s=2 k=3 offsets (0,0),(1,0),(0,1)",
+                       "r": w.r, "cells": cells, "p_alive": w.p, "seed": w.seed,
+                       "ca_steps_per_step": w.n_steps, "kernel": "step_tiled",
+                       "tile_level": level, "l2": "inputs larger than L2 (2 x 3.49 GB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
+                         "avg_launch_ms": launch_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": cells,
+                    "d2h_bytes_per_step": cells, "api": "squeeze_step_host",
+                    "ca_steps_per_step": w.n_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "device_status": status,
+            "bb_compare": compare,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bb_compare(sq, torch, dev, stream, steps=20):
+    """Compact tiled step vs the bounding-box kernel at level 16, same GPU.
+    Compact state (86 MB) fits in L2, so L2 is flushed before every timed
+    compact step; the box (2 x 4.29 GB) does not."""
+    w = COMPARE
+    pq = I.p_q24(w.p)
+    h = sq.Handle(w.fractal, w.r)
+    a = torch.empty(h.cells, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    sq.squeeze_init_bernoulli(h.h, a, w.seed, pq)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        sq.squeeze_step(h.h, a, b, 2, sq.SQUEEZE_STEP_TILED, stream)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        sq.squeeze_step(h.h, a, b, 1, sq.SQUEEZE_STEP_TILED, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        tot += s0.elapsed_time(s1)
+        a, b = b, a
+    compact = h.cells * steps / (tot / 1e3)
+    # resident (no flush) for context
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    sq.squeeze_step(h.h, a, b, 200, sq.SQUEEZE_STEP_TILED, stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    resident = h.cells * 200 / (r0.elapsed_time(r1) / 1e3)
+    del flush
+    g0 = torch.empty(h.side * h.side, dtype=torch.uint8, device=dev)
+    g1 = torch.empty_like(g0)
+    sq.squeeze_bb_init(h.h, g0, w.seed, pq)
+    sq.squeeze_bb_step(h.h, g0, g1, 2, stream)
+    torch.cuda.synchronize()
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    sq.squeeze_bb_step(h.h, g0, g1, steps, stream)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    bb_ms = q0.elapsed_time(q1)
+    bb = h.cells * steps / (bb_ms / 1e3)
+    bb_gbs = 2 * h.side * h.side * steps / (bb_ms / 1e3) / 1e9
+    out = {"workload": w.name, "r": w.r, "steps": steps,
+           "compact_cell_updates_per_s": compact,
+           "compact_l2": "flushed before every step",
+           "compact_resident_cell_updates_per_s": resident,
+           "bb_cell_updates_per_s": bb, "bb_box_gbs": bb_gbs,
+           "speedup_compact_over_bb": compact / bb,
+           "memory_bytes": {"compact": 2 * h.cells, "bb": 2 * h.side * h.side}}
+    h.close()
+    del g0, g1, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    main()

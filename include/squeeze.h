@@ -1,0 +1,189 @@
+/*
+ * squeeze.h -- C ABI of the GB300 compact-fractal library.
+ *
+ * The library runs the neighbourhood step of Squeeze (Quezada, Navarro,
+ * Hitschfeld, Bustos, arXiv 2201.00613) on an NBB fractal that is stored only
+ * in compact form: lambda maps a compact index to expanded space (Sec. 3.3),
+ * the 8 Moore neighbours are formed there, nu maps each back to a compact
+ * index or rejects it as a hole (Sec. 3.4), and a Life-like rule writes the
+ * next state into a second compact buffer (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Return value: SQUEEZE_OK (0) or a negative SQUEEZE_ERR_* code.  Nothing
+ *     throws, exits or traps; squeeze_status_string() describes a code.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The library keeps no reference to either
+ *     after the call returns.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream).  Argument errors are reported synchronously;
+ *     errors found on the device are latched in a per-handle status word and
+ *     reported by squeeze_device_status().
+ *   - The handle owns only small per-fractal tables in device memory,
+ *     allocated by squeeze_create() and freed by squeeze_destroy().
+ *
+ * Compact layout (Sec. 3.1): level mu odd unrolls along x, even along y, so
+ * the compact rectangle has W = k^ceil(r/2) columns and H = k^floor(r/2)
+ * rows, stored row-major: omega = w_y * W + w_x.  A state buffer holds k^r
+ * bytes, one per fractal cell; a cell is alive iff its byte is nonzero, and
+ * the library writes only 0 and 1.
+ */
+#ifndef SQUEEZE_H
+#define SQUEEZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SQUEEZE_OK 0
+#define SQUEEZE_ERR_INVALID_ARG (-1)   /* bad pointer, size, descriptor or kind   */
+#define SQUEEZE_ERR_UNSUPPORTED (-2)   /* valid request this build cannot serve   */
+#define SQUEEZE_ERR_OOM (-3)           /* device or host allocation failed        */
+#define SQUEEZE_ERR_CUDA (-4)          /* a CUDA runtime call failed              */
+#define SQUEEZE_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait gave up     */
+#define SQUEEZE_ERR_DEVICE_BOUNDS (-6) /* a device-side bounds check fired        */
+
+/* ---- step kernels --------------------------------------------------------- */
+#define SQUEEZE_STEP_AUTO 0    /* tiled kernel when the level allows, else per-cell ALU */
+#define SQUEEZE_STEP_TILED 1   /* bit-sliced tile kernel (self-similar neighbour program) */
+#define SQUEEZE_MAP_ALU 2      /* one thread per cell: integer lambda + 8 nu (Sec. 3.2)  */
+#define SQUEEZE_MAP_TC_BF16 3  /* one thread per cell, map sums on tcgen05 kind::f16    */
+#define SQUEEZE_MAP_TC_I8 4    /* tcgen05 kind::i8: not available on sm_103a            */
+
+typedef struct squeeze_handle squeeze_handle;
+
+/* squeeze_create -- describe a level-r NBB fractal F_n^{k,s} (Sec. 3).
+ *   s        growth factor per level, 2 <= s <= 16.
+ *   k        replicas per level, 1 <= k <= min(s*s, 255).
+ *   offsets  host array of 2*k bytes: replica beta sits at (tau_x, tau_y) =
+ *            (offsets[2*beta], offsets[2*beta+1]), each < s, all pairs
+ *            distinct (Eq. tau; the replica order fixes the compact order).
+ *   r        level; requires s^r <= 2^30 and W, H < 2^32.
+ *   out      receives the new handle.
+ * Errors: INVALID_ARG for any violated bound; OOM / CUDA when the device
+ * tables cannot be allocated on the current device. */
+int squeeze_create(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
+                   squeeze_handle **out);
+
+/* squeeze_destroy -- free the handle's device tables.  Synchronises the
+ * device first.  NULL is accepted. */
+int squeeze_destroy(squeeze_handle *h);
+
+/* squeeze_info -- sizes of the fractal (Sec. 3, Eq. V and Sec. 3.1).
+ *   n_cells = k^r; width = W; height = H; side = n = s^r.  Any output pointer
+ *   may be NULL. */
+int squeeze_info(const squeeze_handle *h, uint64_t *n_cells, uint64_t *width,
+                 uint64_t *height, uint64_t *side);
+
+/* squeeze_set_rule -- birth/survive masks of the outer-totalistic rule:
+ * a dead cell with c alive fractal neighbours becomes alive iff bit c of
+ * `birth` is set; an alive cell stays alive iff bit c of `survive` is set.
+ * Default B3/S23: birth = 1<<3, survive = (1<<2)|(1<<3) (Sec. 4).  Masks must
+ * fit in 9 bits.  Affects steps enqueued after the call. */
+int squeeze_set_rule(squeeze_handle *h, uint32_t birth, uint32_t survive);
+
+/* squeeze_lambda -- compact -> expanded map (Sec. 3.3, Eqs. lambda, beta).
+ *   d_omega  count linear compact indices (uint64).
+ *   d_xy     receives 2*count int32: (x, y) per index; (-1, -1) for an index
+ *            >= k^r.
+ * Uses the integer ALU form. */
+int squeeze_lambda(const squeeze_handle *h, const uint64_t *d_omega, int32_t *d_xy,
+                   uint64_t count, void *stream);
+
+/* squeeze_nu -- expanded -> compact map with hole rejection (Sec. 3.4,
+ * Eqs. theta, t, f, nux, nuy; theta read as the base-s digit mu-1 and odd
+ * levels accumulated on x, which makes nu the inverse of lambda).
+ *   d_xy     2*count int32 points (x, y); any value is allowed.
+ *   d_omega  receives count uint64: the compact index, or UINT64_MAX for a
+ *            hole or a point outside [0, s^r)^2. */
+int squeeze_nu(const squeeze_handle *h, const int32_t *d_xy, uint64_t *d_omega,
+               uint64_t count, void *stream);
+
+/* squeeze_map_tc -- the same two maps with their digit-times-weight sums run
+ * as tcgen05 matrix multiplies (Sec. 3.6): kind = SQUEEZE_MAP_TC_BF16 (bf16
+ * operands, fp32 accumulate, exact by construction; see the design notes for
+ * the bound) or SQUEEZE_MAP_TC_I8 (UNSUPPORTED on sm_103a).
+ *   direction 0: lambda (d_in = uint64 omega, d_out = int32 xy pairs);
+ *   direction 1: nu (d_in = int32 xy pairs, d_out = uint64 omega).
+ * Same outputs as squeeze_lambda / squeeze_nu. */
+int squeeze_map_tc(const squeeze_handle *h, int direction, const void *d_in, void *d_out,
+                   uint64_t count, int kind, void *stream);
+
+/* squeeze_init_bernoulli -- seeded Bernoulli initial state in compact order.
+ * Cell omega with expanded position (x, y) = lambda(omega) is alive iff
+ * (SplitMix64 output number (y*2^32 + x) of the stream seeded with `seed`)
+ * >> 40 is below p_q24 (= floor(p * 2^24)); SplitMix64 as published by
+ * Steele, Lea and Flood (OOPSLA 2014).  Keying by expanded position makes the
+ * state independent of the replica order.
+ *   d_state  k^r bytes, written with 0/1. */
+int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t seed,
+                           uint32_t p_q24, void *stream);
+
+/* squeeze_step -- n_steps synchronous rule steps on the compact state
+ * (Sec. 3.2 neighbourhood exploration, Sec. 4 automaton): holes and points
+ * outside the box are dead neighbours; no wrap.
+ *   d_buf0   k^r bytes, the current state (read on even steps).
+ *   d_buf1   k^r bytes, scratch for the other parity.
+ *   The result is in d_buf0 when n_steps is even and in d_buf1 when odd.
+ *   kind     SQUEEZE_STEP_* / SQUEEZE_MAP_*.  TC_I8 -> UNSUPPORTED.
+ * The two buffers must not overlap.  n_steps = 0 enqueues nothing. */
+int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
+                 int kind, void *stream);
+
+/* squeeze_step_host -- the same run from and to HOST memory: copies h_in
+ * (k^r bytes, ideally pinned) into d_buf0, runs n_steps, copies the result to
+ * h_out (k^r bytes), all on `stream`, then synchronises the stream.
+ * d_buf0 / d_buf1 are caller-owned device work buffers of k^r bytes. */
+int squeeze_step_host(squeeze_handle *h, const uint8_t *h_in, uint8_t *h_out,
+                      uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps, int kind,
+                      void *stream);
+
+/* squeeze_tiled_level -- the tile level L the tiled kernel uses for this
+ * handle (a tile is one level-L sub-replica, k^L cells), or a negative code
+ * when the tiled kernel is not available (then AUTO runs the per-cell ALU
+ * kernel).  squeeze_set_tiled_level() overrides the choice (0 < L <= r). */
+int squeeze_tiled_level(const squeeze_handle *h);
+int squeeze_set_tiled_level(squeeze_handle *h, uint32_t level);
+
+/* ---- expanded bounding-box comparator (Sec. 4, approach "BB") ------------
+ * The same automaton on the n x n expanded grid, one byte per cell:
+ * bit 0 = alive, bit 1 = fractal cell; holes are 0 and stay 0.  Grids hold
+ * n*n bytes, row-major (y * n + x). */
+
+/* squeeze_bb_init -- Bernoulli start on the box, identical cell by cell to
+ * squeeze_init_bernoulli (same seed / p_q24 give the same alive cells). */
+int squeeze_bb_init(const squeeze_handle *h, uint8_t *d_grid, uint64_t seed, uint32_t p_q24,
+                    void *stream);
+
+/* squeeze_bb_step -- n_steps steps on the box; result in d_grid0 when n_steps
+ * is even, d_grid1 when odd. */
+int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
+                    uint64_t n_steps, void *stream);
+
+/* squeeze_bb_to_compact -- gather the alive bits of the box into compact order
+ * (d_state, k^r bytes of 0/1), for comparing the two representations. */
+int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_t *d_state,
+                          void *stream);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+/* squeeze_device_status -- synchronise the device, then read and clear the
+ * handle's device status word: *status = SQUEEZE_OK, DEVICE_BOUNDS or
+ * DEVICE_TIMEOUT.  Returns CUDA if the synchronisation itself failed. */
+int squeeze_device_status(squeeze_handle *h, int *status);
+
+/* squeeze_status_string -- static text for a status code. */
+const char *squeeze_status_string(int status);
+
+/* squeeze_last_cuda_error -- text of the last CUDA error this thread saw in
+ * the library ("" when none). */
+const char *squeeze_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQUEEZE_H */

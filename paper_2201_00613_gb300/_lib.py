@@ -1,0 +1,254 @@
+"""ctypes binding of libsqueeze.so (include/squeeze.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as raw device/host pointers,
+streams as ``cudaStream_t`` values.  Every computation runs in the library's
+CUDA kernels; there is no Python or CPU fallback.  If the shared library is
+missing and cannot be built, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+SQUEEZE_OK = 0
+SQUEEZE_ERR_INVALID_ARG = -1
+SQUEEZE_ERR_UNSUPPORTED = -2
+SQUEEZE_ERR_OOM = -3
+SQUEEZE_ERR_CUDA = -4
+SQUEEZE_ERR_DEVICE_TIMEOUT = -5
+SQUEEZE_ERR_DEVICE_BOUNDS = -6
+
+SQUEEZE_STEP_AUTO = 0
+SQUEEZE_STEP_TILED = 1
+SQUEEZE_MAP_ALU = 2
+SQUEEZE_MAP_TC_BF16 = 3
+SQUEEZE_MAP_TC_I8 = 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SqueezeError(RuntimeError):
+    """A non-zero status returned by the library."""
+
+    def __init__(self, code: int, where: str):
+        self.code = code
+        lib = _load()
+        msg = lib.squeeze_status_string(code).decode()
+        cuda = lib.squeeze_last_cuda_error().decode()
+        super().__init__("%s: %s (%d)%s" % (where, msg, code, (" [" + cuda + "]") if cuda else ""))
+
+
+_SIGS = {
+    "squeeze_create": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
+                        ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "squeeze_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "squeeze_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_uint64)] * 4, ctypes.c_int),
+    "squeeze_set_rule": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_lambda": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                        ctypes.c_void_p], ctypes.c_int),
+    "squeeze_nu": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                    ctypes.c_void_p], ctypes.c_int),
+    "squeeze_map_tc": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_init_bernoulli": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                      ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_step_host": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p],
+                          ctypes.c_int),
+    "squeeze_tiled_level": ([ctypes.c_void_p], ctypes.c_int),
+    "squeeze_set_tiled_level": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_bb_init": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                         ctypes.c_void_p], ctypes.c_int),
+    "squeeze_bb_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                         ctypes.c_void_p], ctypes.c_int),
+    "squeeze_bb_to_compact": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p], ctypes.c_int),
+    "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "squeeze_last_cuda_error": ([], ctypes.c_char_p),
+}
+
+
+def exported_names() -> list:
+    """Names of every entry point the binding expects the library to export."""
+    return list(_SIGS)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if _build.stale() else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libsqueeze.so is missing and could not be built")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def lib():
+    """The loaded ctypes library."""
+    return _load()
+
+
+def _check(code: int, where: str):
+    if code != SQUEEZE_OK:
+        raise SqueezeError(code, where)
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor, a numpy array or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take a pointer of %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- entry points (same names and argument order as the C ABI) ----------------
+
+def squeeze_create(s: int, k: int, offsets, r: int):
+    """Create a handle for the level-r NBB fractal; offsets = k (tau_x, tau_y) pairs."""
+    flat = bytes(int(v) for pair in offsets for v in pair)
+    if len(flat) != 2 * k:
+        raise ValueError("need k offset pairs")
+    buf = ctypes.create_string_buffer(flat, len(flat))
+    out = ctypes.c_void_p()
+    _check(_load().squeeze_create(s, k, buf, r, ctypes.byref(out)), "squeeze_create")
+    return out.value
+
+
+def squeeze_destroy(h):
+    _check(_load().squeeze_destroy(h), "squeeze_destroy")
+
+
+def squeeze_info(h):
+    """(n_cells, width W, height H, side n)."""
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(_load().squeeze_info(h, *[ctypes.byref(x) for x in v]), "squeeze_info")
+    return tuple(int(x.value) for x in v)
+
+
+def squeeze_set_rule(h, birth: int, survive: int):
+    _check(_load().squeeze_set_rule(h, birth, survive), "squeeze_set_rule")
+
+
+def squeeze_lambda(h, d_omega, d_xy, count: int, stream=None):
+    _check(_load().squeeze_lambda(h, _ptr(d_omega), _ptr(d_xy), count, _stream(stream)),
+           "squeeze_lambda")
+
+
+def squeeze_nu(h, d_xy, d_omega, count: int, stream=None):
+    _check(_load().squeeze_nu(h, _ptr(d_xy), _ptr(d_omega), count, _stream(stream)), "squeeze_nu")
+
+
+def squeeze_map_tc(h, direction: int, d_in, d_out, count: int, kind: int, stream=None):
+    _check(_load().squeeze_map_tc(h, direction, _ptr(d_in), _ptr(d_out), count, kind,
+                                  _stream(stream)), "squeeze_map_tc")
+
+
+def squeeze_init_bernoulli(h, d_state, seed: int, p_q24: int, stream=None):
+    _check(_load().squeeze_init_bernoulli(h, _ptr(d_state), seed, p_q24, _stream(stream)),
+           "squeeze_init_bernoulli")
+
+
+def squeeze_step(h, d_buf0, d_buf1, n_steps: int, kind: int = SQUEEZE_STEP_AUTO, stream=None):
+    _check(_load().squeeze_step(h, _ptr(d_buf0), _ptr(d_buf1), n_steps, kind, _stream(stream)),
+           "squeeze_step")
+
+
+def squeeze_step_host(h, h_in, h_out, d_buf0, d_buf1, n_steps: int,
+                      kind: int = SQUEEZE_STEP_AUTO, stream=None):
+    _check(_load().squeeze_step_host(h, _ptr(h_in), _ptr(h_out), _ptr(d_buf0), _ptr(d_buf1),
+                                     n_steps, kind, _stream(stream)), "squeeze_step_host")
+
+
+def squeeze_tiled_level(h) -> int:
+    return int(_load().squeeze_tiled_level(h))
+
+
+def squeeze_set_tiled_level(h, level: int):
+    _check(_load().squeeze_set_tiled_level(h, level), "squeeze_set_tiled_level")
+
+
+def squeeze_bb_init(h, d_grid, seed: int, p_q24: int, stream=None):
+    _check(_load().squeeze_bb_init(h, _ptr(d_grid), seed, p_q24, _stream(stream)),
+           "squeeze_bb_init")
+
+
+def squeeze_bb_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
+    _check(_load().squeeze_bb_step(h, _ptr(d_grid0), _ptr(d_grid1), n_steps, _stream(stream)),
+           "squeeze_bb_step")
+
+
+def squeeze_bb_to_compact(h, d_grid, d_state, stream=None):
+    _check(_load().squeeze_bb_to_compact(h, _ptr(d_grid), _ptr(d_state), _stream(stream)),
+           "squeeze_bb_to_compact")
+
+
+def squeeze_device_status(h) -> int:
+    v = ctypes.c_int()
+    _check(_load().squeeze_device_status(h, ctypes.byref(v)), "squeeze_device_status")
+    return int(v.value)
+
+
+def squeeze_status_string(code: int) -> str:
+    return _load().squeeze_status_string(code).decode()
+
+
+def squeeze_last_cuda_error() -> str:
+    return _load().squeeze_last_cuda_error().decode()
+
+
+class Handle:
+    """Owns one squeeze handle; closes it on ``close()`` or at context exit."""
+
+    def __init__(self, fractal, r: int):
+        self.fractal = fractal
+        self.r = r
+        self.h = squeeze_create(fractal.s, fractal.k, fractal.offsets, r)
+        self.cells, self.width, self.height, self.side = squeeze_info(self.h)
+
+    def close(self):
+        if self.h:
+            squeeze_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,199 @@
+// bb.cu -- expanded bounding-box comparator (Sec. 4, approach "BB").
+//
+// The whole n x n box is stored, one byte per cell: bit 0 = alive, bit 1 =
+// fractal cell.  Holes are marked once at initialisation (value 0) and never
+// change, so the step needs no per-cell digit test: a hole simply contributes
+// no alive neighbour and is written back as 0.  One thread handles a 16-byte
+// column chunk over a strip of rows and computes the neighbour counts of 16
+// cells at a time with byte-wise (SWAR) arithmetic.
+#include "squeeze_internal.cuh"
+
+namespace sq {
+namespace {
+
+constexpr int kBBRows = 32;     // rows per thread strip
+constexpr int kBBThreads = 256;  // 16-byte chunks per block along a row
+
+__global__ void bb_init_kernel(FracDev f, uint8_t *__restrict__ grid, uint64_t seed,
+                               uint32_t p_q24) {
+  __shared__ SmemTables t;
+  load_tables(t, f);
+  __syncthreads();
+  uint64_t total = (uint64_t)f.n * f.n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t y = (uint32_t)(i / f.n), x = (uint32_t)(i - (uint64_t)y * f.n);
+    uint32_t ux = x, uy = y;
+    bool member = true;
+    for (uint32_t mu = 1; mu <= f.r && member; ++mu) {
+      uint32_t qx = fdiv(f.divs, ux), qy = fdiv(f.divs, uy);
+      member = t.hnu[(uy - qy * f.s) * f.s + (ux - qx * f.s)] != kHole;
+      ux = qx;
+      uy = qy;
+    }
+    grid[i] = member ? (uint8_t)(2u | bernoulli_cell(seed, p_q24, x, y)) : (uint8_t)0;
+  }
+}
+
+// Generic byte-per-thread step (any n).
+__global__ void bb_step_simple(uint32_t n, Rule rule, const uint8_t *__restrict__ in,
+                               uint8_t *__restrict__ out) {
+  uint64_t total = (uint64_t)n * n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t y = (uint32_t)(i / n), x = (uint32_t)(i - (uint64_t)y * n);
+    uint8_t v = in[i];
+    if (!(v & 2)) {
+      out[i] = 0;
+      continue;
+    }
+    uint32_t c = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy) continue;
+        int64_t qx = (int64_t)x + dx, qy = (int64_t)y + dy;
+        if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
+        c += in[(uint64_t)qy * n + qx] & 1u;
+      }
+    out[i] = (uint8_t)(2u | apply_rule(rule, v & 1u, c));
+  }
+}
+
+// Byte-wise "equals c" over 4 counts in [0, 8]: 0x01 in each byte whose count is c.
+__device__ __forceinline__ uint32_t bytes_eq(uint32_t cnt, uint32_t c) {
+  uint32_t x = cnt ^ (c * 0x01010101u);  // each byte <= 0x0F
+  return (~(x + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+}
+
+__device__ __forceinline__ uint32_t swar_rule(Rule rule, uint32_t cnt, uint32_t alive) {
+  uint32_t next = 0;
+  uint32_t any = rule.birth | rule.survive;
+#pragma unroll
+  for (uint32_t c = 0; c <= 8; ++c) {
+    if (!((any >> c) & 1u)) continue;
+    uint32_t e = bytes_eq(cnt, c);
+    bool b = (rule.birth >> c) & 1u, s = (rule.survive >> c) & 1u;
+    next |= b && s ? e : (b ? (e & ~alive) : (e & alive));
+  }
+  return next;
+}
+
+struct Row16 {
+  uint32_t a[4];  // alive bits (0x01 per byte)
+  uint32_t h[4];  // horizontal 3-sums
+};
+
+__device__ __forceinline__ void make_row(const uint4 &v, uint32_t left, uint32_t right, Row16 &o) {
+  uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o.a[j] = w[j] & 0x01010101u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t lw = j ? (o.a[j - 1] >> 24) : (left & 1u);
+    uint32_t rw = j < 3 ? (o.a[j + 1] << 24) : ((right & 1u) << 24);
+    uint32_t L = (o.a[j] << 8) | lw;
+    uint32_t R = (o.a[j] >> 8) | rw;
+    o.h[j] = o.a[j] + L + R;
+  }
+}
+
+// Load one 16-byte chunk of row y (zeros off the box) and its two edge bytes.
+__device__ __forceinline__ void load_row(const uint8_t *__restrict__ in, uint32_t n, int64_t y,
+                                         uint32_t chunk, uint32_t nchunks, Row16 &o) {
+  uint4 v = make_uint4(0, 0, 0, 0);
+  bool in_box = y >= 0 && y < (int64_t)n;
+  bool live = chunk < nchunks;
+  const uint8_t *row = in + (uint64_t)(in_box ? y : 0) * n;
+  if (in_box && live) v = __ldg(reinterpret_cast<const uint4 *>(row) + chunk);
+  unsigned lane = threadIdx.x & 31u;
+  uint32_t left = __shfl_up_sync(0xFFFFFFFFu, v.w >> 24, 1);
+  uint32_t right = __shfl_down_sync(0xFFFFFFFFu, v.x, 1) & 0xFFu;
+  if (lane == 0) left = (in_box && live && chunk > 0) ? row[chunk * 16 - 1] : 0u;
+  if (lane == 31) right = (in_box && chunk + 1 < nchunks) ? row[chunk * 16 + 16] : 0u;
+  make_row(v, left, right, o);
+}
+
+// SWAR step; requires n % 16 == 0.  Block: kBBThreads consecutive chunks of a
+// row; grid.y: strips of kBBRows rows.
+__global__ void __launch_bounds__(kBBThreads) bb_step_swar(uint32_t n, Rule rule,
+                                                           const uint8_t *__restrict__ in,
+                                                           uint8_t *__restrict__ out) {
+  uint32_t nchunks = n / 16;
+  uint32_t chunk = blockIdx.x * kBBThreads + threadIdx.x;
+  int64_t y0 = (int64_t)blockIdx.y * kBBRows;
+  Row16 up, cur, dn;
+  load_row(in, n, y0 - 1, chunk, nchunks, up);
+  load_row(in, n, y0, chunk, nchunks, cur);
+  uint4 vcur = make_uint4(0, 0, 0, 0);
+  if (chunk < nchunks && y0 < n) vcur = __ldg(reinterpret_cast<const uint4 *>(in + (uint64_t)y0 * n) + chunk);
+  for (int i = 0; i < kBBRows; ++i) {
+    int64_t y = y0 + i;
+    if (y >= n) break;  // uniform across the block
+    load_row(in, n, y + 1, chunk, nchunks, dn);
+    uint4 vnext = make_uint4(0, 0, 0, 0);
+    if (chunk < nchunks && y + 1 < n)
+      vnext = __ldg(reinterpret_cast<const uint4 *>(in + (uint64_t)(y + 1) * n) + chunk);
+    if (chunk < nchunks) {
+      uint32_t w[4] = {vcur.x, vcur.y, vcur.z, vcur.w};
+      uint32_t o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t cnt = up.h[j] + dn.h[j] + cur.h[j] - cur.a[j];
+        uint32_t next = swar_rule(rule, cnt, cur.a[j]);
+        o[j] = (w[j] & 0x02020202u) | (next & (w[j] >> 1) & 0x01010101u);
+      }
+      reinterpret_cast<uint4 *>(out + (uint64_t)y * n)[chunk] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+    up = cur;
+    cur = dn;
+    vcur = vnext;
+  }
+}
+
+__global__ void bb_gather_kernel(FracDev f, const uint8_t *__restrict__ grid,
+                                 uint8_t *__restrict__ state) {
+  __shared__ SmemTables t;
+  load_tables(t, f);
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < f.cells;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t wy = (uint32_t)(i / f.W), wx = (uint32_t)(i - (uint64_t)wy * f.W);
+    uint32_t x, y;
+    lambda_alu(f, t, wx, wy, x, y);
+    state[i] = grid[(uint64_t)y * f.n + x] & 1u;
+  }
+}
+
+}  // namespace
+}  // namespace sq
+
+using namespace sq;
+
+int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uint32_t p_q24,
+                      cudaStream_t st) {
+  uint64_t total = (uint64_t)h->f.n * h->f.n;
+  bb_init_kernel<<<grid_for(total, 256), 256, 0, st>>>(h->f, grid, seed, p_q24);
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st) {
+  uint32_t n = h->f.n;
+  if (n % 16 == 0 && ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0)) {
+    uint32_t nchunks = n / 16;
+    dim3 grid((nchunks + kBBThreads - 1) / kBBThreads, (n + kBBRows - 1) / kBBRows);
+    bb_step_swar<<<grid, kBBThreads, 0, st>>>(n, h->rule, in, out);
+  } else {
+    uint64_t total = (uint64_t)n * n;
+    bb_step_simple<<<grid_for(total, 256), 256, 0, st>>>(n, h->rule, in, out);
+  }
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,
+                        cudaStream_t st) {
+  bb_gather_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, grid, state);
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}

@@ -1,0 +1,199 @@
+// squeeze_internal.cuh -- shared device-side definitions of the CUDA library.
+//
+// Everything here belongs to the GPU path: the fractal descriptor passed to
+// kernels by value, exact division by a runtime constant, the per-cell lambda
+// and nu maps (Sec. 3.3 / 3.4 of arXiv 2201.00613) and the outer-totalistic
+// rule of Sec. 4.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "squeeze.h"
+
+namespace sq {
+
+constexpr uint8_t kHole = 0xFF;   // H_nu entry of a digit pair that is not a replica
+constexpr int kMaxS = 16;          // s <= 16, so H_nu has at most 256 entries
+constexpr int kMaxK = 255;
+
+// Exact unsigned 32-bit division by a runtime divisor d >= 1 with one
+// multiply-high (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, round-up variant with the add-back step).
+struct FastDiv {
+  uint32_t d;   // divisor
+  uint32_t m;   // magic multiplier
+  uint32_t l;   // ceil(log2(d)); 0 for d == 1
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 0u, 0u};
+  if (d <= 1) return f;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.l = l;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d) + 1u;
+  return f;
+}
+
+__host__ __device__ inline uint32_t fdiv(const FastDiv &f, uint32_t n) {
+  if (f.d == 1) return n;
+#ifdef __CUDA_ARCH__
+  uint32_t t = __umulhi(f.m, n);
+#else
+  uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
+// Rule masks: a dead cell with c alive neighbours is born iff bit c of
+// `birth`; an alive one survives iff bit c of `survive`.
+struct Rule {
+  uint32_t birth;
+  uint32_t survive;
+};
+
+// Fractal descriptor handed to every kernel by value.
+struct FracDev {
+  uint32_t s, k, r;
+  uint32_t n;          // s^r, side of the bounding box (<= 2^30)
+  uint32_t W, H;       // compact columns (odd levels) and rows (even levels)
+  uint64_t cells;      // k^r
+  FastDiv divk, divs, divW;
+  uint8_t taux[256];   // H_lambda: tau(beta) = (taux[beta], tauy[beta])
+  uint8_t tauy[256];
+  uint8_t hnu[256];    // H_nu[theta_y * s + theta_x] = beta, or kHole
+};
+
+// Tables staged in shared memory by the per-cell kernels.
+struct SmemTables {
+  uint8_t taux[256];
+  uint8_t tauy[256];
+  uint8_t hnu[256];
+};
+
+__device__ inline void load_tables(SmemTables &t, const FracDev &f) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    t.taux[i] = f.taux[i];
+    t.tauy[i] = f.tauy[i];
+    t.hnu[i] = f.hnu[i];
+  }
+}
+
+// lambda (Sec. 3.3): sum over levels mu = 1..r of tau(beta_mu) * s^(mu-1),
+// beta_mu the base-k digit ceil(mu/2)-1 of w_x (odd mu) or w_y (even mu).
+__device__ inline void lambda_alu(const FracDev &f, const SmemTables &t, uint32_t wx,
+                                  uint32_t wy, uint32_t &x, uint32_t &y) {
+  uint32_t X = 0, Y = 0, scale = 1;
+  for (uint32_t mu = 1; mu <= f.r; ++mu) {
+    uint32_t src = (mu & 1u) ? wx : wy;
+    uint32_t q = fdiv(f.divk, src);
+    uint32_t beta = src - q * f.k;
+    if (mu & 1u) wx = q; else wy = q;
+    X += t.taux[beta] * scale;
+    Y += t.tauy[beta] * scale;
+    scale *= f.s;
+  }
+  x = X;
+  y = Y;
+}
+
+// nu (Sec. 3.4): per level the base-s digit pair theta_mu selects a replica id
+// through H_nu (a hole rejects the point); odd levels accumulate id *
+// k^floor((mu-1)/2) on w_x, even levels on w_y.
+__device__ inline bool nu_alu(const FracDev &f, const SmemTables &t, int32_t x, int32_t y,
+                              uint32_t &wx, uint32_t &wy) {
+  if (x < 0 || y < 0 || (uint32_t)x >= f.n || (uint32_t)y >= f.n) return false;
+  uint32_t ux = (uint32_t)x, uy = (uint32_t)y;
+  uint32_t nx = 0, ny = 0, wtx = 1, wty = 1;
+  for (uint32_t mu = 1; mu <= f.r; ++mu) {
+    uint32_t qx = fdiv(f.divs, ux), qy = fdiv(f.divs, uy);
+    uint32_t tx = ux - qx * f.s, ty = uy - qy * f.s;
+    ux = qx;
+    uy = qy;
+    uint32_t id = t.hnu[ty * f.s + tx];
+    if (id == kHole) return false;
+    if (mu & 1u) {
+      nx += id * wtx;
+      wtx *= f.k;
+    } else {
+      ny += id * wty;
+      wty *= f.k;
+    }
+  }
+  wx = nx;
+  wy = ny;
+  return true;
+}
+
+__device__ __host__ inline uint32_t apply_rule(const Rule &rule, bool alive, uint32_t c) {
+  return ((alive ? rule.survive : rule.birth) >> c) & 1u;
+}
+
+// SplitMix64 output number i of the stream seeded with `seed`
+// (Steele, Lea, Flood, OOPSLA 2014): mix(seed + (i+1) * gamma).
+__device__ __host__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __host__ inline uint8_t bernoulli_cell(uint64_t seed, uint32_t p_q24, uint32_t x,
+                                                  uint32_t y) {
+  uint64_t key = ((uint64_t)y << 32) | (uint64_t)x;
+  return (uint8_t)((splitmix64_at(seed, key) >> 40) < (uint64_t)p_q24);
+}
+
+inline unsigned grid_for(uint64_t items, unsigned block, unsigned cap = 152u * 16u) {
+  uint64_t g = (items + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace sq
+
+// ---- host-side internals shared between translation units ------------------
+
+struct TiledProgram;  // defined in step_tiled.cu
+
+struct squeeze_handle {
+  sq::FracDev f;
+  sq::Rule rule;
+  int *d_status;             // device status word (SQUEEZE_OK / DEVICE_*)
+  int device;                // CUDA device the tables live on
+  uint32_t tiled_level;      // 0 = not chosen yet
+  TiledProgram *tiled;       // lazily built neighbour program of the tiled kernel
+};
+
+// Error plumbing (handle.cu).
+int sq_cuda_fail(cudaError_t e);
+#define SQ_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return sq_cuda_fail(e_);   \
+  } while (0)
+
+// Launchers implemented in the kernel translation units.
+int sq_launch_lambda(const squeeze_handle *h, const uint64_t *omega, int32_t *xy,
+                     uint64_t count, cudaStream_t st);
+int sq_launch_nu(const squeeze_handle *h, const int32_t *xy, uint64_t *omega, uint64_t count,
+                 cudaStream_t st);
+int sq_launch_init(const squeeze_handle *h, uint8_t *state, uint64_t seed, uint32_t p_q24,
+                   cudaStream_t st);
+int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
+                       cudaStream_t st);
+int sq_tiled_prepare(squeeze_handle *h);
+int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
+                         cudaStream_t st);
+void sq_tiled_free(TiledProgram *p);
+int sq_tiled_default_level(const squeeze_handle *h);
+int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
+int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,
+                     uint64_t count, cudaStream_t st);
+int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uint32_t p_q24,
+                      cudaStream_t st);
+int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
+int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,
+                        cudaStream_t st);

@@ -1,0 +1,41 @@
+"""Run the compact step on one level for profiler captures.
+
+  python -m paper_2201_00613_gb300.profile_step --level 18 --steps 3 [--kind tiled|alu|tc]
+
+Initialises the seeded Bernoulli(0.5) triangle state at the given level and
+runs `steps` steps, one kernel launch per step.  Used with ncu on a case that
+is larger than L2 but small enough for a multi-pass capture.
+"""
+import argparse
+import sys
+
+import torch
+
+from . import _lib as sq
+from . import inputs as I
+
+KINDS = {"tiled": sq.SQUEEZE_STEP_TILED, "alu": sq.SQUEEZE_MAP_ALU, "tc": sq.SQUEEZE_MAP_TC_BF16}
+FRACTALS = {"triangle": I.TRIANGLE, "carpet": I.CARPET, "vicsek": I.VICSEK}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--level", type=int, default=18)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--kind", default="tiled", choices=sorted(KINDS))
+    p.add_argument("--fractal", default="triangle", choices=sorted(FRACTALS))
+    a = p.parse_args(argv)
+    f = FRACTALS[a.fractal]
+    with sq.Handle(f, a.level) as h:
+        s0 = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+        s1 = torch.empty_like(s0)
+        sq.squeeze_init_bernoulli(h.h, s0, 3, I.p_q24(0.5))
+        sq.squeeze_step(h.h, s0, s1, a.steps, KINDS[a.kind])
+        torch.cuda.synchronize()
+        st = sq.squeeze_device_status(h.h)
+        print("level %d cells %d steps %d kind %s status %d" % (a.level, h.cells, a.steps, a.kind, st))
+        return 0 if st == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())
