@@ -30,6 +30,8 @@
  *       neighbours only; cells outside the box and holes are dead; no wrap;
  *       synchronous update into a second buffer.  Other birth/survive masks
  *       are accepted as 9-bit masks over the neighbour count.
+ *   R10 (silent): one byte per cell; a cell is alive iff bit 0 of its byte
+ *       is set.  States written here are 0 or 1.
  *   R7 (initial states): cell (x, y) is alive iff the top 24 bits of output
  *       number (y * 2^32 + x) of a SplitMix64 stream seeded with `seed` are
  *       below p_q24 (SplitMix64: Steele, Lea, Flood, OOPSLA 2014).
@@ -193,8 +195,8 @@ void orc_box_to_compact(uint32_t s, uint32_t k, const uint8_t *tau, uint32_t r,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Bounding-box cellular-automaton step (Sec. 4; reading R6).  `member` marks
- * the fractal cells of the n x n box.  For a fractal cell p with c alive
+/* Bounding-box cellular-automaton step (Sec. 4; readings R6, R10).  `member`
+ * marks the fractal cells of the n x n box.  For a fractal cell p with c alive
  * fractal Moore neighbours: next = alive ? bit c of survive : bit c of birth.
  * Non-fractal cells are written 0.                                          */
 void orc_box_step(int64_t n, const uint8_t *member, const uint8_t *in, uint8_t *out,
@@ -211,9 +213,9 @@ void orc_box_step(int64_t n, const uint8_t *member, const uint8_t *in, uint8_t *
                     int64_t qx = x + dx, qy = y + dy;
                     if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
                     int64_t q = qy * n + qx;
-                    if (member[q] && in[q]) ++c;
+                    if (member[q] && (in[q] & 1u)) ++c;
                 }
-            uint32_t mask = in[p] ? survive : birth;
+            uint32_t mask = (in[p] & 1u) ? survive : birth;
             out[p] = (uint8_t)((mask >> c) & 1u);
         }
 }

@@ -321,3 +321,11 @@ def test_light_cone_locality_of_box_step():
     yy, xx = np.nonzero(da != db)
     if yy.size:
         assert np.max(np.maximum(np.abs(yy - ys[i]), np.abs(xx - xs[i]))) <= T
+
+
+def test_state_is_bit_zero_of_each_byte():
+    """Reading R10: only bit 0 of a cell's byte is its state."""
+    f, r = I.TRIANGLE, 6
+    rng = np.random.default_rng(3)
+    raw = rng.integers(0, 256, f.k ** r).astype(np.uint8)
+    assert np.array_equal(oracle.run_compact(f, r, raw, 3), oracle.run_compact(f, r, raw & 1, 3))
