@@ -24,8 +24,8 @@
  * Compact layout (Sec. 3.1): level mu odd unrolls along x, even along y, so
  * the compact rectangle has W = k^ceil(r/2) columns and H = k^floor(r/2)
  * rows, stored row-major: omega = w_y * W + w_x.  A state buffer holds k^r
- * bytes, one per fractal cell; a cell is alive iff its byte is nonzero, and
- * the library writes only 0 and 1.
+ * bytes, one per fractal cell; a cell is alive iff bit 0 of its byte is set
+ * (the other bits are ignored), and the library writes only 0 and 1.
  */
 #ifndef SQUEEZE_H
 #define SQUEEZE_H
@@ -142,9 +142,12 @@ int squeeze_step_host(squeeze_handle *h, const uint8_t *h_in, uint8_t *h_out,
                       void *stream);
 
 /* squeeze_tiled_level -- the tile level L the tiled kernel uses for this
- * handle (a tile is one level-L sub-replica, k^L cells), or a negative code
- * when the tiled kernel is not available (then AUTO runs the per-cell ALU
- * kernel).  squeeze_set_tiled_level() overrides the choice (0 < L <= r). */
+ * handle (a tile is one level-L sub-replica, k^L cells, stored as a
+ * k^ceil(L/2) x k^floor(L/2) compact rectangle), or a negative code when the
+ * tiled kernel is not available (then AUTO runs the per-cell ALU kernel).
+ * squeeze_set_tiled_level() overrides the choice: 0 < L <= r, else
+ * INVALID_ARG; a tile row wider than 32 cells (k^ceil(L/2) > 32) gives
+ * UNSUPPORTED. */
 int squeeze_tiled_level(const squeeze_handle *h);
 int squeeze_set_tiled_level(squeeze_handle *h, uint32_t level);
 

@@ -171,6 +171,7 @@ int squeeze_tiled_level(const squeeze_handle *h) {
 
 int squeeze_set_tiled_level(squeeze_handle *h, uint32_t level) {
   if (check_handle(h) || level == 0 || level > h->f.r) return SQUEEZE_ERR_INVALID_ARG;
+  if (!sq_tiled_level_fits(h, level)) return SQUEEZE_ERR_UNSUPPORTED;
   if (h->tiled && h->tiled_level != level) {
     cudaError_t e = cudaDeviceSynchronize();
     sq_tiled_free(h->tiled);

@@ -84,9 +84,9 @@ __global__ void step_alu_kernel(FracDev f, Rule rule, const uint8_t *__restrict_
       if (d == 4) continue;
       int32_t qx = (int32_t)x + d % 3 - 1, qy = (int32_t)y + d / 3 - 1;
       uint32_t nx, ny;
-      if (nu_alu(f, t, qx, qy, nx, ny)) c += in[(uint64_t)ny * f.W + nx] != 0;
+      if (nu_alu(f, t, qx, qy, nx, ny)) c += in[(uint64_t)ny * f.W + nx] & 1u;
     }
-    out[i] = (uint8_t)apply_rule(rule, in[i] != 0, c);
+    out[i] = (uint8_t)apply_rule(rule, in[i] & 1u, c);
   }
 }
 

@@ -189,6 +189,7 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
                          cudaStream_t st);
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
+bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,
                      uint64_t count, cudaStream_t st);

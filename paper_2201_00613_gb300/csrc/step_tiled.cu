@@ -14,11 +14,18 @@
 // a carry.
 //
 // A CTA owns a group of up to 32 tiles lying side by side in compact x.  It
-// stages their bytes in shared memory, transposes them so that bit i of word
-// c is the state of local cell c in tile i, runs the rule on whole words with
-// a bit-sliced adder (32 cells per bitwise operation), transposes back and
-// writes the group's bytes.  Reads and writes of the compact buffers are
-// coalesced 16-byte accesses; only halo bytes are single-byte loads.
+// stages their bytes in shared memory; each lane packs one tile row (<= 32
+// cells) into a 32-bit word and a 5-stage shuffle butterfly transposes the
+// warp's 32 words, so that bit i of a word is the state of one local cell in
+// tile i.  The rule then runs on whole words with a bit-sliced adder (32
+// cells per bitwise operation); the inverse transpose and an unaligned,
+// merged write-back return the bytes to the staging rows.  Reads and writes
+// of the compact buffers are coalesced 16-byte accesses; only halo bytes are
+// single-byte loads.
+//
+// Bit order of a packed row word: bit 8b + j holds tile-row byte 4j + b (the
+// order the pack produces for free); the neighbour program is built in that
+// order, with slot p = 32 * ly + (8 * (lx & 3) + (lx >> 2)).
 #include <stdlib.h>
 #include <string.h>
 
@@ -28,13 +35,15 @@
 
 struct TiledProgram {
   uint32_t L, TW, TH, cells, nhalo;
+  uint32_t slots;           // TH * 32 padded word slots
   uint32_t dir_mask;        // bit d set when some halo slot uses direction d
   uint32_t tiles_x, tiles_y, groups_per_band;
   uint64_t groups;
   uint32_t pitch;           // bytes per staging row
   size_t smem;
   int grid;
-  uint16_t *d_refs;         // cells x 8 local references
+  int threads;              // CTA size: whole warps, chosen to balance the TH rows
+  uint16_t *d_refs;         // 8 x slots byte offsets of the neighbour words
   uint64_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
   uint8_t *d_halo_dir;      // nhalo directions, (dy + 1) * 3 + (dx + 1)
 };
@@ -42,14 +51,15 @@ struct TiledProgram {
 namespace sq {
 namespace {
 
-constexpr int kTiledThreads = 256;
-constexpr int kTiledWarps = kTiledThreads / 32;
-constexpr size_t kTiledSmemCap = 48 * 1024;
+constexpr int kTiledMaxThreads = 384;
+constexpr size_t kTiledSmemCap = 52 * 1024;
 
 struct TiledDev {
   FracDev f;
   Rule rule;
-  uint32_t L, TW, TH, cells, nhalo, dir_mask;
+  uint32_t L, TW, TH, cells, nhalo, dir_mask, slots;
+  uint32_t valid;       // packed-word bits that hold a real cell (lx < TW)
+  uint32_t nwin;        // aligned 32-bit words covering one tile row
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
   FastDiv div_tw, div_gpb;
@@ -66,6 +76,9 @@ __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
 }
 
 // Outer-totalistic rule on 32 cells at once: n[0..7] are the neighbour bits.
+// kLife: the rule is B3/S23, evaluated as "count in {2,3} and (count odd or
+// alive)"; otherwise the birth/survive masks are evaluated count by count.
+template <bool kLife>
 __device__ __forceinline__ uint32_t rule_word(const Rule &rule, uint32_t self, const uint32_t *n) {
   uint32_t s0 = n[0] ^ n[1] ^ n[2], c0 = maj3(n[0], n[1], n[2]);
   uint32_t s1 = n[3] ^ n[4] ^ n[5], c1 = maj3(n[3], n[4], n[5]);
@@ -74,6 +87,7 @@ __device__ __forceinline__ uint32_t rule_word(const Rule &rule, uint32_t self, c
   uint32_t t = c0 ^ c1 ^ c2, u = maj3(c0, c1, c2);
   uint32_t b1 = t ^ c3, v = t & c3;
   uint32_t b2 = u ^ v, b3 = u & v;
+  if (kLife) return b1 & ~b2 & ~b3 & (b0 | self);
   uint32_t next = 0, any = rule.birth | rule.survive;
 #pragma unroll
   for (uint32_t c = 0; c <= 8; ++c) {
@@ -123,139 +137,211 @@ __device__ bool adjacent_tile(const TiledDev &p, const uint8_t *taux, const uint
   return true;
 }
 
-__global__ void __launch_bounds__(kTiledThreads) step_tiled_kernel(TiledDev p,
-                                                                   const uint8_t *__restrict__ in,
-                                                                   uint8_t *__restrict__ out) {
+// 32x32 bit transpose across a warp: on return lane j holds the word whose
+// bit i was bit j of lane i's input.  Five butterfly stages; keep[] / rot[]
+// are the per-lane masks and rotations of each stage (see make_transpose).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, const uint32_t *keep,
+                                                const uint32_t *rot) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> s);
+    uint32_t t = __funnelshift_l(y, y, rot[s]);
+    x = (x & keep[s]) | (t & ~keep[s]);
+  }
+  return x;
+}
+
+__device__ __forceinline__ void make_transpose(unsigned lane, uint32_t *keep, uint32_t *rot) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    uint32_t j = 16u >> s;
+    bool upper = lane & j;
+    keep[s] = upper ? ~m[s] : m[s];
+    rot[s] = upper ? 32u - j : j;
+  }
+}
+
+// The kernel is instantiated for the common tile-row widths so that the word
+// counts of a row are compile-time constants; kTW = 0 takes TW at run time.
+template <bool kLife, int kTW>
+__global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
+    TiledDev p, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const uint32_t cells = p.cells, nhalo = p.nhalo;
-  // Shared-memory carve-up (all offsets multiples of 16 bytes).
-  uint16_t *refs = reinterpret_cast<uint16_t *>(smem);                       // cells * 8
-  size_t off = ((size_t)cells * 16 + 15) & ~(size_t)15;
-  uint32_t *win = reinterpret_cast<uint32_t *>(smem + off);                  // cells + nhalo + 1
-  off += (((size_t)cells + nhalo + 1) * 4 + 15) & ~(size_t)15;
-  uint32_t *wout = reinterpret_cast<uint32_t *>(smem + off);                 // cells
-  off += ((size_t)cells * 4 + 15) & ~(size_t)15;
+  const uint32_t slots = p.slots, nhalo = p.nhalo;
+  const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
+  const uint32_t nwin = kTW ? (3u + (uint32_t)kTW + 3u) / 4u : p.nwin;
+  // Shared-memory carve-up; `win` sits at offset 0 so that the neighbour
+  // references can be stored as byte offsets.
+  uint32_t *win = reinterpret_cast<uint32_t *>(smem);                        // slots + nhalo + 1
+  size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
+  uint32_t *wout = reinterpret_cast<uint32_t *>(smem + off);                 // slots
+  off += (size_t)slots * 4;
+  uint16_t *refs = reinterpret_cast<uint16_t *>(smem + off);                 // 8 * slots, d-major
+  off += (size_t)slots * 16;
   uint64_t *adj = reinterpret_cast<uint64_t *>(smem + off);                  // 9 * 32
   off += 9 * 32 * 8;
-  uint32_t *row_a = reinterpret_cast<uint32_t *>(smem + off);                // TH
-  off += ((size_t)p.TH * 4 + 15) & ~(size_t)15;
+  uint64_t *rowS = reinterpret_cast<uint64_t *>(smem + off);                 // TH
+  off += ((size_t)p.TH * 8 + 15) & ~(size_t)15;
   uint8_t *tab = smem + off;                                                 // 3 * 256
   off += 3 * 256;
-  uint8_t *stage = smem + off;                                               // TH * pitch
+  uint8_t *stage = smem + off;                                               // TH * pitch + 64
+  const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
+  uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
 
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  for (uint32_t i = tid; i < cells * 8; i += blockDim.x) refs[i] = p.refs[i];
-  for (uint32_t i = tid; i < 256; i += blockDim.x) {
+  const unsigned nthreads = blockDim.x, nw = nthreads >> 5;
+  uint32_t keep[5], rot[5];
+  make_transpose(lane, keep, rot);
+  for (uint32_t i = tid; i < slots * 8; i += nthreads) refs[i] = p.refs[i];
+  for (uint32_t i = tid; i < 256; i += nthreads) {
     tab[i] = p.f.taux[i];
     tab[256 + i] = p.f.tauy[i];
     tab[512 + i] = p.f.hnu[i];
   }
-  if (tid == 0) win[cells + nhalo] = 0u;  // the "no neighbour" word
+  if (tid == 0) win[slots + nhalo] = 0u;  // the "no neighbour" word
   const uint64_t total = p.f.cells, W = p.f.W;
+  const uint32_t valid = p.valid;
 
   for (uint64_t g = blockIdx.x; g < p.groups; g += gridDim.x) {
     const uint32_t ty = fdiv(p.div_gpb, (uint32_t)g);  // groups < 2^32 checked on the host
     const uint32_t tx0 = ((uint32_t)g - ty * p.groups_per_band) * 32u;
     const uint32_t ntiles = min(32u, p.tiles_x - tx0);
-    const uint32_t seg = ntiles * p.TW;  // bytes of this group in one compact row
+    const uint32_t seg = ntiles * TW;  // bytes of this group in one compact row
+    const uint64_t row0 = (uint64_t)ty * p.TH * W + (uint64_t)tx0 * TW;
 
-    // Phase 1: stage the group's rows (16-byte aligned chunks) with cp.async;
-    // warp 0 also resolves each tile's adjacent blocks.
-    for (uint32_t ly = tid; ly < p.TH; ly += blockDim.x) {
-      uint64_t S = ((uint64_t)ty * p.TH + ly) * W + (uint64_t)tx0 * p.TW;
-      row_a[ly] = (uint32_t)(S & 15u);
-    }
-    __syncthreads();
-    const uint32_t nchunk = (15u + seg + 15u) / 16u;
-    for (uint32_t i = tid; i < p.TH * nchunk; i += blockDim.x) {
-      uint32_t ly = i / nchunk, c = i - ly * nchunk;
-      uint64_t S = ((uint64_t)ty * p.TH + ly) * W + (uint64_t)tx0 * p.TW;
-      uint64_t A = (S & ~(uint64_t)15) + 16ull * c;
-      if (A >= S + seg) continue;
-      uint8_t *dst = stage + (size_t)ly * p.pitch + 16u * c;
-      if (A + 16 <= total) {
-        uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(in + A));
-      } else {
-        for (uint32_t b = 0; b < 16; ++b) dst[b] = A + b < total ? in[A + b] : 0;
-      }
-    }
-    if (warp == 0) {
-      uint32_t tx = tx0 + lane;
-#pragma unroll 1
-      for (int d = 0; d < 9; ++d) {
-        uint64_t base = ~0ull;
-        if (((p.dir_mask >> d) & 1u) && lane < ntiles) {
-          uint32_t ntx, nty;
-          if (adjacent_tile(p, tab, tab + 256, tab + 512, tx, ty, d % 3 - 1, d / 3 - 1, ntx, nty))
-            base = (uint64_t)nty * p.TH * W + (uint64_t)ntx * p.TW;
+    // Phase 1: stage the group's rows (16-byte aligned chunks) with cp.async,
+    // one warp per row; meanwhile the warps resolve the tiles' adjacent
+    // blocks, one direction each.
+    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+      const uint64_t S = row0 + (uint64_t)ly * W, A0 = S & ~(uint64_t)15;
+      const uint32_t nch = (uint32_t)((S - A0 + seg + 15) >> 4);
+      if (lane == 0) rowS[ly] = S;
+      uint8_t *dst_row = stage + (size_t)ly * p.pitch;
+      for (uint32_t c = lane; c < nch; c += 32) {
+        uint64_t A = A0 + 16ull * c;
+        uint8_t *dst = dst_row + 16u * c;
+        if (A + 16 <= total) {
+          uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(in + A));
+        } else {
+          for (uint32_t b = 0; b < 16; ++b) dst[b] = A + b < total ? in[A + b] : 0;
         }
-        adj[d * 32 + lane] = base;
       }
+    }
+    for (uint32_t d = warp; d < 9; d += nw) {
+      uint64_t base = ~0ull;
+      if (((p.dir_mask >> d) & 1u) && lane < ntiles) {
+        uint32_t ntx, nty;
+        if (adjacent_tile(p, tab, tab + 256, tab + 512, tx0 + lane, ty, (int)(d % 3) - 1,
+                          (int)(d / 3) - 1, ntx, nty))
+          base = (uint64_t)nty * p.TH * W + (uint64_t)ntx * TW;
+      }
+      adj[d * 32 + lane] = base;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 
-    // Phase 2: transpose bytes -> words (bit i = tile i) and gather halo words.
-    for (uint32_t c = warp; c < cells; c += kTiledWarps) {
-      uint32_t ly = fdiv(p.div_tw, c), lx = c - ly * p.TW;
-      bool alive = false;
-      if (lane < ntiles) alive = stage[(size_t)ly * p.pitch + row_a[ly] + lane * p.TW + lx] != 0;
-      uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
-      if (lane == 0) win[c] = word;
+    // Phase 2: pack each tile row into a word (lane = tile; bit 8b + j <- byte
+    // 4j + b), transpose so that lane L holds local cell (ly, lx(L)) of all 32
+    // tiles; gather the halo words.
+    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+      uint32_t acc = 0;
+      if (lane < ntiles) {
+        uint32_t o = ly * p.pitch + ((uint32_t)rowS[ly] & 15u) + lane * TW;
+        const uint32_t *w = stage32 + (o >> 2);
+        uint32_t sh = (o & 3u) * 8u;
+        uint32_t wv[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) wv[j] = (uint32_t)j < nwin ? w[j] : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          acc += (__funnelshift_r(wv[j], wv[j + 1], sh) & 0x01010101u) << j;
+        acc &= valid;
+      }
+      win[ly * 32u + lane] = transpose32(acc, keep, rot);
     }
-    for (uint32_t h = warp; h < nhalo; h += kTiledWarps) {
+    for (uint32_t h = warp; h < nhalo; h += nw) {
       uint64_t base = adj[p.halo_dir[h] * 32u + lane];
       bool alive = false;
       if (base != ~0ull) {
         uint64_t a = base + p.halo_off[h];
-        if (a < total) alive = in[a] != 0;
+        if (a < total) alive = in[a] & 1u;
         else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
       }
       uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
-      if (lane == 0) win[cells + h] = word;
+      if (lane == 0) win[slots + h] = word;
     }
     __syncthreads();
 
-    // Phase 3: the rule on whole words.
-    for (uint32_t c = tid; c < cells; c += blockDim.x) {
-      uint4 rr = reinterpret_cast<const uint4 *>(refs)[c];
+    // Phase 3: the rule on whole words (references are byte offsets into win).
+    for (uint32_t c = tid; c < slots; c += nthreads) {
       uint32_t n[8];
-      n[0] = win[rr.x & 0xFFFFu];
-      n[1] = win[rr.x >> 16];
-      n[2] = win[rr.y & 0xFFFFu];
-      n[3] = win[rr.y >> 16];
-      n[4] = win[rr.z & 0xFFFFu];
-      n[5] = win[rr.z >> 16];
-      n[6] = win[rr.w & 0xFFFFu];
-      n[7] = win[rr.w >> 16];
-      wout[c] = rule_word(p.rule, win[c], n);
+#pragma unroll
+      for (int d = 0; d < 8; ++d)
+        n[d] = *reinterpret_cast<const uint32_t *>(smem + refs[d * slots + c]);
+      wout[c] = rule_word<kLife>(p.rule, win[c], n);
     }
     __syncthreads();
 
-    // Phase 4: transpose words -> bytes into the staging rows.
-    for (uint32_t c = warp; c < cells; c += kTiledWarps) {
-      uint32_t ly = fdiv(p.div_tw, c), lx = c - ly * p.TW;
-      uint32_t word = wout[c];
-      if (lane < ntiles)
-        stage[(size_t)ly * p.pitch + row_a[ly] + lane * p.TW + lx] = (uint8_t)((word >> lane) & 1u);
-    }
-    __syncthreads();
-
-    // Phase 5: write the group's bytes; partial 16-byte chunks at the two ends
-    // of a row segment are written byte by byte (they border other groups).
-    for (uint32_t i = tid; i < p.TH * nchunk; i += blockDim.x) {
-      uint32_t ly = i / nchunk, c = i - ly * nchunk;
-      uint64_t S = ((uint64_t)ty * p.TH + ly) * W + (uint64_t)tx0 * p.TW;
-      uint64_t A = (S & ~(uint64_t)15) + 16ull * c;
-      if (A >= S + seg) continue;
-      const uint8_t *src = stage + (size_t)ly * p.pitch + 16u * c;
-      if (A >= S && A + 16 <= S + seg) {
-        *reinterpret_cast<uint4 *>(out + A) = *reinterpret_cast<const uint4 *>(src);
-      } else {
-        for (uint32_t b = 0; b < 16; ++b)
-          if (A + b >= S && A + b < S + seg) out[A + b] = src[b];
+    // Phase 4: inverse transpose (lane = tile again), unpack to bytes and write
+    // the tile rows back into the staging rows at their unaligned offsets.
+    // A word shared by two neighbouring lanes is handed to the right-hand lane.
+    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+      uint32_t y = transpose32(wout[ly * 32u + lane], keep, rot) & valid;
+      uint32_t o = ly * p.pitch + ((uint32_t)rowS[ly] & 15u) + lane * TW;
+      if (TW >= 4) {
+        uint32_t shb = o & 3u, sh = shb * 8u, base = o >> 2;
+        uint32_t u[9], prev = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          uint32_t v = (y >> t) & 0x01010101u;
+          u[t] = __funnelshift_l(prev, v, sh);
+          prev = v;
+        }
+        u[8] = __funnelshift_l(prev, 0u, sh);
+        uint32_t E = (shb + TW - 1) >> 2;
+        bool partial = ((shb + TW) & 3u) != 0;
+        uint32_t last;
+        if (kTW) {
+          constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
+          last = E == E0 ? u[E0] : u[E0 + 1 < 9 ? E0 + 1 : 8];
+        } else {
+          last = 0;
+#pragma unroll
+          for (int t = 0; t < 9; ++t) last = (uint32_t)t == E ? u[t] : last;
+        }
+        uint32_t recv = __shfl_up_sync(0xFFFFFFFFu, partial ? last : 0u, 1);
+        if (lane >= 1) u[0] |= recv;
+        bool give = partial && lane + 1 < ntiles;
+        if (lane < ntiles) {
+#pragma unroll
+          for (int t = 0; t < 9; ++t)
+            if ((uint32_t)t < E || ((uint32_t)t == E && !give)) stage32w[base + t] = u[t];
+        }
+      } else if (lane < ntiles) {
+        for (uint32_t b = 0; b < TW; ++b) {
+          uint32_t L = 8u * (b & 3u) + (b >> 2);
+          stage[o + b] = (uint8_t)((y >> L) & 1u);
+        }
       }
+    }
+    __syncthreads();
+
+    // Phase 5: write the group's bytes, one warp per row: whole 16-byte
+    // chunks inside the row segment as vector stores, the < 16 bytes at each
+    // end (they share a chunk with a neighbouring group) one byte per lane.
+    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+      const uint64_t S = rowS[ly], A0 = S & ~(uint64_t)15, E = S + seg;
+      const uint64_t F0 = (S + 15) & ~(uint64_t)15, F1 = E & ~(uint64_t)15;
+      const uint8_t *src_row = stage + (size_t)ly * p.pitch;  // staging byte j = address A0 + j
+      for (uint64_t A = F0 + 16ull * lane; A < F1; A += 16ull * 32)
+        *reinterpret_cast<uint4 *>(out + A) =
+            *reinterpret_cast<const uint4 *>(src_row + (uint32_t)(A - A0));
+      const uint64_t head_end = F0 < E ? F0 : E;
+      const uint64_t tail_beg = F1 > head_end ? F1 : head_end;
+      uint64_t A = lane < 16 ? S + lane : tail_beg + (lane - 16);
+      if (lane < 16 ? A < head_end : A < E) out[A] = src_row[(uint32_t)(A - A0)];
     }
     __syncthreads();
   }
@@ -263,24 +349,40 @@ __global__ void __launch_bounds__(kTiledThreads) step_tiled_kernel(TiledDev p,
 
 // ---- host side: the level-L neighbour program ------------------------------
 
+const void *tiled_kernel_for(bool life, uint32_t TW) {
+  if (life) {
+    if (TW == 27) return (const void *)step_tiled_kernel<true, 27>;
+    if (TW == 25) return (const void *)step_tiled_kernel<true, 25>;
+    return (const void *)step_tiled_kernel<true, 0>;
+  }
+  if (TW == 27) return (const void *)step_tiled_kernel<false, 27>;
+  if (TW == 25) return (const void *)step_tiled_kernel<false, 25>;
+  return (const void *)step_tiled_kernel<false, 0>;
+}
+
+
 uint64_t ipow(uint64_t b, uint32_t e) {
   uint64_t p = 1;
   while (e--) p *= b;
   return p;
 }
 
-size_t smem_for(uint32_t cells, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
-  size_t off = ((size_t)cells * 16 + 15) & ~(size_t)15;
-  off += (((size_t)cells + nhalo + 1) * 4 + 15) & ~(size_t)15;
-  off += ((size_t)cells * 4 + 15) & ~(size_t)15;
+size_t smem_for(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
+  size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
+  off += (size_t)slots * 4;
+  off += (size_t)slots * 16;
   off += 9 * 32 * 8;
-  off += ((size_t)TH * 4 + 15) & ~(size_t)15;
+  off += ((size_t)TH * 8 + 15) & ~(size_t)15;
   off += 3 * 256;
-  off += (size_t)TH * pitch;
+  off += (size_t)TH * pitch + 64;  // slack: row reads round up to whole words
   return off;
 }
 
+// Staging row: up to 15 bytes of alignment offset + 32 tiles + one spare chunk.
 uint32_t pitch_for(uint32_t TW) { return ((32u * TW + 30u) / 16u + 1u) * 16u; }
+
+// Slot of local cell lx inside its row word (the pack's bit order).
+inline uint32_t lane_of(uint32_t lx) { return 8u * (lx & 3u) + (lx >> 2); }
 
 // Local lambda of the level-L fractal: compact (lx, ly) -> expanded (X, Y).
 void local_lambda(const FracDev &f, uint32_t L, uint32_t lx, uint32_t ly, uint32_t &X,
@@ -310,15 +412,24 @@ void sq_tiled_free(TiledProgram *p) {
   delete p;
 }
 
+// A tile row (k^ceil(L/2) cells) must fit one 32-bit word.
+bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
+  return level >= 1 && level <= h->f.r && ipow(h->f.k, (level + 1) / 2) <= 32 &&
+         ipow(h->f.k, level / 2) <= 4096;
+}
+
+// Largest level whose tile rows fit one 32-bit word and whose shared memory
+// stays within kTiledSmemCap (so that several CTAs share an SM).
 int sq_tiled_default_level(const squeeze_handle *h) {
   const FracDev &f = h->f;
   int best = -1;
   for (uint32_t L = 1; L <= f.r; ++L) {
-    uint64_t cells = ipow(f.k, L);
-    if (cells > 16384) break;
-    uint32_t TW = (uint32_t)ipow(f.k, (L + 1) / 2), TH = (uint32_t)ipow(f.k, L / 2);
-    // halo slots are bounded by the perimeter cells times 3
-    size_t sm = smem_for((uint32_t)cells, 12u * (uint32_t)ipow(f.s, L) + 8u, TH, pitch_for(TW));
+    uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2);
+    if (TW > 32 || TH > 4096) break;
+    uint32_t slots = (uint32_t)TH * 32;
+    // halo slots are bounded by 4 edges of s^L cells plus corners
+    size_t sm = smem_for(slots, 4u * (uint32_t)ipow(f.s, L) + 8u, (uint32_t)TH,
+                         pitch_for((uint32_t)TW));
     if (sm <= kTiledSmemCap) best = (int)L;
   }
   return best;
@@ -329,8 +440,10 @@ int sq_tiled_prepare(squeeze_handle *h) {
   const FracDev &f = h->f;
   uint32_t L = h->tiled_level ? h->tiled_level : (uint32_t)sq_tiled_default_level(h);
   if ((int)L <= 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
-  uint32_t TW = (uint32_t)ipow(f.k, (L + 1) / 2), TH = (uint32_t)ipow(f.k, L / 2);
-  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L);
+  uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
+  if (TW64 > 32 || TH64 > 4096) return SQUEEZE_ERR_UNSUPPORTED;  // a tile row must fit one word
+  uint32_t TW = (uint32_t)TW64, TH = (uint32_t)TH64;
+  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH * 32;
   if ((uint64_t)side * side > (1ull << 28)) return SQUEEZE_ERR_UNSUPPORTED;
 
   // Local lambda and its inverse over the level-L box.
@@ -340,12 +453,14 @@ int sq_tiled_prepare(squeeze_handle *h) {
     local_lambda(f, L, c % TW, c / TW, X[c], Y[c]);
     inv[(size_t)Y[c] * side + X[c]] = (int32_t)c;
   }
-  // Neighbour references: local cell, halo slot, or the zero word.
-  std::vector<uint32_t> refs((size_t)cells * 8);
-  std::vector<uint64_t> halo_key;  // (dir << 32) | local cell in the adjacent block
+  auto slot_of = [&](uint32_t c) { return (c / TW) * 32u + lane_of(c % TW); };
+  // Neighbour references (by slot): local cell, halo slot, or the zero word.
   const uint32_t kNone = 0xFFFFFFFFu;
+  std::vector<uint32_t> refs((size_t)slots * 8, kNone);
+  std::vector<uint64_t> halo_key;  // (dir << 32) | local cell in the adjacent block
   for (uint32_t c = 0; c < cells; ++c) {
-    int slot = 0;
+    int k8 = 0;
+    uint32_t sc = slot_of(c);
     for (int d = 0; d < 9; ++d) {
       if (d == 4) continue;
       int64_t qx = (int64_t)X[c] + d % 3 - 1, qy = (int64_t)Y[c] + d / 3 - 1;
@@ -355,23 +470,27 @@ int sq_tiled_prepare(squeeze_handle *h) {
       uint32_t ref = kNone;
       if (target >= 0) {
         if (bx == 0 && by == 0) {
-          ref = (uint32_t)target;
+          ref = slot_of((uint32_t)target);
         } else {
           uint64_t key = ((uint64_t)((by + 1) * 3 + (bx + 1)) << 32) | (uint32_t)target;
           size_t i = 0;
           while (i < halo_key.size() && halo_key[i] != key) ++i;
           if (i == halo_key.size()) halo_key.push_back(key);
-          ref = cells + (uint32_t)i;
+          ref = slots + (uint32_t)i;
         }
       }
-      refs[(size_t)c * 8 + slot++] = ref;
+      refs[(size_t)sc * 8 + k8++] = ref;
     }
   }
   uint32_t nhalo = (uint32_t)halo_key.size();
-  if ((uint64_t)cells + nhalo + 1 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
-  std::vector<uint16_t> refs16((size_t)cells * 8);
-  for (size_t i = 0; i < refs.size(); ++i)
-    refs16[i] = (uint16_t)(refs[i] == kNone ? cells + nhalo : refs[i]);
+  // References are byte offsets into the word array, stored d-major.
+  if (((uint64_t)slots + nhalo + 1) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
+  std::vector<uint16_t> refs16((size_t)slots * 8);
+  for (uint32_t c = 0; c < slots; ++c)
+    for (uint32_t d = 0; d < 8; ++d) {
+      uint32_t r = refs[(size_t)c * 8 + d];
+      refs16[(size_t)d * slots + c] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
+    }
   std::vector<uint64_t> halo_off(nhalo);
   std::vector<uint8_t> halo_dir(nhalo);
   uint32_t dir_mask = 0;
@@ -388,6 +507,7 @@ int sq_tiled_prepare(squeeze_handle *h) {
   p->TW = TW;
   p->TH = TH;
   p->cells = cells;
+  p->slots = slots;
   p->nhalo = nhalo;
   p->dir_mask = dir_mask;
   p->tiles_x = f.W / TW;
@@ -395,8 +515,8 @@ int sq_tiled_prepare(squeeze_handle *h) {
   p->groups_per_band = (p->tiles_x + 31) / 32;
   p->groups = (uint64_t)p->groups_per_band * p->tiles_y;
   p->pitch = pitch_for(TW);
-  p->smem = smem_for(cells, nhalo, TH, p->pitch);
-  if (p->groups >= (1ull << 32)) {
+  p->smem = smem_for(slots, nhalo, TH, p->pitch);
+  if (p->groups >= (1ull << 32) || p->smem > 200 * 1024) {
     delete p;
     return SQUEEZE_ERR_UNSUPPORTED;
   }
@@ -409,13 +529,20 @@ int sq_tiled_prepare(squeeze_handle *h) {
     e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
     e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p->smem);
+  // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
+  int best_w = 8;
+  for (int w = 12; w >= 6; --w)
+    if ((TH + w - 1) / w * w - TH < (TH + best_w - 1) / best_w * best_w - TH) best_w = w;
+  p->threads = 32 * best_w;
   int per_sm = 0, sms = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tiled_kernel, kTiledThreads,
-                                                      p->smem);
+  for (int life = 0; life < 2 && e == cudaSuccess; ++life) {
+    const void *fn = tiled_kernel_for(life != 0, TW);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    int n = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, p->threads, p->smem);
+    per_sm = life ? (n < per_sm ? n : per_sm) : n;
+  }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) {
     sq_tiled_free(p);
@@ -444,7 +571,11 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
   d.TW = p->TW;
   d.TH = p->TH;
   d.cells = p->cells;
+  d.slots = p->slots;
   d.nhalo = p->nhalo;
+  d.nwin = (3u + p->TW + 3u) / 4u;
+  d.valid = 0;
+  for (uint32_t lx = 0; lx < p->TW; ++lx) d.valid |= 1u << lane_of(lx);
   d.dir_mask = p->dir_mask;
   d.tiles_x = p->tiles_x;
   d.tiles_y = p->tiles_y;
@@ -457,7 +588,10 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
   d.halo_off = p->d_halo_off;
   d.halo_dir = p->d_halo_dir;
   d.status = h->d_status;
-  step_tiled_kernel<<<p->grid, kTiledThreads, p->smem, st>>>(d, in, out);
+  bool life = h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
+  void *args[] = {&d, &in, &out};
+  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, p->TW), dim3(p->grid), dim3(p->threads), args,
+                           p->smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }
