@@ -29,6 +29,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "squeeze_internal.cuh"
@@ -43,16 +44,20 @@ struct TiledProgram {
   size_t smem;
   int grid;
   int threads;              // CTA size: whole warps, chosen to balance the TH rows
+  uint32_t ndirs;           // directions that carry halo references
+  uint8_t dir_list[9];      // those directions, (dy + 1) * 3 + (dx + 1)
+  uint32_t halo_start[10];  // halo slots are sorted by direction
   uint16_t *d_refs;         // 8 x slots byte offsets of the neighbour words
-  uint64_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
-  uint8_t *d_halo_dir;      // nhalo directions, (dy + 1) * 3 + (dx + 1)
+  uint32_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
+  uint8_t *d_halo_dir;      // nhalo indices into dir_list
+  uint32_t *d_adj;          // ndirs x tiles: adjacent tile index, or ~0 (hole / off the box)
 };
 
 namespace sq {
 namespace {
 
 constexpr int kTiledMaxThreads = 384;
-constexpr size_t kTiledSmemCap = 52 * 1024;
+constexpr size_t kTiledSmemCap = 56 * 1024;
 
 struct TiledDev {
   FracDev f;
@@ -62,10 +67,15 @@ struct TiledDev {
   uint32_t nwin;        // aligned 32-bit words covering one tile row
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
-  FastDiv div_tw, div_gpb;
+  uint32_t ndirs;
+  uint32_t dir_list[9];
+  uint32_t halo_start[10];   // halo slots of direction j: [halo_start[j], halo_start[j+1])
+  uint64_t tiles;            // tiles_x * tiles_y
+  FastDiv div_tw, div_gpb, div_tiles_x;
   const uint16_t *refs;
-  const uint64_t *halo_off;
+  const uint32_t *halo_off;
   const uint8_t *halo_dir;
+  const uint32_t *adj;
   int *status;
 };
 
@@ -101,20 +111,19 @@ __device__ __forceinline__ uint32_t rule_word(const Rule &rule, uint32_t self, c
 }
 
 // Carry walk: the level-L block adjacent to tile (tx, ty) in direction
-// (dx, dy), as a tile (ntx, nty), or false for a hole / off the box.
+// (dx, dy), as a tile (ntx, nty), or false for a hole / off the box.  Tile
+// coordinates fit 32 bits, so the digit updates use wrap-around arithmetic.
 __device__ bool adjacent_tile(const TiledDev &p, const uint8_t *taux, const uint8_t *tauy,
                               const uint8_t *hnu, uint32_t tx, uint32_t ty, int dx, int dy,
                               uint32_t &ntx, uint32_t &nty) {
   const FracDev &f = p.f;
   int cx = dx, cy = dy;
-  uint32_t qx = tx, qy = ty, pwx = 1, pwy = 1;
-  int64_t ax = tx, ay = ty;
+  uint32_t qx = tx, qy = ty, pwx = 1, pwy = 1, ax = tx, ay = ty;
   for (uint32_t mu = p.L + 1; mu <= f.r && (cx | cy); ++mu) {
     bool odd = mu & 1u;
     uint32_t src = odd ? qx : qy;
     uint32_t q = fdiv(f.divk, src);
     uint32_t beta = src - q * f.k;
-    if (odd) qx = q; else qy = q;
     int ox = (int)taux[beta] + cx, oy = (int)tauy[beta] + cy;
     cx = ox < 0 ? -1 : (ox >= (int)f.s ? 1 : 0);
     cy = oy < 0 ? -1 : (oy >= (int)f.s ? 1 : 0);
@@ -122,19 +131,84 @@ __device__ bool adjacent_tile(const TiledDev &p, const uint8_t *taux, const uint
     oy -= cy * (int)f.s;
     uint32_t nb = hnu[oy * f.s + ox];
     if (nb == kHole) return false;
-    int64_t delta = (int64_t)nb - (int64_t)beta;
+    uint32_t delta = nb - beta;
     if (odd) {
+      qx = q;
       ax += delta * pwx;
       pwx *= f.k;
     } else {
+      qy = q;
       ay += delta * pwy;
       pwy *= f.k;
     }
   }
   if (cx | cy) return false;  // carried past the top level: off the box
-  ntx = (uint32_t)ax;
-  nty = (uint32_t)ay;
+  ntx = ax;
+  nty = ay;
   return true;
+}
+
+// ---- bulk asynchronous copies (TMA, non-tensor form) and mbarriers ----------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for an mbarrier phase, giving up after ~2 s with DEVICE_TIMEOUT.
+__device__ __forceinline__ void mbar_wait(uint64_t *m, uint32_t parity, int *status) {
+  if (mbar_try_wait(m, parity)) return;
+  uint64_t t0 = global_ns();
+  while (!mbar_try_wait(m, parity)) {
+    if (global_ns() - t0 > 2000000000ull) {
+      flag(status, SQUEEZE_ERR_DEVICE_TIMEOUT);
+      return;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(m))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 // 32x32 bit transpose across a warp: on return lane j holds the word whose
@@ -162,12 +236,66 @@ __device__ __forceinline__ void make_transpose(unsigned lane, uint32_t *keep, ui
   }
 }
 
+// Geometry of one group of tiles: band ty, first tile tx0, tile count and the
+// byte offset of the group's first row in the compact buffer.
+struct Group {
+  uint32_t ty, tx0, ntiles, seg;
+  uint64_t row0;
+};
+
+__device__ __forceinline__ Group group_at(const TiledDev &p, uint32_t TW, uint64_t g) {
+  Group G;
+  G.ty = fdiv(p.div_gpb, (uint32_t)g);  // groups < 2^32 checked on the host
+  G.tx0 = ((uint32_t)g - G.ty * p.groups_per_band) * 32u;
+  G.ntiles = min(32u, p.tiles_x - G.tx0);
+  G.seg = G.ntiles * TW;
+  G.row0 = (uint64_t)G.ty * p.TH * p.f.W + (uint64_t)G.tx0 * TW;
+  return G;
+}
+
+// Bytes of row ly that a bulk copy brings in: from the 16-byte aligned start
+// A0 up to the segment end rounded up to 16, clipped (to a multiple of 16) at
+// the end of the buffer; the few bytes past the clip are loaded by threads.
+__device__ __forceinline__ uint32_t row_bulk_bytes(uint64_t S, uint32_t seg, uint64_t total) {
+  uint64_t A0 = S & ~(uint64_t)15;
+  uint64_t nb = (S - A0 + seg + 15) & ~(uint64_t)15;
+  if (A0 + nb > total) nb = (total - A0) & ~(uint64_t)15;
+  return (uint32_t)nb;
+}
+
+// Warp 0: issue the bulk loads of group G's rows into one staging buffer.
+__device__ __forceinline__ void issue_group_loads(const TiledDev &p, const Group &G,
+                                                  const uint8_t *in, uint8_t *stage,
+                                                  uint64_t *mbar, unsigned lane) {
+  const uint64_t W = p.f.W, total = p.f.cells;
+  uint32_t bytes = 0;
+  for (uint32_t ly = lane; ly < p.TH; ly += 32)
+    bytes += row_bulk_bytes(G.row0 + (uint64_t)ly * W, G.seg, total);
+  bytes = __reduce_add_sync(0xFFFFFFFFu, bytes);
+  if (lane == 0) mbar_expect_tx(mbar, bytes);
+  __syncwarp();
+  for (uint32_t ly = lane; ly < p.TH; ly += 32) {
+    uint64_t S = G.row0 + (uint64_t)ly * W;
+    uint32_t nb = row_bulk_bytes(S, G.seg, total);
+    if (nb) bulk_load(stage + (size_t)ly * p.pitch, in + (S & ~(uint64_t)15), nb, mbar);
+  }
+}
+
 // The kernel is instantiated for the common tile-row widths so that the word
 // counts of a row are compile-time constants; kTW = 0 takes TW at run time.
+//
+// Work split inside a CTA (persistent over groups of 32 tiles): warp w owns
+// rows ly = w, w + nw, ... of every group, from packing through the rule to
+// the write-back, so only two CTA barriers separate groups: one before the
+// words of a group are written (the previous group is done reading them) and
+// one before the rule reads them.  Warp w also resolves directions j = w,
+// w + nw, ... of the tiles' adjacent tiles and gathers their halo words.
+// While group i is processed in staging buffer i % 2, warp 0 has already
+// issued the bulk loads of group i + 1 into the other buffer.
 template <bool kLife, int kTW>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
   const uint32_t nwin = kTW ? (3u + (uint32_t)kTW + 3u) / 4u : p.nwin;
@@ -175,80 +303,90 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   // references can be stored as byte offsets.
   uint32_t *win = reinterpret_cast<uint32_t *>(smem);                        // slots + nhalo + 1
   size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
-  uint32_t *wout = reinterpret_cast<uint32_t *>(smem + off);                 // slots
-  off += (size_t)slots * 4;
-  uint16_t *refs = reinterpret_cast<uint16_t *>(smem + off);                 // 8 * slots, d-major
-  off += (size_t)slots * 16;
-  uint64_t *adj = reinterpret_cast<uint64_t *>(smem + off);                  // 9 * 32
-  off += 9 * 32 * 8;
-  uint64_t *rowS = reinterpret_cast<uint64_t *>(smem + off);                 // TH
-  off += ((size_t)p.TH * 8 + 15) & ~(size_t)15;
-  uint8_t *tab = smem + off;                                                 // 3 * 256
-  off += 3 * 256;
-  uint8_t *stage = smem + off;                                               // TH * pitch + 64
-  const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
-  uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
+  uint32_t *hoff = reinterpret_cast<uint32_t *>(smem + off);                 // nhalo
+  off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + off);                 // 2
+  off += 16;
+  const size_t stage_bytes = (size_t)p.TH * p.pitch + 64;
+  uint8_t *stage_base = smem + off;                                          // 2 * stage_bytes
 
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const unsigned nthreads = blockDim.x, nw = nthreads >> 5;
   uint32_t keep[5], rot[5];
   make_transpose(lane, keep, rot);
-  for (uint32_t i = tid; i < slots * 8; i += nthreads) refs[i] = p.refs[i];
-  for (uint32_t i = tid; i < 256; i += nthreads) {
-    tab[i] = p.f.taux[i];
-    tab[256 + i] = p.f.tauy[i];
-    tab[512 + i] = p.f.hnu[i];
+  for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
+  if (tid == 0) {
+    win[slots + nhalo] = 0u;  // the "no neighbour" word
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (tid == 0) win[slots + nhalo] = 0u;  // the "no neighbour" word
+  __syncthreads();
   const uint64_t total = p.f.cells, W = p.f.W;
   const uint32_t valid = p.valid;
 
-  for (uint64_t g = blockIdx.x; g < p.groups; g += gridDim.x) {
-    const uint32_t ty = fdiv(p.div_gpb, (uint32_t)g);  // groups < 2^32 checked on the host
-    const uint32_t tx0 = ((uint32_t)g - ty * p.groups_per_band) * 32u;
-    const uint32_t ntiles = min(32u, p.tiles_x - tx0);
-    const uint32_t seg = ntiles * TW;  // bytes of this group in one compact row
-    const uint64_t row0 = (uint64_t)ty * p.TH * W + (uint64_t)tx0 * TW;
+  if (warp == 0 && blockIdx.x < p.groups)
+    issue_group_loads(p, group_at(p, TW, blockIdx.x), in, stage_base, &mbar[0], lane);
 
-    // Phase 1: stage the group's rows (16-byte aligned chunks) with cp.async,
-    // one warp per row; meanwhile the warps resolve the tiles' adjacent
-    // blocks, one direction each.
-    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
-      const uint64_t S = row0 + (uint64_t)ly * W, A0 = S & ~(uint64_t)15;
-      const uint32_t nch = (uint32_t)((S - A0 + seg + 15) >> 4);
-      if (lane == 0) rowS[ly] = S;
-      uint8_t *dst_row = stage + (size_t)ly * p.pitch;
-      for (uint32_t c = lane; c < nch; c += 32) {
-        uint64_t A = A0 + 16ull * c;
-        uint8_t *dst = dst_row + 16u * c;
-        if (A + 16 <= total) {
-          uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(in + A));
-        } else {
-          for (uint32_t b = 0; b < 16; ++b) dst[b] = A + b < total ? in[A + b] : 0;
+  uint32_t it = 0;
+  for (uint64_t g = blockIdx.x; g < p.groups; g += gridDim.x, ++it) {
+    const uint32_t b = it & 1u;
+    uint8_t *stage = stage_base + b * stage_bytes;
+    const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
+    uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
+    const Group G = group_at(p, TW, g);
+    const uint32_t ntiles = G.ntiles, seg = G.seg;
+
+    // Barrier 1: every warp's bulk stores of the previous group have finished
+    // reading their staging rows, and every warp is done reading `win`.
+    bulk_wait_read();
+    __syncthreads();
+    if (warp == 0 && g + gridDim.x < p.groups)
+      issue_group_loads(p, group_at(p, TW, g + gridDim.x), in, stage_base + (b ^ 1u) * stage_bytes,
+                        &mbar[b ^ 1u], lane);
+
+    // Adjacent tiles (precomputed table) and halo words, one direction per warp.
+    for (uint32_t j = warp; j < p.ndirs; j += nw) {
+      uint64_t base = ~0ull;
+      if (lane < ntiles) {
+        uint32_t t = __ldg(p.adj + j * p.tiles + (uint64_t)G.ty * p.tiles_x + G.tx0 + lane);
+        if (t != ~0u) {
+          uint32_t nty = fdiv(p.div_tiles_x, t), ntx = t - nty * p.tiles_x;
+          base = (uint64_t)nty * p.TH * W + (uint64_t)ntx * TW;
         }
       }
-    }
-    for (uint32_t d = warp; d < 9; d += nw) {
-      uint64_t base = ~0ull;
-      if (((p.dir_mask >> d) & 1u) && lane < ntiles) {
-        uint32_t ntx, nty;
-        if (adjacent_tile(p, tab, tab + 256, tab + 512, tx0 + lane, ty, (int)(d % 3) - 1,
-                          (int)(d / 3) - 1, ntx, nty))
-          base = (uint64_t)nty * p.TH * W + (uint64_t)ntx * TW;
+      for (uint32_t h = p.halo_start[j]; h < p.halo_start[j + 1]; ++h) {
+        bool alive = false;
+        if (base != ~0ull) {
+          uint64_t a = base + hoff[h];
+          if (a < total) alive = __ldg(in + a) & 1u;
+          else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+        }
+        uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
+        if (lane == 0) win[slots + h] = word;
       }
-      adj[d * 32 + lane] = base;
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
 
-    // Phase 2: pack each tile row into a word (lane = tile; bit 8b + j <- byte
-    // 4j + b), transpose so that lane L holds local cell (ly, lx(L)) of all 32
-    // tiles; gather the halo words.
+    mbar_wait(&mbar[b], (it >> 1) & 1u, p.status);
+    // Bytes past the last 16-byte boundary of the buffer (only rows that end
+    // within 16 bytes of it) were not part of a bulk copy: load them here.
+    if (G.row0 + (uint64_t)(p.TH - 1) * W + seg + 16 > total) {
+      for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+        const uint64_t S = G.row0 + (uint64_t)ly * W, A0 = S & ~(uint64_t)15;
+        const uint64_t got = A0 + row_bulk_bytes(S, seg, total);
+        for (uint64_t a = got + lane; a < S + seg; a += 32)
+          stage[(size_t)ly * p.pitch + (uint32_t)(a - A0)] = in[a];
+      }
+      __syncwarp();
+    }
+
+    // Pack each own tile row into a word (lane = tile; bit 8b + j <- byte
+    // 4j + b) and transpose so that lane L holds local cell (ly, lx(L)) of
+    // all 32 tiles.
     for (uint32_t ly = warp; ly < p.TH; ly += nw) {
       uint32_t acc = 0;
       if (lane < ntiles) {
-        uint32_t o = ly * p.pitch + ((uint32_t)rowS[ly] & 15u) + lane * TW;
+        uint32_t o = ly * p.pitch + (((uint32_t)G.row0 + ly * (uint32_t)W) & 15u) + lane * TW;
         const uint32_t *w = stage32 + (o >> 2);
         uint32_t sh = (o & 3u) * 8u;
         uint32_t wv[9];
@@ -261,35 +399,20 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
       }
       win[ly * 32u + lane] = transpose32(acc, keep, rot);
     }
-    for (uint32_t h = warp; h < nhalo; h += nw) {
-      uint64_t base = adj[p.halo_dir[h] * 32u + lane];
-      bool alive = false;
-      if (base != ~0ull) {
-        uint64_t a = base + p.halo_off[h];
-        if (a < total) alive = in[a] & 1u;
-        else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
-      }
-      uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
-      if (lane == 0) win[slots + h] = word;
-    }
+    // Barrier 2: all words of the group (rows and halo) are in place.
     __syncthreads();
 
-    // Phase 3: the rule on whole words (references are byte offsets into win).
-    for (uint32_t c = tid; c < slots; c += nthreads) {
+    // Rule, inverse transpose and write-back of the own rows.
+    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
+      const uint32_t c = ly * 32u + lane;
       uint32_t n[8];
 #pragma unroll
       for (int d = 0; d < 8; ++d)
-        n[d] = *reinterpret_cast<const uint32_t *>(smem + refs[d * slots + c]);
-      wout[c] = rule_word<kLife>(p.rule, win[c], n);
-    }
-    __syncthreads();
-
-    // Phase 4: inverse transpose (lane = tile again), unpack to bytes and write
-    // the tile rows back into the staging rows at their unaligned offsets.
-    // A word shared by two neighbouring lanes is handed to the right-hand lane.
-    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
-      uint32_t y = transpose32(wout[ly * 32u + lane], keep, rot) & valid;
-      uint32_t o = ly * p.pitch + ((uint32_t)rowS[ly] & 15u) + lane * TW;
+        n[d] = *reinterpret_cast<const uint32_t *>(smem + __ldg(p.refs + d * slots + c));
+      const uint32_t next = rule_word<kLife>(p.rule, win[c], n);
+      uint32_t y = transpose32(next, keep, rot) & valid;
+      const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+      uint32_t o = ly * p.pitch + a + lane * TW;
       if (TW >= 4) {
         uint32_t shb = o & 3u, sh = shb * 8u, base = o >> 2;
         uint32_t u[9], prev = 0;
@@ -303,7 +426,7 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
         uint32_t E = (shb + TW - 1) >> 2;
         bool partial = ((shb + TW) & 3u) != 0;
         uint32_t last;
-        if (kTW) {
+        if constexpr (kTW != 0) {
           constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
           last = E == E0 ? u[E0] : u[E0 + 1 < 9 ? E0 + 1 : 8];
         } else {
@@ -315,35 +438,66 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
         if (lane >= 1) u[0] |= recv;
         bool give = partial && lane + 1 < ntiles;
         if (lane < ntiles) {
+          if constexpr (kTW != 0) {
+            constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
 #pragma unroll
-          for (int t = 0; t < 9; ++t)
-            if ((uint32_t)t < E || ((uint32_t)t == E && !give)) stage32w[base + t] = u[t];
+            for (uint32_t t = 0; t < E0; ++t) stage32w[base + t] = u[t];
+            if (E > E0 || !give) stage32w[base + E0] = u[E0];
+            if (E0 + 1 < 9 && E > E0 && !give) stage32w[base + E0 + 1] = u[E0 + 1 < 9 ? E0 + 1 : 8];
+          } else {
+#pragma unroll
+            for (int t = 0; t < 9; ++t)
+              if ((uint32_t)t < E || ((uint32_t)t == E && !give)) stage32w[base + t] = u[t];
+          }
         }
       } else if (lane < ntiles) {
-        for (uint32_t b = 0; b < TW; ++b) {
-          uint32_t L = 8u * (b & 3u) + (b >> 2);
-          stage[o + b] = (uint8_t)((y >> L) & 1u);
+        for (uint32_t bb = 0; bb < TW; ++bb) {
+          uint32_t L = 8u * (bb & 3u) + (bb >> 2);
+          stage[o + bb] = (uint8_t)((y >> L) & 1u);
         }
       }
+      // Write the row: one bulk store for its whole 16-byte chunks
+      // [head, mid_end) and single bytes for the ragged ends (they share a
+      // chunk with a neighbouring group).
+      fence_async_smem();
+      __syncwarp();
+      const uint32_t head = (16u - a) & 15u, mid_end = seg - ((a + seg) & 15u);
+      const bool split = head < mid_end && seg >= head;
+      const uint64_t S = G.row0 + (uint64_t)ly * W;
+      if (lane == 0 && split) {
+        bulk_store(out + S + head, stage + ly * p.pitch + a + head, mid_end - head);
+        bulk_commit();
+      }
+      uint32_t ob = lane < 16u || !split ? lane : mid_end + lane - 16u;
+      bool mine = split ? (lane < 16u ? lane < head : ob < seg) : lane < seg;
+      if (mine) out[S + ob] = stage[ly * p.pitch + a + ob];
     }
-    __syncthreads();
+  }
+  bulk_wait_all();
+}
 
-    // Phase 5: write the group's bytes, one warp per row: whole 16-byte
-    // chunks inside the row segment as vector stores, the < 16 bytes at each
-    // end (they share a chunk with a neighbouring group) one byte per lane.
-    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
-      const uint64_t S = rowS[ly], A0 = S & ~(uint64_t)15, E = S + seg;
-      const uint64_t F0 = (S + 15) & ~(uint64_t)15, F1 = E & ~(uint64_t)15;
-      const uint8_t *src_row = stage + (size_t)ly * p.pitch;  // staging byte j = address A0 + j
-      for (uint64_t A = F0 + 16ull * lane; A < F1; A += 16ull * 32)
-        *reinterpret_cast<uint4 *>(out + A) =
-            *reinterpret_cast<const uint4 *>(src_row + (uint32_t)(A - A0));
-      const uint64_t head_end = F0 < E ? F0 : E;
-      const uint64_t tail_beg = F1 > head_end ? F1 : head_end;
-      uint64_t A = lane < 16 ? S + lane : tail_beg + (lane - 16);
-      if (lane < 16 ? A < head_end : A < E) out[A] = src_row[(uint32_t)(A - A0)];
-    }
-    __syncthreads();
+// One thread per (direction, tile): the adjacent tile of every tile, computed
+// once per fractal and tile level by the carry walk and kept in HBM.
+__global__ void build_adjacency_kernel(TiledDev p, uint32_t *__restrict__ adj) {
+  __shared__ uint8_t tab[768];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    tab[i] = p.f.taux[i];
+    tab[256 + i] = p.f.tauy[i];
+    tab[512 + i] = p.f.hnu[i];
+  }
+  __syncthreads();
+  const uint64_t n = (uint64_t)p.ndirs * p.tiles;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t j = (uint32_t)(i / p.tiles);
+    uint64_t t = i - (uint64_t)j * p.tiles;
+    uint32_t ty = (uint32_t)(t / p.tiles_x), tx = (uint32_t)(t - (uint64_t)ty * p.tiles_x);
+    uint32_t d = p.dir_list[j], ntx, nty;
+    uint32_t r = ~0u;
+    if (adjacent_tile(p, tab, tab + 256, tab + 512, tx, ty, (int)(d % 3) - 1, (int)(d / 3) - 1,
+                      ntx, nty))
+      r = nty * p.tiles_x + ntx;
+    adj[i] = r;
   }
 }
 
@@ -369,17 +523,14 @@ uint64_t ipow(uint64_t b, uint32_t e) {
 
 size_t smem_for(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
   size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
-  off += (size_t)slots * 4;
-  off += (size_t)slots * 16;
-  off += 9 * 32 * 8;
-  off += ((size_t)TH * 8 + 15) & ~(size_t)15;
-  off += 3 * 256;
-  off += (size_t)TH * pitch + 64;  // slack: row reads round up to whole words
+  off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
+  off += 16;
+  off += 2 * ((size_t)TH * pitch + 64);  // two staging buffers (+ slack for whole-word reads)
   return off;
 }
 
 // Staging row: up to 15 bytes of alignment offset + 32 tiles + one spare chunk.
-uint32_t pitch_for(uint32_t TW) { return ((32u * TW + 30u) / 16u + 1u) * 16u; }
+uint32_t pitch_for(uint32_t TW) { return (32u * TW + 15u + 15u) / 16u * 16u; }
 
 // Slot of local cell lx inside its row word (the pack's bit order).
 inline uint32_t lane_of(uint32_t lx) { return 8u * (lx & 3u) + (lx >> 2); }
@@ -404,11 +555,52 @@ void local_lambda(const FracDev &f, uint32_t L, uint32_t lx, uint32_t ly, uint32
 
 using namespace sq;
 
+
+namespace {
+
+TiledDev tiled_dev(const squeeze_handle *h, const TiledProgram *p) {
+  TiledDev d;
+  memset(&d, 0, sizeof(d));
+  d.f = h->f;
+  d.rule = h->rule;
+  d.L = p->L;
+  d.TW = p->TW;
+  d.TH = p->TH;
+  d.cells = p->cells;
+  d.slots = p->slots;
+  d.nhalo = p->nhalo;
+  d.nwin = (3u + p->TW + 3u) / 4u;
+  d.valid = 0;
+  for (uint32_t lx = 0; lx < p->TW; ++lx) d.valid |= 1u << lane_of(lx);
+  d.dir_mask = p->dir_mask;
+  d.ndirs = p->ndirs;
+  for (int i = 0; i < 9; ++i) d.dir_list[i] = p->dir_list[i];
+  for (int i = 0; i < 10; ++i) d.halo_start[i] = p->halo_start[i];
+  d.tiles_x = p->tiles_x;
+  d.tiles_y = p->tiles_y;
+  d.tiles = (uint64_t)p->tiles_x * p->tiles_y;
+  d.groups_per_band = p->groups_per_band;
+  d.pitch = p->pitch;
+  d.groups = p->groups;
+  d.div_tw = make_fastdiv(p->TW);
+  d.div_gpb = make_fastdiv(p->groups_per_band);
+  d.div_tiles_x = make_fastdiv(p->tiles_x);
+  d.refs = p->d_refs;
+  d.halo_off = p->d_halo_off;
+  d.halo_dir = p->d_halo_dir;
+  d.adj = p->d_adj;
+  d.status = h->d_status;
+  return d;
+}
+
+}  // namespace
+
 void sq_tiled_free(TiledProgram *p) {
   if (!p) return;
   cudaFree(p->d_refs);
   cudaFree(p->d_halo_off);
   cudaFree(p->d_halo_dir);
+  cudaFree(p->d_adj);
   delete p;
 }
 
@@ -483,6 +675,21 @@ int sq_tiled_prepare(squeeze_handle *h) {
     }
   }
   uint32_t nhalo = (uint32_t)halo_key.size();
+  // Sort the halo slots by direction (then local cell) and renumber them.
+  {
+    std::vector<uint32_t> order(nhalo), rank(nhalo);
+    for (uint32_t i = 0; i < nhalo; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(),
+              [&](uint32_t x, uint32_t y) { return halo_key[x] < halo_key[y]; });
+    std::vector<uint64_t> sorted(nhalo);
+    for (uint32_t i = 0; i < nhalo; ++i) {
+      rank[order[i]] = i;
+      sorted[i] = halo_key[order[i]];
+    }
+    halo_key.swap(sorted);
+    for (auto &r : refs)
+      if (r != kNone && r >= slots) r = slots + rank[r - slots];
+  }
   // References are byte offsets into the word array, stored d-major.
   if (((uint64_t)slots + nhalo + 1) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
   std::vector<uint16_t> refs16((size_t)slots * 8);
@@ -491,15 +698,27 @@ int sq_tiled_prepare(squeeze_handle *h) {
       uint32_t r = refs[(size_t)c * 8 + d];
       refs16[(size_t)d * slots + c] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
     }
-  std::vector<uint64_t> halo_off(nhalo);
+  std::vector<uint32_t> halo_off(nhalo);
   std::vector<uint8_t> halo_dir(nhalo);
   uint32_t dir_mask = 0;
+  for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(halo_key[i] >> 32);
+  uint8_t dir_list[9] = {0}, dir_index[9] = {0};
+  uint32_t ndirs = 0;
+  for (uint32_t d = 0; d < 9; ++d)
+    if ((dir_mask >> d) & 1u) {
+      dir_index[d] = (uint8_t)ndirs;
+      dir_list[ndirs++] = (uint8_t)d;
+    }
+  if ((uint64_t)TH * f.W > 0xFFFFFFFFull) return SQUEEZE_ERR_UNSUPPORTED;
+  uint32_t halo_start[10] = {0};
   for (uint32_t i = 0; i < nhalo; ++i) {
     uint32_t d = (uint32_t)(halo_key[i] >> 32), lc = (uint32_t)halo_key[i];
-    halo_dir[i] = (uint8_t)d;
-    halo_off[i] = (uint64_t)(lc / TW) * f.W + lc % TW;
-    dir_mask |= 1u << d;
+    halo_dir[i] = dir_index[d];
+    halo_off[i] = (lc / TW) * f.W + lc % TW;
+    halo_start[dir_index[d] + 1] = i + 1;
   }
+  for (uint32_t j = 1; j <= 9; ++j)
+    if (halo_start[j] < halo_start[j - 1]) halo_start[j] = halo_start[j - 1];
 
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
@@ -510,6 +729,9 @@ int sq_tiled_prepare(squeeze_handle *h) {
   p->slots = slots;
   p->nhalo = nhalo;
   p->dir_mask = dir_mask;
+  p->ndirs = ndirs;
+  memcpy(p->dir_list, dir_list, sizeof(dir_list));
+  memcpy(p->halo_start, halo_start, sizeof(halo_start));
   p->tiles_x = f.W / TW;
   p->tiles_y = f.H / TH;
   p->groups_per_band = (p->tiles_x + 31) / 32;
@@ -521,12 +743,12 @@ int sq_tiled_prepare(squeeze_handle *h) {
     return SQUEEZE_ERR_UNSUPPORTED;
   }
   cudaError_t e = cudaMalloc(&p->d_refs, refs16.size() * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_refs, refs16.data(), refs16.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
-    e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 8, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
     e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
@@ -554,6 +776,20 @@ int sq_tiled_prepare(squeeze_handle *h) {
   }
   uint64_t grid = (uint64_t)per_sm * sms;
   p->grid = (int)(grid < p->groups ? grid : p->groups);
+  uint64_t tiles = (uint64_t)p->tiles_x * p->tiles_y;
+  if (ndirs) {
+    e = cudaMalloc(&p->d_adj, (size_t)ndirs * tiles * 4);
+    if (e == cudaSuccess) {
+      TiledDev d = tiled_dev(h, p);
+      build_adjacency_kernel<<<grid_for((uint64_t)ndirs * tiles, 256), 256>>>(d, p->d_adj);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      sq_tiled_free(p);
+      return sq_cuda_fail(e);
+    }
+  }
   h->tiled = p;
   h->tiled_level = L;
   return SQUEEZE_OK;
@@ -564,30 +800,7 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
   const TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
-  TiledDev d;
-  d.f = h->f;
-  d.rule = h->rule;
-  d.L = p->L;
-  d.TW = p->TW;
-  d.TH = p->TH;
-  d.cells = p->cells;
-  d.slots = p->slots;
-  d.nhalo = p->nhalo;
-  d.nwin = (3u + p->TW + 3u) / 4u;
-  d.valid = 0;
-  for (uint32_t lx = 0; lx < p->TW; ++lx) d.valid |= 1u << lane_of(lx);
-  d.dir_mask = p->dir_mask;
-  d.tiles_x = p->tiles_x;
-  d.tiles_y = p->tiles_y;
-  d.groups_per_band = p->groups_per_band;
-  d.pitch = p->pitch;
-  d.groups = p->groups;
-  d.div_tw = make_fastdiv(p->TW);
-  d.div_gpb = make_fastdiv(p->groups_per_band);
-  d.refs = p->d_refs;
-  d.halo_off = p->d_halo_off;
-  d.halo_dir = p->d_halo_dir;
-  d.status = h->d_status;
+  TiledDev d = tiled_dev(h, p);
   bool life = h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
   void *args[] = {&d, &in, &out};
   SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, p->TW), dim3(p->grid), dim3(p->threads), args,
