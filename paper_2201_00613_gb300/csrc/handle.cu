@@ -29,6 +29,43 @@ int check_handle(const squeeze_handle *h) { return h ? SQUEEZE_OK : SQUEEZE_ERR_
 
 }  // namespace
 
+// Validate an NBB descriptor and fill the kernel-side tables (no device work).
+int sq_fill_fractal(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r, sq::FracDev &f) {
+  if (!offsets) return SQUEEZE_ERR_INVALID_ARG;
+  if (s < 2 || s > (uint32_t)sq::kMaxS) return SQUEEZE_ERR_INVALID_ARG;
+  if (k < 1 || k > s * s || k > (uint32_t)sq::kMaxK) return SQUEEZE_ERR_INVALID_ARG;
+  if (r > 62) return SQUEEZE_ERR_INVALID_ARG;
+  uint64_t n, W, H;
+  if (!fits_pow(s, r, 1ull << 30, &n)) return SQUEEZE_ERR_INVALID_ARG;
+  if (!fits_pow(k, (r + 1) / 2, 0xFFFFFFFFull, &W)) return SQUEEZE_ERR_INVALID_ARG;
+  if (!fits_pow(k, r / 2, 0xFFFFFFFFull, &H)) return SQUEEZE_ERR_INVALID_ARG;
+  memset(&f, 0, sizeof(f));
+  f.s = s;
+  f.k = k;
+  f.r = r;
+  f.n = (uint32_t)n;
+  f.W = (uint32_t)W;
+  f.H = (uint32_t)H;
+  f.cells = W * H;
+  f.divk = sq::make_fastdiv(k);
+  f.divs = sq::make_fastdiv(s);
+  f.divW = sq::make_fastdiv((uint32_t)W);
+  memset(f.hnu, sq::kHole, sizeof(f.hnu));
+  for (uint32_t b = 0; b < k; ++b) {
+    uint32_t tx = offsets[2 * b], ty = offsets[2 * b + 1];
+    if (tx >= s || ty >= s || f.hnu[ty * s + tx] != sq::kHole)
+      return SQUEEZE_ERR_INVALID_ARG;  // offset out of range or repeated
+    f.taux[b] = (uint8_t)tx;
+    f.tauy[b] = (uint8_t)ty;
+    f.hnu[ty * s + tx] = (uint8_t)b;
+  }
+  return SQUEEZE_OK;
+}
+
+void sq_set_error_text(const char *text) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s", text);
+}
+
 int sq_cuda_fail(cudaError_t e) {
   snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e),
            cudaGetErrorString(e));
@@ -54,42 +91,15 @@ const char *squeeze_last_cuda_error(void) { return g_last_cuda_error; }
 
 int squeeze_create(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
                    squeeze_handle **out) {
-  if (!out || !offsets) return SQUEEZE_ERR_INVALID_ARG;
+  if (!out) return SQUEEZE_ERR_INVALID_ARG;
   *out = nullptr;
-  if (s < 2 || s > (uint32_t)sq::kMaxS) return SQUEEZE_ERR_INVALID_ARG;
-  if (k < 1 || k > s * s || k > (uint32_t)sq::kMaxK) return SQUEEZE_ERR_INVALID_ARG;
-  if (r > 62) return SQUEEZE_ERR_INVALID_ARG;
-  uint64_t n, W, H, cells;
-  if (!fits_pow(s, r, 1ull << 30, &n)) return SQUEEZE_ERR_INVALID_ARG;
-  if (!fits_pow(k, (r + 1) / 2, 0xFFFFFFFFull, &W)) return SQUEEZE_ERR_INVALID_ARG;
-  if (!fits_pow(k, r / 2, 0xFFFFFFFFull, &H)) return SQUEEZE_ERR_INVALID_ARG;
-  cells = W * H;
-
+  sq::FracDev f;
+  int rc = sq_fill_fractal(s, k, offsets, r, f);
+  if (rc) return rc;
   squeeze_handle *h = new (std::nothrow) squeeze_handle;
   if (!h) return SQUEEZE_ERR_OOM;
   memset(h, 0, sizeof(*h));
-  sq::FracDev &f = h->f;
-  f.s = s;
-  f.k = k;
-  f.r = r;
-  f.n = (uint32_t)n;
-  f.W = (uint32_t)W;
-  f.H = (uint32_t)H;
-  f.cells = cells;
-  f.divk = sq::make_fastdiv(k);
-  f.divs = sq::make_fastdiv(s);
-  f.divW = sq::make_fastdiv((uint32_t)W);
-  memset(f.hnu, sq::kHole, sizeof(f.hnu));
-  for (uint32_t b = 0; b < k; ++b) {
-    uint32_t tx = offsets[2 * b], ty = offsets[2 * b + 1];
-    if (tx >= s || ty >= s || f.hnu[ty * s + tx] != sq::kHole) {
-      delete h;
-      return SQUEEZE_ERR_INVALID_ARG;  // offset out of range or repeated
-    }
-    f.taux[b] = (uint8_t)tx;
-    f.tauy[b] = (uint8_t)ty;
-    f.hnu[ty * s + tx] = (uint8_t)b;
-  }
+  h->f = f;
   h->rule.birth = 1u << 3;
   h->rule.survive = (1u << 2) | (1u << 3);
   cudaError_t e = cudaGetDevice(&h->device);

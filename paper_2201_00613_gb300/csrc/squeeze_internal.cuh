@@ -145,6 +145,58 @@ __device__ __host__ inline uint8_t bernoulli_cell(uint64_t seed, uint32_t p_q24,
   return (uint8_t)((splitmix64_at(seed, key) >> 40) < (uint64_t)p_q24);
 }
 
+// Kernel-side description of a tiled-step program (see step_tiled.cu).
+struct TiledDev {
+  FracDev f;
+  Rule rule;
+  uint32_t L, TW, TH, cells, nhalo, dir_mask, slots;
+  uint32_t valid;            // packed-word bits that hold a real cell (lx < TW)
+  uint32_t nwin;             // aligned 32-bit words covering one tile row
+  uint32_t tiles_x, tiles_y, groups_per_band, pitch;
+  uint64_t groups;
+  uint32_t ndirs;
+  uint32_t dir_list[9];
+  uint32_t halo_start[10];   // halo slots of direction j: [halo_start[j], halo_start[j+1])
+  uint64_t tiles;            // tiles_x * tiles_y
+  FastDiv div_tw, div_gpb, div_tiles_x;
+  const uint16_t *refs;      // 8 x slots byte offsets of the neighbour words
+  const uint32_t *halo_off;  // nhalo byte offsets inside a tile
+  const uint8_t *halo_dir;   // nhalo direction indices
+  const uint32_t *adj;       // ndirs x tiles adjacent tile indices (~0: none)
+  int *status;
+};
+
+// Geometry and launch shape of a tiled-step program, independent of where its
+// tables live.
+struct TileSpec {
+  uint32_t L, TW, TH, cells, slots, nhalo, ndirs, dir_mask;
+  uint8_t dir_list[9];
+  uint32_t halo_start[10];
+  uint32_t tiles_x, tiles_y, groups_per_band, pitch;
+  uint64_t groups;
+  size_t smem;
+  int grid, threads;
+};
+
+// Capacities needed to build the program of one tile level.
+struct TileBuildSizes {
+  uint64_t box, cells, slots, halo;
+};
+
+// Caller-provided host buffers for building a program: work arrays (inv, X,
+// Y, refs, halo_key, halo_sorted, order, rank) and outputs (refs16 with
+// 8 * slots entries, halo_off and halo_dir with one entry per halo slot).
+struct TileBuild {
+  int32_t *inv;
+  uint32_t *X, *Y, *refs;
+  uint64_t *halo_key, *halo_sorted;
+  uint32_t *order, *rank;
+  uint16_t *refs16;
+  uint32_t *halo_off;
+  uint8_t *halo_dir;
+  uint64_t box_cap, cells_cap, slots_cap, halo_cap;
+};
+
 inline unsigned grid_for(uint64_t items, unsigned block, unsigned cap = 152u * 16u) {
   uint64_t g = (items + block - 1) / block;
   if (g < 1) g = 1;
@@ -167,8 +219,10 @@ struct squeeze_handle {
   TiledProgram *tiled;       // lazily built neighbour program of the tiled kernel
 };
 
-// Error plumbing (handle.cu).
+// Error plumbing and descriptor validation (handle.cu).
 int sq_cuda_fail(cudaError_t e);
+void sq_set_error_text(const char *text);
+int sq_fill_fractal(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r, sq::FracDev &f);
 #define SQ_CUDA(call)                                 \
   do {                                                \
     cudaError_t e_ = (call);                          \
@@ -189,6 +243,16 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
                          cudaStream_t st);
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
+int sq_tiled_default_level_for(const sq::FracDev &f);
+void sq_tile_build_sizes(const sq::FracDev &f, uint32_t L, sq::TileBuildSizes &z);
+int sq_tile_build(const sq::FracDev &f, uint32_t L, const sq::TileBuild &B, sq::TileSpec &sp);
+int sq_tile_launch_config(sq::TileSpec &sp, int device);
+sq::TiledDev sq_tiled_dev(const sq::FracDev &f, const sq::Rule &rule, const sq::TileSpec &sp,
+                          const uint16_t *refs, const uint32_t *halo_off,
+                          const uint8_t *halo_dir, const uint32_t *adj, int *status);
+int sq_tile_build_adjacency(const sq::TiledDev &d, uint32_t *adj, cudaStream_t st);
+int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t *in,
+                   uint8_t *out, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,

@@ -35,18 +35,7 @@
 #include "squeeze_internal.cuh"
 
 struct TiledProgram {
-  uint32_t L, TW, TH, cells, nhalo;
-  uint32_t slots;           // TH * 32 padded word slots
-  uint32_t dir_mask;        // bit d set when some halo slot uses direction d
-  uint32_t tiles_x, tiles_y, groups_per_band;
-  uint64_t groups;
-  uint32_t pitch;           // bytes per staging row
-  size_t smem;
-  int grid;
-  int threads;              // CTA size: whole warps, chosen to balance the TH rows
-  uint32_t ndirs;           // directions that carry halo references
-  uint8_t dir_list[9];      // those directions, (dy + 1) * 3 + (dx + 1)
-  uint32_t halo_start[10];  // halo slots are sorted by direction
+  sq::TileSpec spec;
   uint16_t *d_refs;         // 8 x slots byte offsets of the neighbour words
   uint32_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
   uint8_t *d_halo_dir;      // nhalo indices into dir_list
@@ -58,26 +47,6 @@ namespace {
 
 constexpr int kTiledMaxThreads = 384;
 constexpr size_t kTiledSmemCap = 56 * 1024;
-
-struct TiledDev {
-  FracDev f;
-  Rule rule;
-  uint32_t L, TW, TH, cells, nhalo, dir_mask, slots;
-  uint32_t valid;       // packed-word bits that hold a real cell (lx < TW)
-  uint32_t nwin;        // aligned 32-bit words covering one tile row
-  uint32_t tiles_x, tiles_y, groups_per_band, pitch;
-  uint64_t groups;
-  uint32_t ndirs;
-  uint32_t dir_list[9];
-  uint32_t halo_start[10];   // halo slots of direction j: [halo_start[j], halo_start[j+1])
-  uint64_t tiles;            // tiles_x * tiles_y
-  FastDiv div_tw, div_gpb, div_tiles_x;
-  const uint16_t *refs;
-  const uint32_t *halo_off;
-  const uint8_t *halo_dir;
-  const uint32_t *adj;
-  int *status;
-};
 
 __device__ __forceinline__ void flag(int *status, int code) { atomicCAS(status, 0, code); }
 
@@ -556,44 +525,42 @@ void local_lambda(const FracDev &f, uint32_t L, uint32_t lx, uint32_t ly, uint32
 using namespace sq;
 
 
-namespace {
-
-TiledDev tiled_dev(const squeeze_handle *h, const TiledProgram *p) {
+TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
+                      const uint16_t *refs, const uint32_t *halo_off, const uint8_t *halo_dir,
+                      const uint32_t *adj, int *status) {
   TiledDev d;
   memset(&d, 0, sizeof(d));
-  d.f = h->f;
-  d.rule = h->rule;
-  d.L = p->L;
-  d.TW = p->TW;
-  d.TH = p->TH;
-  d.cells = p->cells;
-  d.slots = p->slots;
-  d.nhalo = p->nhalo;
-  d.nwin = (3u + p->TW + 3u) / 4u;
+  d.f = f;
+  d.rule = rule;
+  d.L = sp.L;
+  d.TW = sp.TW;
+  d.TH = sp.TH;
+  d.cells = sp.cells;
+  d.slots = sp.slots;
+  d.nhalo = sp.nhalo;
+  d.nwin = (3u + sp.TW + 3u) / 4u;
   d.valid = 0;
-  for (uint32_t lx = 0; lx < p->TW; ++lx) d.valid |= 1u << lane_of(lx);
-  d.dir_mask = p->dir_mask;
-  d.ndirs = p->ndirs;
-  for (int i = 0; i < 9; ++i) d.dir_list[i] = p->dir_list[i];
-  for (int i = 0; i < 10; ++i) d.halo_start[i] = p->halo_start[i];
-  d.tiles_x = p->tiles_x;
-  d.tiles_y = p->tiles_y;
-  d.tiles = (uint64_t)p->tiles_x * p->tiles_y;
-  d.groups_per_band = p->groups_per_band;
-  d.pitch = p->pitch;
-  d.groups = p->groups;
-  d.div_tw = make_fastdiv(p->TW);
-  d.div_gpb = make_fastdiv(p->groups_per_band);
-  d.div_tiles_x = make_fastdiv(p->tiles_x);
-  d.refs = p->d_refs;
-  d.halo_off = p->d_halo_off;
-  d.halo_dir = p->d_halo_dir;
-  d.adj = p->d_adj;
-  d.status = h->d_status;
+  for (uint32_t lx = 0; lx < sp.TW; ++lx) d.valid |= 1u << lane_of(lx);
+  d.dir_mask = sp.dir_mask;
+  d.ndirs = sp.ndirs;
+  for (int i = 0; i < 9; ++i) d.dir_list[i] = sp.dir_list[i];
+  for (int i = 0; i < 10; ++i) d.halo_start[i] = sp.halo_start[i];
+  d.tiles_x = sp.tiles_x;
+  d.tiles_y = sp.tiles_y;
+  d.tiles = (uint64_t)sp.tiles_x * sp.tiles_y;
+  d.groups_per_band = sp.groups_per_band;
+  d.pitch = sp.pitch;
+  d.groups = sp.groups;
+  d.div_tw = make_fastdiv(sp.TW);
+  d.div_gpb = make_fastdiv(sp.groups_per_band);
+  d.div_tiles_x = make_fastdiv(sp.tiles_x);
+  d.refs = refs;
+  d.halo_off = halo_off;
+  d.halo_dir = halo_dir;
+  d.adj = adj;
+  d.status = status;
   return d;
 }
-
-}  // namespace
 
 void sq_tiled_free(TiledProgram *p) {
   if (!p) return;
@@ -604,7 +571,6 @@ void sq_tiled_free(TiledProgram *p) {
   delete p;
 }
 
-// A tile row (k^ceil(L/2) cells) must fit one 32-bit word.
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
   return level >= 1 && level <= h->f.r && ipow(h->f.k, (level + 1) / 2) <= 32 &&
          ipow(h->f.k, level / 2) <= 4096;
@@ -612,8 +578,9 @@ bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
 
 // Largest level whose tile rows fit one 32-bit word and whose shared memory
 // stays within kTiledSmemCap (so that several CTAs share an SM).
-int sq_tiled_default_level(const squeeze_handle *h) {
-  const FracDev &f = h->f;
+int sq_tiled_default_level(const squeeze_handle *h) { return sq_tiled_default_level_for(h->f); }
+
+int sq_tiled_default_level_for(const FracDev &f) {
   int best = -1;
   for (uint32_t L = 1; L <= f.r; ++L) {
     uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2);
@@ -627,35 +594,44 @@ int sq_tiled_default_level(const squeeze_handle *h) {
   return best;
 }
 
-int sq_tiled_prepare(squeeze_handle *h) {
-  if (h->tiled) return SQUEEZE_OK;
-  const FracDev &f = h->f;
-  uint32_t L = h->tiled_level ? h->tiled_level : (uint32_t)sq_tiled_default_level(h);
-  if ((int)L <= 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
+void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
+  uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2), side = ipow(f.s, L);
+  z.box = side * side;
+  z.cells = TW * TH;
+  z.slots = TH * 32;
+  z.halo = 8 * z.cells;
+}
+
+// Host construction of the level-L neighbour program (see the file comment):
+// local lambda and its inverse over the level-L box, 8 references per slot
+// (local slot, halo slot or the zero word), halo slots sorted by direction.
+int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp) {
+  if (L == 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
   uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
   if (TW64 > 32 || TH64 > 4096) return SQUEEZE_ERR_UNSUPPORTED;  // a tile row must fit one word
   uint32_t TW = (uint32_t)TW64, TH = (uint32_t)TH64;
   uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH * 32;
-  if ((uint64_t)side * side > (1ull << 28)) return SQUEEZE_ERR_UNSUPPORTED;
+  if ((uint64_t)side * side > B.box_cap || cells > B.cells_cap || slots > B.slots_cap)
+    return SQUEEZE_ERR_UNSUPPORTED;
+  if ((uint64_t)TH * f.W > 0xFFFFFFFFull) return SQUEEZE_ERR_UNSUPPORTED;
 
-  // Local lambda and its inverse over the level-L box.
-  std::vector<int32_t> inv((size_t)side * side, -1);
-  std::vector<uint32_t> X(cells), Y(cells);
+  int32_t *inv = B.inv;
+  for (uint64_t i = 0; i < (uint64_t)side * side; ++i) inv[i] = -1;
   for (uint32_t c = 0; c < cells; ++c) {
-    local_lambda(f, L, c % TW, c / TW, X[c], Y[c]);
-    inv[(size_t)Y[c] * side + X[c]] = (int32_t)c;
+    local_lambda(f, L, c % TW, c / TW, B.X[c], B.Y[c]);
+    inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
   auto slot_of = [&](uint32_t c) { return (c / TW) * 32u + lane_of(c % TW); };
-  // Neighbour references (by slot): local cell, halo slot, or the zero word.
   const uint32_t kNone = 0xFFFFFFFFu;
-  std::vector<uint32_t> refs((size_t)slots * 8, kNone);
-  std::vector<uint64_t> halo_key;  // (dir << 32) | local cell in the adjacent block
+  uint32_t *refs = B.refs;
+  for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;
+  uint32_t nhalo = 0;
   for (uint32_t c = 0; c < cells; ++c) {
     int k8 = 0;
     uint32_t sc = slot_of(c);
     for (int d = 0; d < 9; ++d) {
       if (d == 4) continue;
-      int64_t qx = (int64_t)X[c] + d % 3 - 1, qy = (int64_t)Y[c] + d / 3 - 1;
+      int64_t qx = (int64_t)B.X[c] + d % 3 - 1, qy = (int64_t)B.Y[c] + d / 3 - 1;
       int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
       int64_t lxp = qx - (int64_t)bx * side, lyp = qy - (int64_t)by * side;
       int32_t target = inv[(size_t)lyp * side + lxp];
@@ -664,131 +640,169 @@ int sq_tiled_prepare(squeeze_handle *h) {
         if (bx == 0 && by == 0) {
           ref = slot_of((uint32_t)target);
         } else {
+          // (direction << 32) | local cell in the adjacent block
           uint64_t key = ((uint64_t)((by + 1) * 3 + (bx + 1)) << 32) | (uint32_t)target;
-          size_t i = 0;
-          while (i < halo_key.size() && halo_key[i] != key) ++i;
-          if (i == halo_key.size()) halo_key.push_back(key);
-          ref = slots + (uint32_t)i;
+          uint32_t i = 0;
+          while (i < nhalo && B.halo_key[i] != key) ++i;
+          if (i == nhalo) {
+            if (nhalo == B.halo_cap) return SQUEEZE_ERR_UNSUPPORTED;
+            B.halo_key[nhalo++] = key;
+          }
+          ref = slots + i;
         }
       }
       refs[(size_t)sc * 8 + k8++] = ref;
     }
   }
-  uint32_t nhalo = (uint32_t)halo_key.size();
   // Sort the halo slots by direction (then local cell) and renumber them.
-  {
-    std::vector<uint32_t> order(nhalo), rank(nhalo);
-    for (uint32_t i = 0; i < nhalo; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(),
-              [&](uint32_t x, uint32_t y) { return halo_key[x] < halo_key[y]; });
-    std::vector<uint64_t> sorted(nhalo);
-    for (uint32_t i = 0; i < nhalo; ++i) {
-      rank[order[i]] = i;
-      sorted[i] = halo_key[order[i]];
-    }
-    halo_key.swap(sorted);
-    for (auto &r : refs)
-      if (r != kNone && r >= slots) r = slots + rank[r - slots];
-  }
+  for (uint32_t i = 0; i < nhalo; ++i) B.order[i] = i;
+  std::sort(B.order, B.order + nhalo,
+            [&](uint32_t x, uint32_t y) { return B.halo_key[x] < B.halo_key[y]; });
+  for (uint32_t i = 0; i < nhalo; ++i) B.rank[B.order[i]] = i;
+  for (size_t i = 0; i < (size_t)slots * 8; ++i)
+    if (refs[i] != kNone && refs[i] >= slots) refs[i] = slots + B.rank[refs[i] - slots];
+  // keys in sorted order
+  uint64_t *sorted = B.halo_sorted;
+  for (uint32_t i = 0; i < nhalo; ++i) sorted[B.rank[i]] = B.halo_key[i];
   // References are byte offsets into the word array, stored d-major.
   if (((uint64_t)slots + nhalo + 1) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
-  std::vector<uint16_t> refs16((size_t)slots * 8);
   for (uint32_t c = 0; c < slots; ++c)
     for (uint32_t d = 0; d < 8; ++d) {
       uint32_t r = refs[(size_t)c * 8 + d];
-      refs16[(size_t)d * slots + c] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
+      B.refs16[(size_t)d * slots + c] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
     }
-  std::vector<uint32_t> halo_off(nhalo);
-  std::vector<uint8_t> halo_dir(nhalo);
   uint32_t dir_mask = 0;
-  for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(halo_key[i] >> 32);
-  uint8_t dir_list[9] = {0}, dir_index[9] = {0};
-  uint32_t ndirs = 0;
+  for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(sorted[i] >> 32);
+  memset(&sp, 0, sizeof(sp));
+  uint8_t dir_index[9] = {0};
   for (uint32_t d = 0; d < 9; ++d)
     if ((dir_mask >> d) & 1u) {
-      dir_index[d] = (uint8_t)ndirs;
-      dir_list[ndirs++] = (uint8_t)d;
+      dir_index[d] = (uint8_t)sp.ndirs;
+      sp.dir_list[sp.ndirs++] = (uint8_t)d;
     }
-  if ((uint64_t)TH * f.W > 0xFFFFFFFFull) return SQUEEZE_ERR_UNSUPPORTED;
-  uint32_t halo_start[10] = {0};
   for (uint32_t i = 0; i < nhalo; ++i) {
-    uint32_t d = (uint32_t)(halo_key[i] >> 32), lc = (uint32_t)halo_key[i];
-    halo_dir[i] = dir_index[d];
-    halo_off[i] = (lc / TW) * f.W + lc % TW;
-    halo_start[dir_index[d] + 1] = i + 1;
+    uint32_t d = (uint32_t)(sorted[i] >> 32), lc = (uint32_t)sorted[i];
+    B.halo_dir[i] = dir_index[d];
+    B.halo_off[i] = (lc / TW) * f.W + lc % TW;
+    sp.halo_start[dir_index[d] + 1] = i + 1;
   }
   for (uint32_t j = 1; j <= 9; ++j)
-    if (halo_start[j] < halo_start[j - 1]) halo_start[j] = halo_start[j - 1];
-
-  TiledProgram *p = new TiledProgram;
-  memset(p, 0, sizeof(*p));
-  p->L = L;
-  p->TW = TW;
-  p->TH = TH;
-  p->cells = cells;
-  p->slots = slots;
-  p->nhalo = nhalo;
-  p->dir_mask = dir_mask;
-  p->ndirs = ndirs;
-  memcpy(p->dir_list, dir_list, sizeof(dir_list));
-  memcpy(p->halo_start, halo_start, sizeof(halo_start));
-  p->tiles_x = f.W / TW;
-  p->tiles_y = f.H / TH;
-  p->groups_per_band = (p->tiles_x + 31) / 32;
-  p->groups = (uint64_t)p->groups_per_band * p->tiles_y;
-  p->pitch = pitch_for(TW);
-  p->smem = smem_for(slots, nhalo, TH, p->pitch);
-  if (p->groups >= (1ull << 32) || p->smem > 200 * 1024) {
-    delete p;
-    return SQUEEZE_ERR_UNSUPPORTED;
-  }
-  cudaError_t e = cudaMalloc(&p->d_refs, refs16.size() * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_refs, refs16.data(), refs16.size() * 2, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nhalo)
-    e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nhalo)
-    e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
+    if (sp.halo_start[j] < sp.halo_start[j - 1]) sp.halo_start[j] = sp.halo_start[j - 1];
+  sp.L = L;
+  sp.TW = TW;
+  sp.TH = TH;
+  sp.cells = cells;
+  sp.slots = slots;
+  sp.nhalo = nhalo;
+  sp.dir_mask = dir_mask;
+  sp.tiles_x = f.W / TW;
+  sp.tiles_y = f.H / TH;
+  sp.groups_per_band = (sp.tiles_x + 31) / 32;
+  sp.groups = (uint64_t)sp.groups_per_band * sp.tiles_y;
+  sp.pitch = pitch_for(TW);
+  sp.smem = smem_for(slots, nhalo, TH, sp.pitch);
+  if (sp.groups >= (1ull << 32) || sp.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
   int best_w = 8;
   for (int w = 12; w >= 6; --w)
     if ((TH + w - 1) / w * w - TH < (TH + best_w - 1) / best_w * best_w - TH) best_w = w;
-  p->threads = 32 * best_w;
+  sp.threads = 32 * best_w;
+  return SQUEEZE_OK;
+}
+
+// Shared-memory opt-in and the persistent grid (CTAs per SM x SMs).
+int sq_tile_launch_config(TileSpec &sp, int device) {
   int per_sm = 0, sms = 0;
+  cudaError_t e = cudaSuccess;
   for (int life = 0; life < 2 && e == cudaSuccess; ++life) {
-    const void *fn = tiled_kernel_for(life != 0, TW);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    const void *fn = tiled_kernel_for(life != 0, sp.TW);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
     int n = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, p->threads, p->smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
     per_sm = life ? (n < per_sm ? n : per_sm) : n;
   }
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return sq_cuda_fail(e);
+  if (per_sm < 1) return SQUEEZE_ERR_UNSUPPORTED;
+  uint64_t grid = (uint64_t)per_sm * sms;
+  sp.grid = (int)(grid < sp.groups ? grid : sp.groups);
+  return SQUEEZE_OK;
+}
+
+int sq_tile_build_adjacency(const TiledDev &d, uint32_t *adj, cudaStream_t st) {
+  uint64_t n = (uint64_t)d.ndirs * d.tiles;
+  if (!n) return SQUEEZE_OK;
+  build_adjacency_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, adj);
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uint8_t *out,
+                   cudaStream_t st) {
+  if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
+  bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
+  TiledDev dd = d;
+  void *args[] = {&dd, &in, &out};
+  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW), dim3(sp.grid), dim3(sp.threads), args,
+                           sp.smem, st));
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_tiled_prepare(squeeze_handle *h) {
+  if (h->tiled) return SQUEEZE_OK;
+  const FracDev &f = h->f;
+  uint32_t L = h->tiled_level ? h->tiled_level : (uint32_t)sq_tiled_default_level(h);
+  if ((int)L <= 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
+  if (!sq_tiled_level_fits(h, L)) return SQUEEZE_ERR_UNSUPPORTED;
+  TileBuildSizes z;
+  sq_tile_build_sizes(f, L, z);
+  if (z.box > (1ull << 28)) return SQUEEZE_ERR_UNSUPPORTED;
+  std::vector<int32_t> inv(z.box);
+  std::vector<uint32_t> X(z.cells), Y(z.cells), refs(z.slots * 8), order(z.halo), rank(z.halo);
+  std::vector<uint64_t> keys(z.halo), sorted(z.halo);
+  std::vector<uint16_t> refs16(z.slots * 8);
+  std::vector<uint32_t> halo_off(z.halo);
+  std::vector<uint8_t> halo_dir(z.halo);
+  TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
+                 order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
+                 z.box, z.cells, z.slots, z.halo};
+  TiledProgram *p = new TiledProgram;
+  memset(p, 0, sizeof(*p));
+  int rc = sq_tile_build(f, L, B, p->spec);
+  if (rc == SQUEEZE_OK) rc = sq_tile_launch_config(p->spec, h->device);
+  if (rc != SQUEEZE_OK) {
+    delete p;
+    return rc;
+  }
+  const TileSpec &sp = p->spec;
+  uint32_t nhalo = sp.nhalo;
+  cudaError_t e = cudaMalloc(&p->d_refs, (size_t)sp.slots * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_refs, refs16.data(), (size_t)sp.slots * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nhalo)
+    e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nhalo)
+    e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
+  uint64_t tiles = (uint64_t)sp.tiles_x * sp.tiles_y;
+  if (e == cudaSuccess && sp.ndirs) e = cudaMalloc(&p->d_adj, (size_t)sp.ndirs * tiles * 4);
   if (e != cudaSuccess) {
     sq_tiled_free(p);
     return sq_cuda_fail(e);
   }
-  if (per_sm < 1) {
-    sq_tiled_free(p);
-    return SQUEEZE_ERR_UNSUPPORTED;
+  TiledDev d = sq_tiled_dev(f, h->rule, sp, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
+                            h->d_status);
+  rc = sq_tile_build_adjacency(d, p->d_adj, 0);
+  if (rc == SQUEEZE_OK) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = sq_cuda_fail(e);
   }
-  uint64_t grid = (uint64_t)per_sm * sms;
-  p->grid = (int)(grid < p->groups ? grid : p->groups);
-  uint64_t tiles = (uint64_t)p->tiles_x * p->tiles_y;
-  if (ndirs) {
-    e = cudaMalloc(&p->d_adj, (size_t)ndirs * tiles * 4);
-    if (e == cudaSuccess) {
-      TiledDev d = tiled_dev(h, p);
-      build_adjacency_kernel<<<grid_for((uint64_t)ndirs * tiles, 256), 256>>>(d, p->d_adj);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-      sq_tiled_free(p);
-      return sq_cuda_fail(e);
-    }
+  if (rc != SQUEEZE_OK) {
+    sq_tiled_free(p);
+    return rc;
   }
   h->tiled = p;
   h->tiled_level = L;
@@ -799,12 +813,7 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
                          cudaStream_t st) {
   const TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
-  if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
-  TiledDev d = tiled_dev(h, p);
-  bool life = h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
-  void *args[] = {&d, &in, &out};
-  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, p->TW), dim3(p->grid), dim3(p->threads), args,
-                           p->smem, st));
-  SQ_CUDA(cudaGetLastError());
-  return SQUEEZE_OK;
+  TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
+                            p->d_adj, h->d_status);
+  return sq_tile_launch(d, p->spec, in, out, st);
 }
