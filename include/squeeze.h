@@ -171,6 +171,34 @@ int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
 int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_t *d_state,
                           void *stream);
 
+/* ---- allocation-free step ------------------------------------------------- */
+
+/* squeeze_step_noalloc -- one tiled step (as squeeze_step with
+ * SQUEEZE_STEP_TILED, n_steps = 1) that allocates no memory, for callers
+ * that may not call cudaMalloc: code inside an application or framework that
+ * owns the whole device-memory budget, and latency-critical code that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree.  The paper
+ * has no counterpart; this is an interface of this library only.
+ *   s, k, offsets, r   the fractal, validated as in squeeze_create.
+ *   birth, survive     9-bit rule masks (B3/S23: 1<<3, (1<<2)|(1<<3)).
+ *   d_in, d_out        device buffers of k^r bytes, 16-byte aligned, not
+ *                      overlapping; the step reads d_in and writes d_out.
+ *   h_status           NULL, or a host int that receives the device status
+ *                      (OK / DEVICE_BOUNDS / DEVICE_TIMEOUT); when given, the
+ *                      call waits for the step to finish.
+ * All scratch (neighbour program, halo tables, per-tile adjacency table and
+ * the status word) lives in one fixed 4 MiB device array that every GPU
+ * loading the library keeps until exit; a level whose scratch would not fit
+ * (the Sierpinski triangle above r = 16, for instance) is rejected with
+ * UNSUPPORTED and a message in squeeze_last_cuda_error().  The first call on
+ * a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  Every
+ * call rewrites the array and clears its status word, so calls that overlap
+ * on the GPU (different streams, or threads without ordering) race on it. */
+int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
+                         uint32_t birth, uint32_t survive, const uint8_t *d_in, uint8_t *d_out,
+                         int *h_status, void *stream);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 
 /* squeeze_device_status -- synchronise the device, then read and clear the

@@ -69,6 +69,9 @@ _SIGS = {
                          ctypes.c_void_p], ctypes.c_int),
     "squeeze_bb_to_compact": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p], ctypes.c_int),
+    "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
+                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
     "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "squeeze_last_cuda_error": ([], ctypes.c_char_p),
@@ -211,6 +214,21 @@ def squeeze_bb_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
 def squeeze_bb_to_compact(h, d_grid, d_state, stream=None):
     _check(_load().squeeze_bb_to_compact(h, _ptr(d_grid), _ptr(d_state), _stream(stream)),
            "squeeze_bb_to_compact")
+
+
+def squeeze_step_noalloc(s: int, k: int, offsets, r: int, birth: int, survive: int,
+                         d_in, d_out, wait_status: bool = True, stream=None):
+    """One tiled step that allocates no memory (see include/squeeze.h).
+
+    Returns the device status when wait_status is true, else None.
+    """
+    flat = bytes(int(v) for pair in offsets for v in pair)
+    buf = ctypes.create_string_buffer(flat, len(flat))
+    st = ctypes.c_int(-99)
+    _check(_load().squeeze_step_noalloc(s, k, buf, r, birth, survive, _ptr(d_in), _ptr(d_out),
+                                        ctypes.byref(st) if wait_status else None,
+                                        _stream(stream)), "squeeze_step_noalloc")
+    return int(st.value) if wait_status else None
 
 
 def squeeze_device_status(h) -> int:
