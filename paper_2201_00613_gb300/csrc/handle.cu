@@ -203,7 +203,7 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
   cudaStream_t st = (cudaStream_t)stream;
   bool aligned = (((uintptr_t)d_buf0 | (uintptr_t)d_buf1) & 15u) == 0;
   if (kind == SQUEEZE_STEP_AUTO)
-    kind = aligned && (sq_tiled_default_level(h) > 0 || h->tiled_level) ? SQUEEZE_STEP_TILED
+    kind = aligned && (h->tiled_level || sq_tiled_default_level(h) > 0) ? SQUEEZE_STEP_TILED
                                                                         : SQUEEZE_MAP_ALU;
   if (kind == SQUEEZE_STEP_TILED && !aligned) return SQUEEZE_ERR_INVALID_ARG;
   if (kind == SQUEEZE_STEP_TILED) {

@@ -175,7 +175,8 @@ struct TileSpec {
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
   size_t smem;
-  int grid, threads;
+  int grid, threads;   // grid of the B3/S23 instantiation
+  int grid_rule;       // grid of the generic-rule instantiation
 };
 
 // Capacities needed to build the program of one tile level.
@@ -244,6 +245,7 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
 int sq_tiled_default_level_for(const sq::FracDev &f);
+size_t sq_tiled_smem_cap();
 void sq_tile_build_sizes(const sq::FracDev &f, uint32_t L, sq::TileBuildSizes &z);
 int sq_tile_build(const sq::FracDev &f, uint32_t L, const sq::TileBuild &B, sq::TileSpec &sp);
 int sq_tile_launch_config(sq::TileSpec &sp, int device);

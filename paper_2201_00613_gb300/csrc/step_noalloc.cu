@@ -78,10 +78,11 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
   }
   unsigned char *scratch = g_scratch_dev[dev];
 
-  // The largest tile level whose program fits the static buffers.
+  // The largest tile level whose program fits the static buffers and the
+  // kernel's shared-memory budget (tried from the top, built in place).
   TileSpec sp;
-  int L = sq_tiled_default_level_for(f);
-  for (rc = SQUEEZE_ERR_UNSUPPORTED; L >= 1; --L) {
+  rc = SQUEEZE_ERR_UNSUPPORTED;
+  for (int L = (int)(f.r < 16 ? f.r : 16); L >= 1; --L) {
     TileBuildSizes z;
     sq_tile_build_sizes(f, (uint32_t)L, z);
     if (z.box > kBoxCap || z.cells > kCellsCap || z.slots > kSlotsCap) continue;
@@ -89,7 +90,8 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
                    g_work.sorted, g_work.order, g_work.rank,  g_work.refs16, g_work.halo_off,
                    g_work.halo_dir, kBoxCap,    kCellsCap,    kSlotsCap,     kHaloCap};
     rc = sq_tile_build(f, (uint32_t)L, B, sp);
-    if (rc == SQUEEZE_OK) break;
+    if (rc == SQUEEZE_OK && sp.smem <= sq_tiled_smem_cap()) break;
+    rc = SQUEEZE_ERR_UNSUPPORTED;
   }
   if (rc != SQUEEZE_OK) {
     sq_set_error_text("squeeze_step_noalloc: no tile level fits the static host buffers");

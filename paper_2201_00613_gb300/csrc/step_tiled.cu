@@ -180,18 +180,24 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-// 32x32 bit transpose across a warp: on return lane j holds the word whose
+// 32x32 bit transposes across a warp: on return lane j holds the word whose
 // bit i was bit j of lane i's input.  Five butterfly stages; keep[] / rot[]
 // are the per-lane masks and rotations of each stage (see make_transpose).
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, const uint32_t *keep,
-                                                const uint32_t *rot) {
+// kN independent transposes with their shuffle stages interleaved.
+template <int kN>
+__device__ __forceinline__ void transpose32_n(uint32_t *x, const uint32_t *keep,
+                                              const uint32_t *rot) {
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
-    uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> s);
-    uint32_t t = __funnelshift_l(y, y, rot[s]);
-    x = (x & keep[s]) | (t & ~keep[s]);
+    uint32_t y[kN];
+#pragma unroll
+    for (int k = 0; k < kN; ++k) y[k] = __shfl_xor_sync(0xFFFFFFFFu, x[k], 16 >> s);
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+      uint32_t t = __funnelshift_l(y[k], y[k], rot[s]);
+      x[k] = (x[k] & keep[s]) | (t & ~keep[s]);
+    }
   }
-  return x;
 }
 
 __device__ __forceinline__ void make_transpose(unsigned lane, uint32_t *keep, uint32_t *rot) {
@@ -232,7 +238,8 @@ __device__ __forceinline__ uint32_t row_bulk_bytes(uint64_t S, uint32_t seg, uin
   return (uint32_t)nb;
 }
 
-// Warp 0: issue the bulk loads of group G's rows into one staging buffer.
+// Warp 0: issue the bulk loads of group G's rows into one staging buffer; the
+// buffer's mbarrier completes when all their bytes have landed.
 __device__ __forceinline__ void issue_group_loads(const TiledDev &p, const Group &G,
                                                   const uint8_t *in, uint8_t *stage,
                                                   uint64_t *mbar, unsigned lane) {
@@ -250,32 +257,109 @@ __device__ __forceinline__ void issue_group_loads(const TiledDev &p, const Group
   }
 }
 
+// Rows a warp keeps in flight at once (independent shuffle chains).
+constexpr int kRowsInFlight = 3;
+
+// Pack tile row ly of the staging buffer into a word (lane = tile; bit 8b + j
+// <- byte 4j + b of the row); 0 for lanes past the group.
+template <int kTW>
+__device__ __forceinline__ uint32_t pack_row(const TiledDev &p, const uint32_t *stage32,
+                                             uint32_t o, bool live, uint32_t valid) {
+  const uint32_t nwin = kTW ? (3u + (uint32_t)kTW + 3u) / 4u : p.nwin;
+  uint32_t acc = 0;
+  if (live) {
+    const uint32_t *w = stage32 + (o >> 2);
+    uint32_t sh = (o & 3u) * 8u;
+    uint32_t wv[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) wv[j] = (uint32_t)j < nwin ? w[j] : 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += (__funnelshift_r(wv[j], wv[j + 1], sh) & 0x01010101u) << j;
+    acc &= valid;
+  }
+  return acc;
+}
+
+// Unpack a packed row word y into bytes and write them at staging offset o;
+// a word shared with the neighbouring lane's segment is handed to the
+// right-hand lane, which merges it.
+template <int kTW>
+__device__ __forceinline__ void unpack_row(uint32_t *stage32w, uint8_t *stage, uint32_t y,
+                                           uint32_t o, uint32_t TW, unsigned lane,
+                                           uint32_t ntiles) {
+  if (TW >= 4) {
+    uint32_t shb = o & 3u, sh = shb * 8u, base = o >> 2;
+    uint32_t u[9], prev = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      uint32_t v = (y >> t) & 0x01010101u;
+      u[t] = __funnelshift_l(prev, v, sh);
+      prev = v;
+    }
+    u[8] = __funnelshift_l(prev, 0u, sh);
+    uint32_t E = (shb + TW - 1) >> 2;
+    bool partial = ((shb + TW) & 3u) != 0;
+    uint32_t last;
+    if constexpr (kTW != 0) {
+      constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
+      last = E == E0 ? u[E0] : u[E0 + 1 < 9 ? E0 + 1 : 8];
+    } else {
+      last = 0;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) last = (uint32_t)t == E ? u[t] : last;
+    }
+    uint32_t recv = __shfl_up_sync(0xFFFFFFFFu, partial ? last : 0u, 1);
+    if (lane >= 1) u[0] |= recv;
+    bool give = partial && lane + 1 < ntiles;
+    if (lane < ntiles) {
+      if constexpr (kTW != 0) {
+        constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
+#pragma unroll
+        for (uint32_t t = 0; t < E0; ++t) stage32w[base + t] = u[t];
+        if (E > E0 || !give) stage32w[base + E0] = u[E0];
+        if (E0 + 1 < 9 && E > E0 && !give) stage32w[base + E0 + 1] = u[E0 + 1 < 9 ? E0 + 1 : 8];
+      } else {
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+          if ((uint32_t)t < E || ((uint32_t)t == E && !give)) stage32w[base + t] = u[t];
+      }
+    }
+  } else if (lane < ntiles) {
+    for (uint32_t bb = 0; bb < TW; ++bb) {
+      uint32_t L = 8u * (bb & 3u) + (bb >> 2);
+      stage[o + bb] = (uint8_t)((y >> L) & 1u);
+    }
+  }
+}
+
 // The kernel is instantiated for the common tile-row widths so that the word
 // counts of a row are compile-time constants; kTW = 0 takes TW at run time.
 //
 // Work split inside a CTA (persistent over groups of 32 tiles): warp w owns
 // rows ly = w, w + nw, ... of every group, from packing through the rule to
-// the write-back, so only two CTA barriers separate groups: one before the
-// words of a group are written (the previous group is done reading them) and
-// one before the rule reads them.  Warp w also resolves directions j = w,
-// w + nw, ... of the tiles' adjacent tiles and gathers their halo words.
-// While group i is processed in staging buffer i % 2, warp 0 has already
-// issued the bulk loads of group i + 1 into the other buffer.
+// the write-back, and keeps kRowsInFlight of them in flight.  The word array
+// is double-buffered by group, so one CTA barrier per group suffices (before
+// the rule reads the words): a warp that passed it knows every warp finished
+// the group before, whose word buffer and staging buffer may then be reused.
+// Warp w also resolves directions j = w, w + nw, ... of the tiles' adjacent
+// tiles and gathers their halo words.  While group i is processed in staging
+// buffer i % 2, the bulk loads of group i + 1 land in the other one.
 template <bool kLife, int kTW>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
-  const uint32_t nwin = kTW ? (3u + (uint32_t)kTW + 3u) / 4u : p.nwin;
-  // Shared-memory carve-up; `win` sits at offset 0 so that the neighbour
-  // references can be stored as byte offsets.
-  uint32_t *win = reinterpret_cast<uint32_t *>(smem);                        // slots + nhalo + 1
-  size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
+  // Shared-memory carve-up; each word buffer starts at a multiple of 16 bytes
+  // and holds slots + nhalo + 1 words, referenced by byte offset.
+  const size_t win_bytes = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
+  size_t off = 2 * win_bytes;
   uint32_t *hoff = reinterpret_cast<uint32_t *>(smem + off);                 // nhalo
   off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + off);                 // 2
   off += 16;
+  uint8_t *rowa = smem + off;                                                // 2 * TH
+  off += ((size_t)2 * p.TH + 15) & ~(size_t)15;
   const size_t stage_bytes = (size_t)p.TH * p.pitch + 64;
   uint8_t *stage_base = smem + off;                                          // 2 * stage_bytes
 
@@ -285,7 +369,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   make_transpose(lane, keep, rot);
   for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
   if (tid == 0) {
-    win[slots + nhalo] = 0u;  // the "no neighbour" word
+    reinterpret_cast<uint32_t *>(smem)[slots + nhalo] = 0u;  // "no neighbour" words
+    reinterpret_cast<uint32_t *>(smem + win_bytes)[slots + nhalo] = 0u;
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -300,19 +385,17 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   uint32_t it = 0;
   for (uint64_t g = blockIdx.x; g < p.groups; g += gridDim.x, ++it) {
     const uint32_t b = it & 1u;
+    unsigned char *wbase = smem + b * win_bytes;
+    uint32_t *win = reinterpret_cast<uint32_t *>(wbase);
     uint8_t *stage = stage_base + b * stage_bytes;
     const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
     uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
     const Group G = group_at(p, TW, g);
     const uint32_t ntiles = G.ntiles, seg = G.seg;
 
-    // Barrier 1: every warp's bulk stores of the previous group have finished
-    // reading their staging rows, and every warp is done reading `win`.
+    // This warp's bulk stores of the previous group must finish reading the
+    // other staging buffer before the CTA barrier below lets it be refilled.
     bulk_wait_read();
-    __syncthreads();
-    if (warp == 0 && g + gridDim.x < p.groups)
-      issue_group_loads(p, group_at(p, TW, g + gridDim.x), in, stage_base + (b ^ 1u) * stage_bytes,
-                        &mbar[b ^ 1u], lane);
 
     // Adjacent tiles (precomputed table) and halo words, one direction per warp.
     for (uint32_t j = warp; j < p.ndirs; j += nw) {
@@ -349,97 +432,101 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
       __syncwarp();
     }
 
-    // Pack each own tile row into a word (lane = tile; bit 8b + j <- byte
-    // 4j + b) and transpose so that lane L holds local cell (ly, lx(L)) of
-    // all 32 tiles.
-    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
-      uint32_t acc = 0;
-      if (lane < ntiles) {
-        uint32_t o = ly * p.pitch + (((uint32_t)G.row0 + ly * (uint32_t)W) & 15u) + lane * TW;
-        const uint32_t *w = stage32 + (o >> 2);
-        uint32_t sh = (o & 3u) * 8u;
-        uint32_t wv[9];
+    // Pack the own tile rows into words (lane = tile) and transpose them so
+    // that lane L holds local cell (ly, lx(L)) of all 32 tiles.
+    for (uint32_t ly0 = warp; ly0 < p.TH; ly0 += kRowsInFlight * nw) {
+      uint32_t acc[kRowsInFlight];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) wv[j] = (uint32_t)j < nwin ? w[j] : 0u;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          acc += (__funnelshift_r(wv[j], wv[j + 1], sh) & 0x01010101u) << j;
-        acc &= valid;
+      for (int k = 0; k < kRowsInFlight; ++k) {
+        const uint32_t ly = ly0 + k * nw;
+        const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+        if (lane == 0 && ly < p.TH) rowa[b * p.TH + ly] = (uint8_t)a;
+        acc[k] = pack_row<kTW>(p, stage32, ly * p.pitch + a + lane * TW, ly < p.TH && lane < ntiles,
+                               valid);
       }
-      win[ly * 32u + lane] = transpose32(acc, keep, rot);
+      transpose32_n<kRowsInFlight>(acc, keep, rot);
+#pragma unroll
+      for (int k = 0; k < kRowsInFlight; ++k)
+        if (ly0 + k * nw < p.TH) win[(ly0 + k * nw) * 32u + lane] = acc[k];
     }
-    // Barrier 2: all words of the group (rows and halo) are in place.
+    // The only CTA barrier of the group: all words (rows and halo) are in
+    // place, and every warp has finished the previous group.
     __syncthreads();
+    if (warp == 0 && g + gridDim.x < p.groups)
+      issue_group_loads(p, group_at(p, TW, g + gridDim.x), in, stage_base + (b ^ 1u) * stage_bytes,
+                        &mbar[b ^ 1u], lane);
 
     // Rule, inverse transpose and write-back of the own rows.
-    for (uint32_t ly = warp; ly < p.TH; ly += nw) {
-      const uint32_t c = ly * 32u + lane;
-      uint32_t n[8];
+    for (uint32_t ly0 = warp; ly0 < p.TH; ly0 += kRowsInFlight * nw) {
+      uint32_t y[kRowsInFlight];
 #pragma unroll
-      for (int d = 0; d < 8; ++d)
-        n[d] = *reinterpret_cast<const uint32_t *>(smem + __ldg(p.refs + d * slots + c));
-      const uint32_t next = rule_word<kLife>(p.rule, win[c], n);
-      uint32_t y = transpose32(next, keep, rot) & valid;
-      const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
-      uint32_t o = ly * p.pitch + a + lane * TW;
-      if (TW >= 4) {
-        uint32_t shb = o & 3u, sh = shb * 8u, base = o >> 2;
-        uint32_t u[9], prev = 0;
+      for (int k = 0; k < kRowsInFlight; ++k) {
+        const uint32_t c = (ly0 + k * nw) * 32u + lane;
+        uint32_t next = 0;
+        if (ly0 + k * nw < p.TH) {
+          const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(p.refs) + c);
+          const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
+          uint32_t n[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          uint32_t v = (y >> t) & 0x01010101u;
-          u[t] = __funnelshift_l(prev, v, sh);
-          prev = v;
-        }
-        u[8] = __funnelshift_l(prev, 0u, sh);
-        uint32_t E = (shb + TW - 1) >> 2;
-        bool partial = ((shb + TW) & 3u) != 0;
-        uint32_t last;
-        if constexpr (kTW != 0) {
-          constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
-          last = E == E0 ? u[E0] : u[E0 + 1 < 9 ? E0 + 1 : 8];
-        } else {
-          last = 0;
-#pragma unroll
-          for (int t = 0; t < 9; ++t) last = (uint32_t)t == E ? u[t] : last;
-        }
-        uint32_t recv = __shfl_up_sync(0xFFFFFFFFu, partial ? last : 0u, 1);
-        if (lane >= 1) u[0] |= recv;
-        bool give = partial && lane + 1 < ntiles;
-        if (lane < ntiles) {
-          if constexpr (kTW != 0) {
-            constexpr uint32_t E0 = kTW > 0 ? ((uint32_t)kTW - 1u) >> 2 : 0u;
-#pragma unroll
-            for (uint32_t t = 0; t < E0; ++t) stage32w[base + t] = u[t];
-            if (E > E0 || !give) stage32w[base + E0] = u[E0];
-            if (E0 + 1 < 9 && E > E0 && !give) stage32w[base + E0 + 1] = u[E0 + 1 < 9 ? E0 + 1 : 8];
-          } else {
-#pragma unroll
-            for (int t = 0; t < 9; ++t)
-              if ((uint32_t)t < E || ((uint32_t)t == E && !give)) stage32w[base + t] = u[t];
+          for (int d = 0; d < 4; ++d) {
+            n[2 * d] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4410));
+            n[2 * d + 1] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4432));
           }
+          next = rule_word<kLife>(p.rule, win[c], n);
         }
-      } else if (lane < ntiles) {
-        for (uint32_t bb = 0; bb < TW; ++bb) {
-          uint32_t L = 8u * (bb & 3u) + (bb >> 2);
-          stage[o + bb] = (uint8_t)((y >> L) & 1u);
-        }
+        y[k] = next;
       }
-      // Write the row: one bulk store for its whole 16-byte chunks
-      // [head, mid_end) and single bytes for the ragged ends (they share a
-      // chunk with a neighbouring group).
+      transpose32_n<kRowsInFlight>(y, keep, rot);
+      uint32_t arow[kRowsInFlight];
+#pragma unroll
+      for (int k = 0; k < kRowsInFlight; ++k) {
+        const uint32_t ly = ly0 + k * nw;
+        arow[k] = ly < p.TH ? rowa[b * p.TH + ly] : 0u;
+        if (ly < p.TH)
+          unpack_row<kTW>(stage32w, stage, y[k] & valid, ly * p.pitch + arow[k] + lane * TW, TW,
+                          lane, ntiles);
+      }
+      // Write the rows: one bulk store per row for its whole 16-byte chunks
+      // [head, mid_end) (lane k issues row k) and, for each ragged end (they
+      // share a chunk with a neighbouring group), up to four aligned pieces
+      // of 8/4/2/1 bytes (lane 2k + side).
       fence_async_smem();
       __syncwarp();
-      const uint32_t head = (16u - a) & 15u, mid_end = seg - ((a + seg) & 15u);
-      const bool split = head < mid_end && seg >= head;
-      const uint64_t S = G.row0 + (uint64_t)ly * W;
-      if (lane == 0 && split) {
-        bulk_store(out + S + head, stage + ly * p.pitch + a + head, mid_end - head);
-        bulk_commit();
+      if (lane < 3u * kRowsInFlight) {  // lanes [0, R): bulk stores; [R, 3R): edges
+        const uint32_t k = lane < (uint32_t)kRowsInFlight ? lane : (lane - kRowsInFlight) >> 1;
+        const uint32_t ly = ly0 + k * nw;
+        if (ly < p.TH) {
+          const uint32_t a = rowa[b * p.TH + ly];
+          const uint32_t head = (16u - a) & 15u, mid_end = seg - ((a + seg) & 15u);
+          const bool split = head < mid_end && seg >= head;
+          uint8_t *g0 = out + G.row0 + (uint64_t)ly * W;  // the row segment in HBM
+          const uint8_t *s0 = stage + ly * p.pitch + a;     // and in staging (same alignment)
+          if (lane < (uint32_t)kRowsInFlight) {
+            if (split) bulk_store(g0 + head, s0 + head, mid_end - head);
+          } else {
+            // side 0: [0, head) or the whole segment when there is no middle;
+            // side 1: [mid_end, seg).
+            const bool side = (lane - kRowsInFlight) & 1u;
+            uint32_t lo = side ? mid_end : 0u, hi = side ? seg : (split ? head : seg);
+            if (side && !split) hi = lo = 0;
+            while (lo < hi) {
+              const uint32_t n = hi - lo, al = (a + lo);
+              if ((al & 1u) || n < 2) { g0[lo] = s0[lo]; lo += 1; }
+              else if ((al & 2u) || n < 4) {
+                *reinterpret_cast<uint16_t *>(g0 + lo) = *reinterpret_cast<const uint16_t *>(s0 + lo);
+                lo += 2;
+              } else if ((al & 4u) || n < 8) {
+                *reinterpret_cast<uint32_t *>(g0 + lo) = *reinterpret_cast<const uint32_t *>(s0 + lo);
+                lo += 4;
+              } else {
+                *reinterpret_cast<uint2 *>(g0 + lo) = *reinterpret_cast<const uint2 *>(s0 + lo);
+                lo += 8;
+              }
+            }
+          }
+        }
       }
-      uint32_t ob = lane < 16u || !split ? lane : mid_end + lane - 16u;
-      bool mine = split ? (lane < 16u ? lane < head : ob < seg) : lane < seg;
-      if (mine) out[S + ob] = stage[ly * p.pitch + a + ob];
+      if (lane < (uint32_t)kRowsInFlight) bulk_commit();
     }
   }
   bulk_wait_all();
@@ -491,9 +578,10 @@ uint64_t ipow(uint64_t b, uint32_t e) {
 }
 
 size_t smem_for(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
-  size_t off = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
+  size_t off = 2 * ((((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15);
   off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
   off += 16;
+  off += ((size_t)2 * TH + 15) & ~(size_t)15;
   off += 2 * ((size_t)TH * pitch + 64);  // two staging buffers (+ slack for whole-word reads)
   return off;
 }
@@ -580,15 +668,44 @@ bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
 // stays within kTiledSmemCap (so that several CTAs share an SM).
 int sq_tiled_default_level(const squeeze_handle *h) { return sq_tiled_default_level_for(h->f); }
 
+// Number of distinct halo references (direction, cell of the adjacent block)
+// of the level-L program.
+uint32_t count_halo(const FracDev &f, uint32_t L) {
+  uint32_t TW = (uint32_t)ipow(f.k, (L + 1) / 2), TH = (uint32_t)ipow(f.k, L / 2);
+  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L);
+  std::vector<int32_t> inv((size_t)side * side, -1);
+  std::vector<uint32_t> X(cells), Y(cells);
+  for (uint32_t c = 0; c < cells; ++c) {
+    local_lambda(f, L, c % TW, c / TW, X[c], Y[c]);
+    inv[(size_t)Y[c] * side + X[c]] = (int32_t)c;
+  }
+  std::vector<uint8_t> seen((size_t)9 * cells, 0);
+  uint32_t n = 0;
+  for (uint32_t c = 0; c < cells; ++c)
+    for (int d = 0; d < 9; ++d) {
+      int64_t qx = (int64_t)X[c] + d % 3 - 1, qy = (int64_t)Y[c] + d / 3 - 1;
+      int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
+      if (bx == 0 && by == 0) continue;
+      int32_t t = inv[(size_t)(qy - (int64_t)by * side) * side + (qx - (int64_t)bx * side)];
+      if (t < 0) continue;
+      uint8_t &m = seen[(size_t)((by + 1) * 3 + (bx + 1)) * cells + t];
+      if (!m) {
+        m = 1;
+        ++n;
+      }
+    }
+  return n;
+}
+
+size_t sq_tiled_smem_cap() { return kTiledSmemCap; }
+
 int sq_tiled_default_level_for(const FracDev &f) {
   int best = -1;
   for (uint32_t L = 1; L <= f.r; ++L) {
-    uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2);
-    if (TW > 32 || TH > 4096) break;
+    uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2), side = ipow(f.s, L);
+    if (TW > 32 || TH > 4096 || side * side > (1ull << 24)) break;
     uint32_t slots = (uint32_t)TH * 32;
-    // halo slots are bounded by 4 edges of s^L cells plus corners
-    size_t sm = smem_for(slots, 4u * (uint32_t)ipow(f.s, L) + 8u, (uint32_t)TH,
-                         pitch_for((uint32_t)TW));
+    size_t sm = smem_for(slots, count_halo(f, L), (uint32_t)TH, pitch_for((uint32_t)TW));
     if (sm <= kTiledSmemCap) best = (int)L;
   }
   return best;
@@ -664,12 +781,12 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   // keys in sorted order
   uint64_t *sorted = B.halo_sorted;
   for (uint32_t i = 0; i < nhalo; ++i) sorted[B.rank[i]] = B.halo_key[i];
-  // References are byte offsets into the word array, stored d-major.
+  // References are byte offsets into the word array, 8 per slot (16 bytes).
   if (((uint64_t)slots + nhalo + 1) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
   for (uint32_t c = 0; c < slots; ++c)
     for (uint32_t d = 0; d < 8; ++d) {
       uint32_t r = refs[(size_t)c * 8 + d];
-      B.refs16[(size_t)d * slots + c] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
+      B.refs16[(size_t)c * 8 + d] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
     }
   uint32_t dir_mask = 0;
   for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(sorted[i] >> 32);
@@ -710,23 +827,22 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   return SQUEEZE_OK;
 }
 
-// Shared-memory opt-in and the persistent grid (CTAs per SM x SMs).
+// Shared-memory opt-in and the persistent grid (CTAs per SM x SMs), per
+// instantiation (the generic-rule kernel may fit fewer CTAs per SM).
 int sq_tile_launch_config(TileSpec &sp, int device) {
-  int per_sm = 0, sms = 0;
-  cudaError_t e = cudaSuccess;
-  for (int life = 0; life < 2 && e == cudaSuccess; ++life) {
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return sq_cuda_fail(e);
+  for (int life = 0; life < 2; ++life) {
     const void *fn = tiled_kernel_for(life != 0, sp.TW);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
     int n = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
-    per_sm = life ? (n < per_sm ? n : per_sm) : n;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
+    if (e != cudaSuccess) return sq_cuda_fail(e);
+    if (n < 1) return SQUEEZE_ERR_UNSUPPORTED;
+    uint64_t grid = (uint64_t)n * sms;
+    (life ? sp.grid : sp.grid_rule) = (int)(grid < sp.groups ? grid : sp.groups);
   }
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (e != cudaSuccess) return sq_cuda_fail(e);
-  if (per_sm < 1) return SQUEEZE_ERR_UNSUPPORTED;
-  uint64_t grid = (uint64_t)per_sm * sms;
-  sp.grid = (int)(grid < sp.groups ? grid : sp.groups);
   return SQUEEZE_OK;
 }
 
@@ -744,8 +860,8 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
   void *args[] = {&dd, &in, &out};
-  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW), dim3(sp.grid), dim3(sp.threads), args,
-                           sp.smem, st));
+  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW), dim3(life ? sp.grid : sp.grid_rule),
+                           dim3(sp.threads), args, sp.smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }
