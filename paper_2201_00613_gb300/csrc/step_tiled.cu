@@ -183,7 +183,10 @@ __device__ __forceinline__ void fence_async_smem() {
 // 32x32 bit transposes across a warp: on return lane j holds the word whose
 // bit i was bit j of lane i's input.  Five butterfly stages; keep[] / rot[]
 // are the per-lane masks and rotations of each stage (see make_transpose).
-// kN independent transposes with their shuffle stages interleaved.
+// kN independent transposes with their shuffle stages interleaved.  The two
+// byte-granular stages (distance 16 and 8) are single byte permutes with
+// per-lane selectors keep[0], keep[1]; the bit-granular ones rotate the
+// partner's word and merge under a per-lane mask.
 template <int kN>
 __device__ __forceinline__ void transpose32_n(uint32_t *x, const uint32_t *keep,
                                               const uint32_t *rot) {
@@ -194,8 +197,12 @@ __device__ __forceinline__ void transpose32_n(uint32_t *x, const uint32_t *keep,
     for (int k = 0; k < kN; ++k) y[k] = __shfl_xor_sync(0xFFFFFFFFu, x[k], 16 >> s);
 #pragma unroll
     for (int k = 0; k < kN; ++k) {
-      uint32_t t = __funnelshift_l(y[k], y[k], rot[s]);
-      x[k] = (x[k] & keep[s]) | (t & ~keep[s]);
+      if (s < 2) {
+        x[k] = __byte_perm(x[k], y[k], keep[s]);
+      } else {
+        uint32_t t = __funnelshift_l(y[k], y[k], rot[s]);
+        x[k] = (x[k] & keep[s]) | (t & ~keep[s]);
+      }
     }
   }
 }
@@ -209,6 +216,11 @@ __device__ __forceinline__ void make_transpose(unsigned lane, uint32_t *keep, ui
     keep[s] = upper ? ~m[s] : m[s];
     rot[s] = upper ? 32u - j : j;
   }
+  // Byte-permute selectors: the lower lane of a pair keeps its own low
+  // half (byte) and takes the partner's low half up; the upper lane takes the
+  // partner's high half down and keeps its own high half.
+  keep[0] = (lane & 16u) ? 0x3276u : 0x5410u;
+  keep[1] = (lane & 8u) ? 0x3715u : 0x6240u;
 }
 
 // Geometry of one group of tiles: band ty, first tile tx0, tile count and the
