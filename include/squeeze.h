@@ -171,6 +171,48 @@ int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
 int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_t *d_state,
                           void *stream);
 
+/* ---- batched steps over many fractals -------------------------------------
+ * A batch steps many independent instances (any mix of NBB fractals and
+ * levels, each with its own handle, rule and buffer pair) together: one CA
+ * step of all of them is a single launch of a persistent kernel whose CTAs
+ * walk a cell-balanced schedule of (instance, group range) entries.  The
+ * paper has no batched form; its step (Sec. 3.2, Sec. 4) is applied to each
+ * instance unchanged, so every result equals the instance's own
+ * squeeze_step with SQUEEZE_STEP_TILED. */
+typedef struct squeeze_batch squeeze_batch;
+typedef struct {
+  squeeze_handle *h;  /* the instance's fractal, level and rule */
+  uint8_t *d_buf0;    /* k^r bytes, 16-byte aligned: the state (even steps) */
+  uint8_t *d_buf1;    /* k^r bytes, 16-byte aligned, not overlapping d_buf0 */
+} squeeze_batch_item;
+
+/* squeeze_batch_create -- validate the items, prepare every handle's tiled
+ * program, build the schedule and copy the descriptors to the device.  The
+ * handles' rules and tile levels are read now: later changes need a new
+ * batch.  The handles and buffers must outlive the batch. */
+int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out);
+
+/* squeeze_batch_configure -- launch shape chosen by the autotuner: threads per
+ * CTA (multiple of 32, 64..288), CTAs per SM (0 = as many as fit) and whether
+ * squeeze_batch_run replays a captured CUDA graph (1) or launches directly. */
+int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_per_sm,
+                            int use_graph);
+
+/* squeeze_batch_info -- the resulting grid, CTA size and shared memory. */
+int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads,
+                       uint32_t *smem_bytes);
+
+/* squeeze_batch_run -- n_steps steps of every instance on `stream`, one
+ * launch per step; with graphs on, the n_steps launches are captured once
+ * (per distinct n_steps and starting buffer) and replayed.  The batch keeps
+ * the step count across calls: every instance's state is in d_buf0 after an
+ * even total number of steps since squeeze_batch_create and in d_buf1 after
+ * an odd one. */
+int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream);
+
+/* squeeze_batch_destroy -- free the batch (not the handles or buffers). */
+int squeeze_batch_destroy(squeeze_batch *b);
+
 /* ---- allocation-free step ------------------------------------------------- */
 
 /* squeeze_step_noalloc -- one tiled step (as squeeze_step with

@@ -69,6 +69,13 @@ _SIGS = {
                          ctypes.c_void_p], ctypes.c_int),
     "squeeze_bb_to_compact": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p], ctypes.c_int),
+    "squeeze_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)],
+                             ctypes.c_int),
+    "squeeze_batch_configure": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
+                                ctypes.c_int),
+    "squeeze_batch_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_uint32)] * 3, ctypes.c_int),
+    "squeeze_batch_run": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
@@ -214,6 +221,39 @@ def squeeze_bb_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
 def squeeze_bb_to_compact(h, d_grid, d_state, stream=None):
     _check(_load().squeeze_bb_to_compact(h, _ptr(d_grid), _ptr(d_state), _stream(stream)),
            "squeeze_bb_to_compact")
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("d_buf0", ctypes.c_void_p), ("d_buf1", ctypes.c_void_p)]
+
+
+def squeeze_batch_create(items):
+    """items: sequence of (handle, d_buf0, d_buf1); returns the batch pointer."""
+    arr = (_BatchItem * len(items))(*[_BatchItem(h, _ptr(a), _ptr(b)) for h, a, b in items])
+    out = ctypes.c_void_p()
+    _check(_load().squeeze_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                        ctypes.byref(out)), "squeeze_batch_create")
+    return out.value
+
+
+def squeeze_batch_configure(b, threads: int, ctas_per_sm: int = 0, use_graph: bool = True):
+    _check(_load().squeeze_batch_configure(b, threads, ctas_per_sm, int(use_graph)),
+           "squeeze_batch_configure")
+
+
+def squeeze_batch_info(b):
+    """(grid, threads per CTA, shared-memory bytes per CTA)."""
+    v = [ctypes.c_uint32() for _ in range(3)]
+    _check(_load().squeeze_batch_info(b, *[ctypes.byref(x) for x in v]), "squeeze_batch_info")
+    return tuple(int(x.value) for x in v)
+
+
+def squeeze_batch_run(b, n_steps: int, stream=None):
+    _check(_load().squeeze_batch_run(b, n_steps, _stream(stream)), "squeeze_batch_run")
+
+
+def squeeze_batch_destroy(b):
+    _check(_load().squeeze_batch_destroy(b), "squeeze_batch_destroy")
 
 
 def squeeze_step_noalloc(s: int, k: int, offsets, r: int, birth: int, survive: int,

@@ -147,7 +147,8 @@ __device__ __host__ inline uint8_t bernoulli_cell(uint64_t seed, uint32_t p_q24,
 
 // Kernel-side description of a tiled-step program (see step_tiled.cu).
 struct TiledDev {
-  FracDev f;
+  uint64_t W;                // compact row length (bytes)
+  uint64_t total;            // k^r, bytes of a state buffer
   Rule rule;
   uint32_t L, TW, TH, cells, nhalo, dir_mask, slots;
   uint32_t valid;            // packed-word bits that hold a real cell (lx < TW)
@@ -159,11 +160,21 @@ struct TiledDev {
   uint32_t halo_start[10];   // halo slots of direction j: [halo_start[j], halo_start[j+1])
   uint64_t tiles;            // tiles_x * tiles_y
   FastDiv div_tw, div_gpb, div_tiles_x;
-  const uint16_t *refs;      // 8 x slots byte offsets of the neighbour words
+  const uint16_t *refs;      // slots x 8 byte offsets of the neighbour words
   const uint32_t *halo_off;  // nhalo byte offsets inside a tile
   const uint8_t *halo_dir;   // nhalo direction indices
   const uint32_t *adj;       // ndirs x tiles adjacent tile indices (~0: none)
   int *status;
+};
+
+// Shared-memory layout of one launch of the tiled kernel (uniform over the
+// instances of a batched launch: the maxima of their needs).
+struct TileLayout {
+  uint32_t win_bytes;        // one word buffer (two are used)
+  uint32_t hoff_bytes;       // halo offsets
+  uint32_t rowa_bytes;       // per-row alignment offsets (two sets)
+  uint32_t stage_bytes;      // one staging buffer (two are used)
+  uint32_t smem;             // total dynamic shared memory
 };
 
 // Geometry and launch shape of a tiled-step program, independent of where its
@@ -196,6 +207,15 @@ struct TileBuild {
   uint32_t *halo_off;
   uint8_t *halo_dir;
   uint64_t box_cap, cells_cap, slots_cap, halo_cap;
+};
+
+// One entry of a batched launch's schedule: CTA c processes entries
+// [sched_start[c], sched_start[c + 1]), each a contiguous range of groups of
+// one instance.
+struct BatchWork {
+  uint32_t instance;
+  uint32_t pad;
+  uint64_t g_first, g_end;
 };
 
 inline unsigned grid_for(uint64_t items, unsigned block, unsigned cap = 152u * 16u) {
@@ -252,9 +272,20 @@ int sq_tile_launch_config(sq::TileSpec &sp, int device);
 sq::TiledDev sq_tiled_dev(const sq::FracDev &f, const sq::Rule &rule, const sq::TileSpec &sp,
                           const uint16_t *refs, const uint32_t *halo_off,
                           const uint8_t *halo_dir, const uint32_t *adj, int *status);
-int sq_tile_build_adjacency(const sq::TiledDev &d, uint32_t *adj, cudaStream_t st);
+sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch);
+sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
+int sq_tile_build_adjacency(const sq::FracDev &f, const sq::TiledDev &d, uint32_t *adj,
+                            cudaStream_t st);
 int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t *in,
                    uint8_t *out, cudaStream_t st);
+// The handle's prepared tiled program (sq_tiled_prepare first).
+int sq_tiled_describe(const squeeze_handle *h, sq::TiledDev *d, sq::TileSpec *sp);
+// CTAs per SM of the batched kernel instance for this shape (0 if it cannot run).
+int sq_batch_occupancy(bool life, uint32_t TW, int threads, uint32_t smem);
+int sq_batch_launch(const sq::TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
+                    const sq::BatchWork *d_work, const uint32_t *d_sched,
+                    const sq::TileLayout &lay, int grid, int threads, bool life, uint32_t TW,
+                    uint32_t parity, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,

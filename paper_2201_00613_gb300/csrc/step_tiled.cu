@@ -82,13 +82,12 @@ __device__ __forceinline__ uint32_t rule_word(const Rule &rule, uint32_t self, c
 // Carry walk: the level-L block adjacent to tile (tx, ty) in direction
 // (dx, dy), as a tile (ntx, nty), or false for a hole / off the box.  Tile
 // coordinates fit 32 bits, so the digit updates use wrap-around arithmetic.
-__device__ bool adjacent_tile(const TiledDev &p, const uint8_t *taux, const uint8_t *tauy,
-                              const uint8_t *hnu, uint32_t tx, uint32_t ty, int dx, int dy,
-                              uint32_t &ntx, uint32_t &nty) {
-  const FracDev &f = p.f;
+__device__ bool adjacent_tile(const FracDev &f, uint32_t L, const uint8_t *taux,
+                              const uint8_t *tauy, const uint8_t *hnu, uint32_t tx, uint32_t ty,
+                              int dx, int dy, uint32_t &ntx, uint32_t &nty) {
   int cx = dx, cy = dy;
   uint32_t qx = tx, qy = ty, pwx = 1, pwy = 1, ax = tx, ay = ty;
-  for (uint32_t mu = p.L + 1; mu <= f.r && (cx | cy); ++mu) {
+  for (uint32_t mu = L + 1; mu <= f.r && (cx | cy); ++mu) {
     bool odd = mu & 1u;
     uint32_t src = odd ? qx : qy;
     uint32_t q = fdiv(f.divk, src);
@@ -236,7 +235,7 @@ __device__ __forceinline__ Group group_at(const TiledDev &p, uint32_t TW, uint64
   G.tx0 = ((uint32_t)g - G.ty * p.groups_per_band) * 32u;
   G.ntiles = min(32u, p.tiles_x - G.tx0);
   G.seg = G.ntiles * TW;
-  G.row0 = (uint64_t)G.ty * p.TH * p.f.W + (uint64_t)G.tx0 * TW;
+  G.row0 = (uint64_t)G.ty * p.TH * p.W + (uint64_t)G.tx0 * TW;
   return G;
 }
 
@@ -255,7 +254,7 @@ __device__ __forceinline__ uint32_t row_bulk_bytes(uint64_t S, uint32_t seg, uin
 __device__ __forceinline__ void issue_group_loads(const TiledDev &p, const Group &G,
                                                   const uint8_t *in, uint8_t *stage,
                                                   uint64_t *mbar, unsigned lane) {
-  const uint64_t W = p.f.W, total = p.f.cells;
+  const uint64_t W = p.W, total = p.total;
   uint32_t bytes = 0;
   for (uint32_t ly = lane; ly < p.TH; ly += 32)
     bytes += row_bulk_bytes(G.row0 + (uint64_t)ly * W, G.seg, total);
@@ -344,58 +343,82 @@ __device__ __forceinline__ void unpack_row(uint32_t *stage32w, uint8_t *stage, u
   }
 }
 
-// The kernel is instantiated for the common tile-row widths so that the word
+// Shared-memory carve-up of the tiled kernel (offsets in bytes; every region
+// starts at a multiple of 16): two word buffers, halo offsets, 2 mbarriers,
+// two sets of row offsets, two staging buffers.
+struct SmemPtrs {
+  unsigned char *win0;
+  uint32_t *hoff;
+  uint64_t *mbar;
+  uint8_t *rowa;
+  uint8_t *stage0;
+};
+
+__device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout &lay) {
+  SmemPtrs q;
+  size_t off = 0;
+  q.win0 = smem;
+  off += 2 * (size_t)lay.win_bytes;
+  q.hoff = reinterpret_cast<uint32_t *>(smem + off);
+  off += lay.hoff_bytes;
+  q.mbar = reinterpret_cast<uint64_t *>(smem + off);
+  off += 16;
+  q.rowa = smem + off;
+  off += lay.rowa_bytes;
+  q.stage0 = smem + off;
+  return q;
+}
+
+// One pass of the tiled step over groups g_first, g_first + g_stride, ...
+// (< g_end) of one fractal instance, by one CTA.
+//
+// The caller is instantiated for the common tile-row widths so that the word
 // counts of a row are compile-time constants; kTW = 0 takes TW at run time.
 //
-// Work split inside a CTA (persistent over groups of 32 tiles): warp w owns
-// rows ly = w, w + nw, ... of every group, from packing through the rule to
-// the write-back, and keeps kRowsInFlight of them in flight.  The word array
-// is double-buffered by group, so one CTA barrier per group suffices (before
-// the rule reads the words): a warp that passed it knows every warp finished
-// the group before, whose word buffer and staging buffer may then be reused.
-// Warp w also resolves directions j = w, w + nw, ... of the tiles' adjacent
-// tiles and gathers their halo words.  While group i is processed in staging
-// buffer i % 2, the bulk loads of group i + 1 land in the other one.
+// Work split inside the CTA: warp w owns rows ly = w, w + nw, ... of every
+// group, from packing through the rule to the write-back, and keeps
+// kRowsInFlight of them in flight.  The word array is double-buffered by
+// group, so one CTA barrier per group suffices (before the rule reads the
+// words): a warp that passed it knows every warp finished the group before,
+// whose word buffer and staging buffer may then be reused.  Warp w also
+// resolves directions j = w, w + nw, ... of the tiles' adjacent tiles and
+// gathers their halo words.  While group i is processed in staging buffer
+// i % 2, the bulk loads of group i + 1 land in the other one.  `it` counts
+// the groups this CTA has processed (it selects buffers and mbarrier phases)
+// and carries over from one call to the next.
 template <bool kLife, int kTW>
-__global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
-    TiledDev p, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &lay,
+                                           const uint8_t *__restrict__ in,
+                                           uint8_t *__restrict__ out, uint64_t g_first,
+                                           uint64_t g_end, uint64_t g_stride,
+                                           unsigned char *smem, const uint32_t *keep,
+                                           const uint32_t *rot, uint32_t &it) {
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
-  // Shared-memory carve-up; each word buffer starts at a multiple of 16 bytes
-  // and holds slots + nhalo + 1 words, referenced by byte offset.
-  const size_t win_bytes = (((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15;
-  size_t off = 2 * win_bytes;
-  uint32_t *hoff = reinterpret_cast<uint32_t *>(smem + off);                 // nhalo
-  off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + off);                 // 2
-  off += 16;
-  uint8_t *rowa = smem + off;                                                // 2 * TH
-  off += ((size_t)2 * p.TH + 15) & ~(size_t)15;
-  const size_t stage_bytes = (size_t)p.TH * p.pitch + 64;
-  uint8_t *stage_base = smem + off;                                          // 2 * stage_bytes
+  const SmemPtrs q = carve(smem, lay);
+  const size_t win_bytes = lay.win_bytes, stage_bytes = lay.stage_bytes;
+  uint32_t *hoff = q.hoff;
+  uint64_t *mbar = q.mbar;
+  uint8_t *rowa = q.rowa;
+  uint8_t *stage_base = q.stage0;
 
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const unsigned nthreads = blockDim.x, nw = nthreads >> 5;
-  uint32_t keep[5], rot[5];
-  make_transpose(lane, keep, rot);
+  __syncthreads();  // the previous call (another instance) is done with every buffer
   for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
   if (tid == 0) {
     reinterpret_cast<uint32_t *>(smem)[slots + nhalo] = 0u;  // "no neighbour" words
     reinterpret_cast<uint32_t *>(smem + win_bytes)[slots + nhalo] = 0u;
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  __syncthreads();
-  const uint64_t total = p.f.cells, W = p.f.W;
+  __syncthreads();  // halo offsets and zero words in place
+  const uint64_t total = p.total, W = p.W;
   const uint32_t valid = p.valid;
 
-  if (warp == 0 && blockIdx.x < p.groups)
-    issue_group_loads(p, group_at(p, TW, blockIdx.x), in, stage_base, &mbar[0], lane);
+  if (warp == 0 && g_first < g_end)
+    issue_group_loads(p, group_at(p, TW, g_first), in, stage_base + (it & 1u) * stage_bytes,
+                      &mbar[it & 1u], lane);
 
-  uint32_t it = 0;
-  for (uint64_t g = blockIdx.x; g < p.groups; g += gridDim.x, ++it) {
+  for (uint64_t g = g_first; g < g_end; g += g_stride, ++it) {
     const uint32_t b = it & 1u;
     unsigned char *wbase = smem + b * win_bytes;
     uint32_t *win = reinterpret_cast<uint32_t *>(wbase);
@@ -464,8 +487,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     // The only CTA barrier of the group: all words (rows and halo) are in
     // place, and every warp has finished the previous group.
     __syncthreads();
-    if (warp == 0 && g + gridDim.x < p.groups)
-      issue_group_loads(p, group_at(p, TW, g + gridDim.x), in, stage_base + (b ^ 1u) * stage_bytes,
+    if (warp == 0 && g + g_stride < g_end)
+      issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
 
     // Rule, inverse transpose and write-back of the own rows.
@@ -541,17 +564,64 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
       if (lane < (uint32_t)kRowsInFlight) bulk_commit();
     }
   }
+}
+
+
+// Mbarriers of the two staging buffers, set up once per CTA.
+__device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLayout &lay) {
+  if (threadIdx.x == 0) {
+    uint64_t *mbar = carve(smem, lay).mbar;
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+}
+
+// One step of one instance; the CTAs of the persistent grid take groups
+// blockIdx.x, blockIdx.x + gridDim.x, ...
+template <bool kLife, int kTW>
+__global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
+    TiledDev p, TileLayout lay, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t keep[5], rot[5];
+  make_transpose(threadIdx.x & 31u, keep, rot);
+  init_barriers(smem, lay);
+  uint32_t it = 0;
+  run_groups<kLife, kTW>(p, lay, in, out, blockIdx.x, p.groups, gridDim.x, smem, keep, rot, it);
+  bulk_wait_all();
+}
+
+// One step of many instances (each with its own fractal, level and
+// buffers) in a single persistent launch.  parity selects the step's input:
+// buffer 0 on even steps, buffer 1 on odd ones.
+template <bool kLife, int kTW>
+__global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
+    const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
+    uint8_t *const *__restrict__ buf1, const BatchWork *__restrict__ work,
+    const uint32_t *__restrict__ sched_start, TileLayout lay, uint32_t parity) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t keep[5], rot[5];
+  make_transpose(threadIdx.x & 31u, keep, rot);
+  init_barriers(smem, lay);
+  uint32_t it = 0;
+  for (uint32_t e = sched_start[blockIdx.x]; e < sched_start[blockIdx.x + 1]; ++e) {
+    const BatchWork w = work[e];
+    const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
+    uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
+    run_groups<kLife, kTW>(devs[w.instance], lay, in, out, w.g_first, w.g_end, 1, smem, keep,
+                           rot, it);
+  }
   bulk_wait_all();
 }
 
 // One thread per (direction, tile): the adjacent tile of every tile, computed
 // once per fractal and tile level by the carry walk and kept in HBM.
-__global__ void build_adjacency_kernel(TiledDev p, uint32_t *__restrict__ adj) {
+__global__ void build_adjacency_kernel(FracDev f, TiledDev p, uint32_t *__restrict__ adj) {
   __shared__ uint8_t tab[768];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    tab[i] = p.f.taux[i];
-    tab[256 + i] = p.f.tauy[i];
-    tab[512 + i] = p.f.hnu[i];
+    tab[i] = f.taux[i];
+    tab[256 + i] = f.tauy[i];
+    tab[512 + i] = f.hnu[i];
   }
   __syncthreads();
   const uint64_t n = (uint64_t)p.ndirs * p.tiles;
@@ -562,14 +632,25 @@ __global__ void build_adjacency_kernel(TiledDev p, uint32_t *__restrict__ adj) {
     uint32_t ty = (uint32_t)(t / p.tiles_x), tx = (uint32_t)(t - (uint64_t)ty * p.tiles_x);
     uint32_t d = p.dir_list[j], ntx, nty;
     uint32_t r = ~0u;
-    if (adjacent_tile(p, tab, tab + 256, tab + 512, tx, ty, (int)(d % 3) - 1, (int)(d / 3) - 1,
-                      ntx, nty))
+    if (adjacent_tile(f, p.L, tab, tab + 256, tab + 512, tx, ty, (int)(d % 3) - 1,
+                      (int)(d / 3) - 1, ntx, nty))
       r = nty * p.tiles_x + ntx;
     adj[i] = r;
   }
 }
 
 // ---- host side: the level-L neighbour program ------------------------------
+
+const void *batch_kernel_for(bool life, uint32_t TW) {
+  if (life) {
+    if (TW == 27) return (const void *)step_batch_kernel<true, 27>;
+    if (TW == 25) return (const void *)step_batch_kernel<true, 25>;
+    return (const void *)step_batch_kernel<true, 0>;
+  }
+  if (TW == 27) return (const void *)step_batch_kernel<false, 27>;
+  if (TW == 25) return (const void *)step_batch_kernel<false, 25>;
+  return (const void *)step_batch_kernel<false, 0>;
+}
 
 const void *tiled_kernel_for(bool life, uint32_t TW) {
   if (life) {
@@ -589,13 +670,36 @@ uint64_t ipow(uint64_t b, uint32_t e) {
   return p;
 }
 
+}  // namespace
+}  // namespace sq
+
+using namespace sq;
+
+TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
+  TileLayout l;
+  l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15);
+  l.hoff_bytes = (uint32_t)(((size_t)nhalo * 4 + 15) & ~(size_t)15);
+  l.rowa_bytes = (uint32_t)(((size_t)2 * TH + 15) & ~(size_t)15);
+  l.stage_bytes = (uint32_t)((size_t)TH * pitch + 64);  // + slack for whole-word reads
+  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + 2 * l.stage_bytes;
+  return l;
+}
+
+TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
+  TileLayout l;
+  l.win_bytes = a.win_bytes > b.win_bytes ? a.win_bytes : b.win_bytes;
+  l.hoff_bytes = a.hoff_bytes > b.hoff_bytes ? a.hoff_bytes : b.hoff_bytes;
+  l.rowa_bytes = a.rowa_bytes > b.rowa_bytes ? a.rowa_bytes : b.rowa_bytes;
+  l.stage_bytes = a.stage_bytes > b.stage_bytes ? a.stage_bytes : b.stage_bytes;
+  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + 2 * l.stage_bytes;
+  return l;
+}
+
+namespace sq {
+namespace {
+
 size_t smem_for(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
-  size_t off = 2 * ((((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15);
-  off += ((size_t)nhalo * 4 + 15) & ~(size_t)15;
-  off += 16;
-  off += ((size_t)2 * TH + 15) & ~(size_t)15;
-  off += 2 * ((size_t)TH * pitch + 64);  // two staging buffers (+ slack for whole-word reads)
-  return off;
+  return sq_tile_layout(slots, nhalo, TH, pitch).smem;
 }
 
 // Staging row: up to 15 bytes of alignment offset + 32 tiles + one spare chunk.
@@ -630,7 +734,8 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
                       const uint32_t *adj, int *status) {
   TiledDev d;
   memset(&d, 0, sizeof(d));
-  d.f = f;
+  d.W = f.W;
+  d.total = f.cells;
   d.rule = rule;
   d.L = sp.L;
   d.TW = sp.TW;
@@ -858,10 +963,10 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
   return SQUEEZE_OK;
 }
 
-int sq_tile_build_adjacency(const TiledDev &d, uint32_t *adj, cudaStream_t st) {
+int sq_tile_build_adjacency(const FracDev &f, const TiledDev &d, uint32_t *adj, cudaStream_t st) {
   uint64_t n = (uint64_t)d.ndirs * d.tiles;
   if (!n) return SQUEEZE_OK;
-  build_adjacency_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, adj);
+  build_adjacency_kernel<<<grid_for(n, 256), 256, 0, st>>>(f, d, adj);
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }
@@ -871,7 +976,8 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
-  void *args[] = {&dd, &in, &out};
+  TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
+  void *args[] = {&dd, &lay, &in, &out};
   SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW), dim3(life ? sp.grid : sp.grid_rule),
                            dim3(sp.threads), args, sp.smem, st));
   SQ_CUDA(cudaGetLastError());
@@ -923,7 +1029,7 @@ int sq_tiled_prepare(squeeze_handle *h) {
   }
   TiledDev d = sq_tiled_dev(f, h->rule, sp, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
                             h->d_status);
-  rc = sq_tile_build_adjacency(d, p->d_adj, 0);
+  rc = sq_tile_build_adjacency(f, d, p->d_adj, 0);
   if (rc == SQUEEZE_OK) {
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = sq_cuda_fail(e);
@@ -944,4 +1050,34 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
   return sq_tile_launch(d, p->spec, in, out, st);
+}
+
+int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
+  const TiledProgram *p = h->tiled;
+  if (!p) return SQUEEZE_ERR_INVALID_ARG;
+  *d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
+                    h->d_status);
+  *sp = p->spec;
+  return SQUEEZE_OK;
+}
+
+int sq_batch_occupancy(bool life, uint32_t TW, int threads, uint32_t smem) {
+  const void *fn = batch_kernel_for(life, TW);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+int sq_batch_launch(const TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
+                    const BatchWork *d_work, const uint32_t *d_sched, const TileLayout &lay,
+                    int grid, int threads, bool life, uint32_t TW, uint32_t parity,
+                    cudaStream_t st) {
+  TileLayout l = lay;
+  void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity};
+  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, TW), dim3(grid), dim3(threads), args, l.smem, st));
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
 }

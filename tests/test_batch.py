@@ -1,0 +1,135 @@
+"""Batched mixed-fractal steps: every instance equals its own run, bit for bit.
+
+Instances of different NBB fractals and levels are stepped together (one
+persistent launch per step, replayed from a CUDA graph).  Each result is
+compared with the instance stepped alone through squeeze_step, and with the
+CPU oracle (full box where it fits, light-cone samples otherwise).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_00613_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2201_00613_gb300 as sq  # noqa: E402
+from paper_2201_00613_gb300.batch import MixedBatch, autotune  # noqa: E402
+
+
+def solo(inst, steps, level=None):
+    with sq.Handle(inst.fractal, inst.r) as h:
+        if level:
+            sq.squeeze_set_tiled_level(h.h, level)
+        a = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        sq.squeeze_init_bernoulli(h.h, a, inst.seed, I.p_q24(inst.p))
+        sq.squeeze_step(h.h, a, b, steps, sq.SQUEEZE_STEP_TILED)
+        torch.cuda.synchronize()
+        return (b if steps % 2 else a).clone()
+
+
+def small_mix():
+    mix = []
+    for i, (f, r) in enumerate([(I.TRIANGLE, 8), (I.CARPET, 4), (I.VICSEK, 5), (I.TRIANGLE, 11),
+                                (I.CARPET, 5), (I.VICSEK, 7), (I.TRIANGLE, 3), (I.TRIANGLE_PAPER, 9),
+                                (I.TRIANGLE, 14), (I.VICSEK, 6), (I.CARPET, 3), (I.FULL2, 6)]):
+        mix.append(I.Instance(f, r, 1000 + i))
+    return mix
+
+
+@pytest.mark.parametrize("use_graph", [True, False], ids=["graph", "direct"])
+def test_small_mix_matches_solo_and_oracle(use_graph):
+    mix = small_mix()
+    with MixedBatch(mix, use_graph=use_graph) as mb:
+        mb.run(3)
+        mb.run(4)  # 7 steps in two runs (two graphs)
+        torch.cuda.synchronize()
+        for i, inst in enumerate(mix):
+            got = mb.state(i)
+            assert torch.equal(got, solo(inst, 7)), inst
+            if inst.fractal.cells(inst.r) <= 200000 and inst.fractal.side(inst.r) <= 1024:
+                c0 = oracle.compact_init(inst.fractal, inst.r, inst.seed, I.p_q24(inst.p))
+                want = oracle.run_compact(inst.fractal, inst.r, c0, 7)
+                assert np.array_equal(got.cpu().numpy(), want), inst
+
+
+def test_batch_rule_mix_and_levels():
+    mix = small_mix()[:6]
+    handles = [sq.Handle(m.fractal, m.r) for m in mix]
+    bufs = []
+    try:
+        for j, (m, h) in enumerate(zip(mix, handles)):
+            if j % 2:
+                sq.squeeze_set_rule(h.h, (1 << 3) | (1 << 6), (1 << 2) | (1 << 3))  # HighLife
+            a = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+            b = torch.empty_like(a)
+            sq.squeeze_init_bernoulli(h.h, a, m.seed, I.p_q24(0.5))
+            bufs.append((a, b))
+        ref = [x[0].clone() for x in bufs]
+        batch = sq.squeeze_batch_create([(h.h, a, b) for h, (a, b) in zip(handles, bufs)])
+        sq.squeeze_batch_configure(batch, 192, 2, True)
+        grid, threads, smem = sq.squeeze_batch_info(batch)
+        assert threads == 192 and grid >= 1 and smem > 0
+        sq.squeeze_batch_run(batch, 5)
+        torch.cuda.synchronize()
+        for (h, (a, b), r0, m) in zip(handles, bufs, ref, mix):
+            x, y = r0.clone(), torch.empty_like(r0)
+            sq.squeeze_step(h.h, x, y, 5, sq.SQUEEZE_STEP_TILED)
+            assert torch.equal(b, y), m
+        sq.squeeze_batch_destroy(batch)
+    finally:
+        for h in handles:
+            h.close()
+
+
+def test_batch_rejects_bad_items():
+    with sq.Handle(I.TRIANGLE, 6) as h:
+        a = torch.zeros(h.cells + 16, dtype=torch.uint8, device="cuda")
+        with pytest.raises(sq.SqueezeError) as e:
+            sq.squeeze_batch_create([(h.h, a, a)])
+        assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+        with pytest.raises(sq.SqueezeError):
+            sq.squeeze_batch_create([(h.h, a[1:], a[8:])])
+
+
+def test_config4_mix_50_steps():
+    """256 instances (triangle r 8-14, carpet r 4-8, Vicsek r 5-9), 50 steps."""
+    mix = I.batch_mix(5, 256)
+    steps = 50
+    with MixedBatch(mix) as mb:
+        mb.run(steps)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(7)
+        for i, inst in enumerate(mix):
+            got = mb.state(i)
+            # every instance against its solo run on the GPU ...
+            if i % 4 == 0:
+                assert torch.equal(got, solo(inst, steps)), inst
+            # ... and against the oracle: light-cone samples of the CA after 50 steps
+            f, r = inst.fractal, inst.r
+            om = rng.integers(0, f.cells(r), size=4).astype(np.uint64)
+            xy = oracle.lam(f, r, om)
+            want = oracle.lightcone(f, r, inst.seed, I.p_q24(inst.p), steps, xy)
+            assert np.array_equal(got[torch.from_numpy(om.astype(np.int64)).cuda()].cpu().numpy(),
+                                  want), inst
+
+
+def test_autotuner_picks_a_valid_shape(tmp_path, monkeypatch):
+    from paper_2201_00613_gb300 import batch as B
+    monkeypatch.setattr(B, "_CACHE", str(tmp_path / "autotune.json"))
+    mix = small_mix()[:5]
+    res = autotune(mix)
+    assert res["threads"] in (192, 256, 288) and res["seconds_per_step"] > 0
+    again = autotune(mix)  # from the cache
+    assert again["threads"] == res["threads"] and again["levels"] == res["levels"]
+    with MixedBatch(mix, levels=res["levels"], threads=res["threads"],
+                    ctas_per_sm=res["ctas_per_sm"]) as mb:
+        mb.run(3)
+        torch.cuda.synchronize()
+        for i, inst in enumerate(mix):
+            assert torch.equal(mb.state(i), solo(inst, 3)), inst
