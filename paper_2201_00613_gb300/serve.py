@@ -1,0 +1,159 @@
+"""Request loop with continuous batching over the batched tiled step.
+
+Requests (a fractal, a level, a seed and a step count) arrive over time.  The
+loop admits an arrived request as soon as a slot is free and the device has
+room for its two state buffers (checked against the free HBM the driver
+reports, minus a reserve), seeds its state on the device, and from then on
+advances it together with every other active request: each round runs one
+batched launch per CA step (squeeze_batch_run) for the largest chunk of steps
+that no active request overshoots.  Requests that arrive while a round is on
+the GPU join at the next round boundary, so their work overlaps with that of
+the requests already running.  A finished request's state stays on the
+device; its latency is the time from arrival to the end of its last round.
+All computation runs in the CUDA library; this module only schedules.
+"""
+from __future__ import annotations
+
+import dataclasses
+import statistics
+import time
+from collections import deque
+
+import torch
+
+from . import _lib as sq
+from . import inputs as I
+
+
+@dataclasses.dataclass
+class Slot:
+    request: object
+    handle: object
+    cur: torch.Tensor     # holds the current state
+    other: torch.Tensor
+    remaining: int
+    admitted_s: float
+    done_s: float = -1.0
+
+
+class RequestLoop:
+    """Continuous-batching loop on one device."""
+
+    def __init__(self, device="cuda", max_slots=64, chunk=25, reserve_bytes=4 << 30,
+                 keep_results=False, levels=None):
+        self.device = torch.device(device)
+        self.max_slots = max_slots
+        self.chunk = chunk
+        self.reserve = reserve_bytes
+        self.keep = keep_results
+        self.levels = levels or {}
+        self.finished = []
+        self.handles = {}   # (fractal name, r) -> Handle, shared by the requests of that shape
+        self.rounds = 0
+        self.batches_built = 0
+        self.refused_for_memory = 0
+
+    def _fits(self, inst) -> bool:
+        free, _ = torch.cuda.mem_get_info(self.device)
+        need = 2 * inst.fractal.cells(inst.r) + (1 << 20)
+        return free - need >= self.reserve
+
+    def _handle(self, inst):
+        key = (inst.fractal.name, inst.r)
+        h = self.handles.get(key)
+        if h is None:
+            h = sq.Handle(inst.fractal, inst.r)
+            lvl = self.levels.get(inst.fractal.name)
+            if lvl:
+                try:
+                    sq.squeeze_set_tiled_level(h.h, min(lvl, inst.r))
+                except sq.SqueezeError:
+                    pass
+            self.handles[key] = h
+        return h
+
+    def close(self):
+        for h in self.handles.values():
+            h.close()
+        self.handles = {}
+
+    def _admit(self, req, now):
+        inst = req.instance
+        h = self._handle(inst)
+        a = torch.empty(h.cells, dtype=torch.uint8, device=self.device)
+        b = torch.empty_like(a)
+        sq.squeeze_init_bernoulli(h.h, a, inst.seed, I.p_q24(inst.p))
+        return Slot(req, h, a, b, req.n_steps, now)
+
+    def run(self, requests, max_seconds=None):
+        """Serve `requests` (sorted by arrival); returns a summary dict."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival_s))
+        active = []
+        batch, members = None, ()
+        cell_updates = 0
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            if max_seconds and now > max_seconds:
+                break
+            while pending and pending[0].arrival_s <= now and len(active) < self.max_slots:
+                if not self._fits(pending[0].instance):
+                    self.refused_for_memory += 1
+                    break
+                active.append(self._admit(pending.popleft(), now))
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival_s - now)))
+                continue
+            ids = tuple(id(s) for s in active)
+            if ids != members:
+                if batch:
+                    sq.squeeze_batch_destroy(batch)
+                batch = sq.squeeze_batch_create([(s.handle.h, s.cur, s.other) for s in active])
+                sq.squeeze_batch_configure(batch, 288, 0, False)  # round lengths vary: no graphs
+                members = ids
+                self.batches_built += 1
+            k = min(self.chunk, min(s.remaining for s in active))
+            sq.squeeze_batch_run(batch, k)
+            torch.cuda.current_stream(self.device).synchronize()
+            self.rounds += 1
+            end = time.perf_counter() - t0
+            still = []
+            for s in active:
+                s.remaining -= k
+                cell_updates += k * s.handle.cells
+                if k % 2:
+                    s.cur, s.other = s.other, s.cur
+                if s.remaining == 0:
+                    s.done_s = end
+                    self.finished.append(s)
+                else:
+                    still.append(s)
+            if len(still) != len(active):
+                # the batch's parity restarts with the next membership; buffers
+                # are passed as (current, other) again then.
+                sq.squeeze_batch_destroy(batch)
+                batch, members = None, ()
+                for s in active:
+                    if s.remaining == 0 and not self.keep:
+                        s.other = None
+                        s.cur = None
+            active = still
+        if batch:
+            sq.squeeze_batch_destroy(batch)
+        makespan = time.perf_counter() - t0
+        lat = [s.done_s - s.request.arrival_s for s in self.finished]
+        lat.sort()
+        pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+        return {
+            "requests": len(self.finished),
+            "makespan_s": makespan,
+            "cell_updates": cell_updates,
+            "cell_updates_per_s": cell_updates / makespan if makespan > 0 else 0.0,
+            "latency_p50_s": pct(0.50),
+            "latency_p99_s": pct(0.99),
+            "latency_mean_s": statistics.mean(lat) if lat else None,
+            "rounds": self.rounds,
+            "batches_built": self.batches_built,
+            "refused_for_memory": self.refused_for_memory,
+        }
