@@ -103,12 +103,21 @@ int squeeze_nu(const squeeze_handle *h, const int32_t *d_xy, uint64_t *d_omega,
                uint64_t count, void *stream);
 
 /* squeeze_map_tc -- the same two maps with their digit-times-weight sums run
- * as tcgen05 matrix multiplies (Sec. 3.6): kind = SQUEEZE_MAP_TC_BF16 (bf16
- * operands, fp32 accumulate, exact by construction; see the design notes for
- * the bound) or SQUEEZE_MAP_TC_I8 (UNSUPPORTED on sm_103a).
- *   direction 0: lambda (d_in = uint64 omega, d_out = int32 xy pairs);
- *   direction 1: nu (d_in = int32 xy pairs, d_out = uint64 omega).
- * Same outputs as squeeze_lambda / squeeze_nu. */
+ * as tcgen05 matrix multiplies (Sec. 3.6).  kind = SQUEEZE_MAP_TC_BF16: the
+ * per-level digits (tau components for lambda, replica ids for nu; all < 256)
+ * are bf16 rows of A, the level weights (s^(mu-1) for lambda; k^((mu-1)/2) or
+ * W k^((mu-2)/2) for nu) are split into radix-256 limbs as the columns of B,
+ * and fp32 accumulates each column.  Exact: with r <= 30 and every digit and
+ * limb <= 255 a column sum is below 30 * 254 * 255 < 2^21 < 2^24, so fp32
+ * holds every partial sum exactly in any order; limbs are recombined in
+ * 64-bit integers.  kind = SQUEEZE_MAP_TC_I8 returns UNSUPPORTED (the integer
+ * MMA kind is not available on sm_103a).
+ *   direction 0: lambda (d_in = count uint64 omega, d_out = count int32 xy
+ *                pairs, (-1, -1) for omega >= k^r);
+ *   direction 1: nu (d_in = count int32 xy pairs, d_out = count uint64
+ *                omega, UINT64_MAX for a hole or a point off the box).
+ * Same outputs as squeeze_lambda / squeeze_nu.  Both pointers 8-byte aligned
+ * (else INVALID_ARG); count = 0 enqueues nothing. */
 int squeeze_map_tc(const squeeze_handle *h, int direction, const void *d_in, void *d_out,
                    uint64_t count, int kind, void *stream);
 

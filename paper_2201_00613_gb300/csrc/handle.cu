@@ -163,6 +163,7 @@ int squeeze_map_tc(const squeeze_handle *h, int direction, const void *d_in, voi
     return SQUEEZE_ERR_INVALID_ARG;
   if (kind == SQUEEZE_MAP_TC_I8) return SQUEEZE_ERR_UNSUPPORTED;
   if (kind != SQUEEZE_MAP_TC_BF16) return SQUEEZE_ERR_INVALID_ARG;
+  if (((uintptr_t)d_in | (uintptr_t)d_out) & 7u) return SQUEEZE_ERR_INVALID_ARG;
   if (!count) return SQUEEZE_OK;
   return sq_launch_map_tc(h, direction, d_in, d_out, count, (cudaStream_t)stream);
 }
