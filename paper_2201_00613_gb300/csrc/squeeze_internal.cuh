@@ -173,6 +173,7 @@ struct TileLayout {
   uint32_t win_bytes;        // one word buffer (two are used)
   uint32_t hoff_bytes;       // halo offsets
   uint32_t rowa_bytes;       // per-row alignment offsets (two sets)
+  uint32_t carry_bytes;      // per-row 16-byte chunk handed to the next group
   uint32_t stage_bytes;      // one staging buffer (two are used)
   uint32_t smem;             // total dynamic shared memory
 };

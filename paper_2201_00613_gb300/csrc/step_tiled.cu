@@ -345,12 +345,13 @@ __device__ __forceinline__ void unpack_row(uint32_t *stage32w, uint8_t *stage, u
 
 // Shared-memory carve-up of the tiled kernel (offsets in bytes; every region
 // starts at a multiple of 16): two word buffers, halo offsets, 2 mbarriers,
-// two sets of row offsets, two staging buffers.
+// two sets of row offsets, the row-end carry chunks, two staging buffers.
 struct SmemPtrs {
   unsigned char *win0;
   uint32_t *hoff;
   uint64_t *mbar;
   uint8_t *rowa;
+  uint8_t *carry;
   uint8_t *stage0;
 };
 
@@ -365,6 +366,8 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
   off += 16;
   q.rowa = smem + off;
   off += lay.rowa_bytes;
+  q.carry = smem + off;
+  off += lay.carry_bytes;
   q.stage0 = smem + off;
   return q;
 }
@@ -400,6 +403,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   uint32_t *hoff = q.hoff;
   uint64_t *mbar = q.mbar;
   uint8_t *rowa = q.rowa;
+  uint8_t *carry = q.carry;
   uint8_t *stage_base = q.stage0;
 
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -427,6 +431,14 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
     const Group G = group_at(p, TW, g);
     const uint32_t ntiles = G.ntiles, seg = G.seg;
+    // A row segment shares its first and last 16-byte chunk with the groups
+    // beside it.  When the next group of the band is also this CTA's next
+    // group, the last partial chunk of each row is handed to it in `carry`
+    // (row ly stays with the same warp from group to group) instead of being
+    // written in pieces, and that group completes the chunk with its own
+    // first bytes and stores it whole.
+    const bool has_prev = g_stride == 1 && g > g_first && G.tx0 != 0;
+    const bool gives = g_stride == 1 && g + 1 < g_end && G.tx0 + 32u < p.tiles_x;
 
     // This warp's bulk stores of the previous group must finish reading the
     // other staging buffer before the CTA barrier below lets it be refilled.
@@ -521,31 +533,47 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
           unpack_row<kTW>(stage32w, stage, y[k] & valid, ly * p.pitch + arow[k] + lane * TW, TW,
                           lane, ntiles);
       }
-      // Write the rows: one bulk store per row for its whole 16-byte chunks
-      // [head, mid_end) (lane k issues row k) and, for each ragged end (they
-      // share a chunk with a neighbouring group), up to four aligned pieces
-      // of 8/4/2/1 bytes (lane 2k + side).
+      __syncwarp();
+      // Carried chunks: take the previous group's tail bytes in front of the
+      // row (staging offsets [0, a)), hand this row's tail on.
+      if (has_prev || gives) {
+        for (uint32_t e = lane; e < 16u * kRowsInFlight; e += 32u) {
+          const uint32_t k = e >> 4, i = e & 15u, ly = ly0 + k * nw;
+          if (ly < p.TH) {
+            const uint32_t a = rowa[b * p.TH + ly], end = a + seg;
+            uint8_t *sb = stage + ly * p.pitch;
+            if (has_prev && i < a) sb[i] = carry[ly * 16u + i];
+            if (gives && i < (end & 15u)) carry[ly * 16u + i] = sb[(end & ~15u) + i];
+          }
+        }
+      }
+      // Write the rows.  In staging offsets (offset 0 is the 16-byte aligned
+      // address below the row start) the bytes [v0, v1) go out: one bulk store
+      // per row for the whole chunks [m0, m1) (lane k issues row k) and, for
+      // each ragged end (a chunk shared with a neighbouring group), up to four
+      // aligned pieces of 8/4/2/1 bytes (lane 2k + side).
       fence_async_smem();
       __syncwarp();
       if (lane < 3u * kRowsInFlight) {  // lanes [0, R): bulk stores; [R, 3R): edges
         const uint32_t k = lane < (uint32_t)kRowsInFlight ? lane : (lane - kRowsInFlight) >> 1;
         const uint32_t ly = ly0 + k * nw;
         if (ly < p.TH) {
-          const uint32_t a = rowa[b * p.TH + ly];
-          const uint32_t head = (16u - a) & 15u, mid_end = seg - ((a + seg) & 15u);
-          const bool split = head < mid_end && seg >= head;
-          uint8_t *g0 = out + G.row0 + (uint64_t)ly * W;  // the row segment in HBM
-          const uint8_t *s0 = stage + ly * p.pitch + a;     // and in staging (same alignment)
+          const uint32_t a = rowa[b * p.TH + ly], end = a + seg;
+          const uint32_t v0 = has_prev ? 0u : a, v1 = gives ? (end & ~15u) : end;
+          const uint32_t m0 = (v0 + 15u) & ~15u, m1 = v1 & ~15u;
+          const bool split = m0 < m1;
+          uint8_t *g0 = out + (G.row0 + (uint64_t)ly * W - a);  // staging offset 0 in HBM
+          const uint8_t *s0 = stage + ly * p.pitch;
           if (lane < (uint32_t)kRowsInFlight) {
-            if (split) bulk_store(g0 + head, s0 + head, mid_end - head);
+            if (split) bulk_store(g0 + m0, s0 + m0, m1 - m0);
           } else {
-            // side 0: [0, head) or the whole segment when there is no middle;
-            // side 1: [mid_end, seg).
+            // side 0: [v0, m0) or all of [v0, v1) when there is no middle;
+            // side 1: [m1, v1).
             const bool side = (lane - kRowsInFlight) & 1u;
-            uint32_t lo = side ? mid_end : 0u, hi = side ? seg : (split ? head : seg);
+            uint32_t lo = side ? m1 : v0, hi = side ? v1 : (split ? m0 : v1);
             if (side && !split) hi = lo = 0;
             while (lo < hi) {
-              const uint32_t n = hi - lo, al = (a + lo);
+              const uint32_t n = hi - lo, al = lo;
               if ((al & 1u) || n < 2) { g0[lo] = s0[lo]; lo += 1; }
               else if ((al & 2u) || n < 4) {
                 *reinterpret_cast<uint16_t *>(g0 + lo) = *reinterpret_cast<const uint16_t *>(s0 + lo);
@@ -577,8 +605,8 @@ __device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLay
   }
 }
 
-// One step of one instance; the CTAs of the persistent grid take groups
-// blockIdx.x, blockIdx.x + gridDim.x, ...
+// One step of one instance; CTA c of the persistent grid takes the
+// contiguous run of groups [c G / grid, (c + 1) G / grid).
 template <bool kLife, int kTW>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, TileLayout lay, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
@@ -587,7 +615,9 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   make_transpose(threadIdx.x & 31u, keep, rot);
   init_barriers(smem, lay);
   uint32_t it = 0;
-  run_groups<kLife, kTW>(p, lay, in, out, blockIdx.x, p.groups, gridDim.x, smem, keep, rot, it);
+  const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
+  const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
+  run_groups<kLife, kTW>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
   bulk_wait_all();
 }
 
@@ -680,8 +710,9 @@ TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t 
   l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15);
   l.hoff_bytes = (uint32_t)(((size_t)nhalo * 4 + 15) & ~(size_t)15);
   l.rowa_bytes = (uint32_t)(((size_t)2 * TH + 15) & ~(size_t)15);
+  l.carry_bytes = 16u * TH;
   l.stage_bytes = (uint32_t)((size_t)TH * pitch + 64);  // + slack for whole-word reads
-  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + 2 * l.stage_bytes;
+  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + l.carry_bytes + 2 * l.stage_bytes;
   return l;
 }
 
@@ -690,8 +721,9 @@ TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
   l.win_bytes = a.win_bytes > b.win_bytes ? a.win_bytes : b.win_bytes;
   l.hoff_bytes = a.hoff_bytes > b.hoff_bytes ? a.hoff_bytes : b.hoff_bytes;
   l.rowa_bytes = a.rowa_bytes > b.rowa_bytes ? a.rowa_bytes : b.rowa_bytes;
+  l.carry_bytes = a.carry_bytes > b.carry_bytes ? a.carry_bytes : b.carry_bytes;
   l.stage_bytes = a.stage_bytes > b.stage_bytes ? a.stage_bytes : b.stage_bytes;
-  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + 2 * l.stage_bytes;
+  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + l.carry_bytes + 2 * l.stage_bytes;
   return l;
 }
 
