@@ -271,6 +271,42 @@ __device__ __forceinline__ void issue_group_loads(const TiledDev &p, const Group
 // Rows a warp keeps in flight at once (independent shuffle chains).
 constexpr int kRowsInFlight = 3;
 
+// Halo bytes per direction that are loaded ahead of the pack.
+constexpr int kHaloAhead = 2;
+
+// Adjacent tile (precomputed table) in direction j of the tile of `lane` in
+// group G, or ~0 (a hole or off the box, and for lanes past the group).
+__device__ __forceinline__ uint32_t adjacent_of(const TiledDev &p, const Group &G, uint32_t j,
+                                                unsigned lane) {
+  if (lane >= G.ntiles) return ~0u;
+  return __ldg(p.adj + j * p.tiles + (uint64_t)G.ty * p.tiles_x + G.tx0 + lane);
+}
+
+// Byte offset of tile t's first cell, or ~0 for t = ~0.
+__device__ __forceinline__ uint64_t tile_base(const TiledDev &p, uint32_t TW, uint32_t t) {
+  if (t == ~0u) return ~0ull;
+  const uint32_t nty = fdiv(p.div_tiles_x, t), ntx = t - nty * p.tiles_x;
+  return (uint64_t)nty * p.TH * p.W + (uint64_t)ntx * TW;
+}
+
+// Halo words h0 .. h1-1 (one direction): bit `lane` of word h is the state of
+// halo reference h of the lane's adjacent tile t (dead for t = ~0).
+__device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint32_t t,
+                                            uint32_t h0, uint32_t h1, const uint32_t *hoff,
+                                            uint32_t *words, const uint8_t *in, unsigned lane) {
+  const uint64_t base = tile_base(p, TW, t);
+  for (uint32_t h = h0; h < h1; ++h) {
+    bool alive = false;
+    if (base != ~0ull) {
+      const uint64_t a = base + hoff[h];
+      if (a < p.total) alive = __ldg(in + a) & 1u;
+      else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+    }
+    const uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
+    if (lane == 0) words[h] = word;
+  }
+}
+
 // Pack tile row ly of the staging buffer into a word (lane = tile; bit 8b + j
 // <- byte 4j + b of the row); 0 for lanes past the group.
 template <int kTW>
@@ -421,6 +457,10 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   if (warp == 0 && g_first < g_end)
     issue_group_loads(p, group_at(p, TW, g_first), in, stage_base + (it & 1u) * stage_bytes,
                       &mbar[it & 1u], lane);
+  // Adjacent tile of this lane's tile in direction j = warp, for the group at hand.
+  uint32_t t_cur = ~0u;
+  if (warp < p.ndirs && g_first < g_end)
+    t_cur = adjacent_of(p, group_at(p, TW, g_first), warp, lane);
 
   for (uint64_t g = g_first; g < g_end; g += g_stride, ++it) {
     const uint32_t b = it & 1u;
@@ -444,27 +484,31 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     // other staging buffer before the CTA barrier below lets it be refilled.
     bulk_wait_read();
 
-    // Adjacent tiles (precomputed table) and halo words, one direction per warp.
-    for (uint32_t j = warp; j < p.ndirs; j += nw) {
-      uint64_t base = ~0ull;
-      if (lane < ntiles) {
-        uint32_t t = __ldg(p.adj + j * p.tiles + (uint64_t)G.ty * p.tiles_x + G.tx0 + lane);
-        if (t != ~0u) {
-          uint32_t nty = fdiv(p.div_tiles_x, t), ntx = t - nty * p.tiles_x;
-          base = (uint64_t)nty * p.TH * W + (uint64_t)ntx * TW;
-        }
-      }
-      for (uint32_t h = p.halo_start[j]; h < p.halo_start[j + 1]; ++h) {
-        bool alive = false;
-        if (base != ~0ull) {
-          uint64_t a = base + hoff[h];
-          if (a < total) alive = __ldg(in + a) & 1u;
+    // Halo words, one direction per warp.  Direction j = warp (the common
+    // case): its adjacent tiles were looked up during the previous group;
+    // the first kHaloAhead halo bytes are loaded now and turned into words
+    // after the pack below, so their latency overlaps the pack.  The rest,
+    // and directions j >= nw, are gathered in place.
+    uint32_t hb[kHaloAhead];
+    uint32_t h_pre = 0, t_next = ~0u;
+    if (warp < p.ndirs) {
+      const uint32_t h0 = p.halo_start[warp], h1 = p.halo_start[warp + 1];
+      h_pre = min(h1 - h0, (uint32_t)kHaloAhead);
+      const uint64_t base = tile_base(p, TW, t_cur);
+#pragma unroll
+      for (int i = 0; i < kHaloAhead; ++i) {
+        hb[i] = 0;
+        if ((uint32_t)i < h_pre && base != ~0ull) {
+          const uint64_t a = base + hoff[h0 + i];
+          if (a < total) hb[i] = __ldg(in + a);
           else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
         }
-        uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
-        if (lane == 0) win[slots + h] = word;
       }
+      if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
     }
+    for (uint32_t j = warp + nw; j < p.ndirs; j += nw)
+      gather_halo(p, TW, adjacent_of(p, G, j, lane), p.halo_start[j], p.halo_start[j + 1], hoff,
+                  win + slots, in, lane);
 
     mbar_wait(&mbar[b], (it >> 1) & 1u, p.status);
     // Bytes past the last 16-byte boundary of the buffer (only rows that end
@@ -495,6 +539,19 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 #pragma unroll
       for (int k = 0; k < kRowsInFlight; ++k)
         if (ly0 + k * nw < p.TH) win[(ly0 + k * nw) * 32u + lane] = acc[k];
+    }
+    if (warp < p.ndirs) {
+      const uint32_t h0 = p.halo_start[warp];
+#pragma unroll
+      for (int i = 0; i < kHaloAhead; ++i) {
+        if ((uint32_t)i < h_pre) {
+          const uint32_t word = __ballot_sync(0xFFFFFFFFu, hb[i] & 1u);
+          if (lane == 0) win[slots + h0 + i] = word;
+        }
+      }
+      if (h0 + h_pre < p.halo_start[warp + 1])
+        gather_halo(p, TW, t_cur, h0 + h_pre, p.halo_start[warp + 1], hoff, win + slots, in, lane);
+      t_cur = t_next;
     }
     // The only CTA barrier of the group: all words (rows and halo) are in
     // place, and every warp has finished the previous group.
