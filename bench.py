@@ -8,8 +8,9 @@ larger than L2, so no flush is needed between steps.
 Printed (rank 0, one JSON line): value = fractal cell-updates/s over all
 ranks; the roofline of the step kernel against the measured HBM copy
 bandwidth; the end-to-end rate through the C ABI from and to pinned host
-memory; the same-GPU bounding-box comparison at level 16; the CPU oracle on a
-bounded sample; SM clocks sampled during the timed region.
+memory; the same-GPU bounding-box comparison at level 16; the integer-ALU
+maps and per-cell step against their tensor-core (tcgen05) forms at level 20;
+the CPU oracle on a bounded sample; SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl squeeze|reference]
 """
@@ -174,6 +175,24 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def replica_max(x, world, device):
+    """Max of a per-rank number over all ranks (the slowest replica bounds the
+    job); the ranks are independent replicas, this is the only collective."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells, ca_steps, bench_steps, ms_max, world):
+    """Whole-job cell-updates/s: every replica steps `cells` cells `ca_steps`
+    times per bench step; the job takes the slowest replica's time."""
+    return world * cells * ca_steps * bench_steps / (ms_max / 1e3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -198,11 +217,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(x, world, dev)
 
     w = WORKLOAD
     pq = I.p_q24(w.p)
@@ -236,7 +251,7 @@ def main():
     status = sq.squeeze_device_status(h.h)
     launches = args.steps * w.n_steps
     ms_per_step = ms / args.steps
-    value = world * cells * w.n_steps * args.steps / (ms / 1e3)
+    value = job_value(cells, w.n_steps, args.steps, ms, world)
     launch_s = ms / 1e3 / launches
     algo_bytes = 2 * cells  # own state read once + new state written once
     peak, peak_kind = peaks()
@@ -261,9 +276,10 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- same-GPU bounding box at level 16 ----------------------------------
-    compare = None
+    compare = maps = None
     if not args.no_compare:
         compare = bb_compare(sq, torch, dev, stream)
+        maps = map_compare(sq, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -291,6 +307,7 @@ def main():
             "clocks": clocks,
             "device_status": status,
             "bb_compare": compare,
+            "map_compare": maps,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -358,6 +375,58 @@ def bb_compare(sq, torch, dev, stream, steps=20):
     del g0, g1, a, b
     torch.cuda.empty_cache()
     return out
+
+
+def map_compare(sq, torch, dev, stream, points=1 << 25):
+    """Integer-ALU maps against the tensor-core (tcgen05 kind::f16) maps at the
+    benchmark level: lambda and nu over `points` seeded compact indices, and
+    one per-cell step of each kind over the whole state, checked bit for bit."""
+    w = WORKLOAD
+    h = sq.Handle(w.fractal, w.r)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(I.R20_SAMPLE_SEED)
+    om = torch.randint(0, h.cells, (points,), generator=gen, dtype=torch.int64, device=dev)
+    xy = {k: torch.empty((points, 2), dtype=torch.int32, device=dev) for k in ("alu", "tc")}
+    back = {k: torch.empty(points, dtype=torch.int64, device=dev) for k in ("alu", "tc")}
+    TC = sq.SQUEEZE_MAP_TC_BF16
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    rate = {"lambda": {}, "nu": {}, "step": {}}
+    rate["lambda"]["alu"] = points / timed(lambda: sq.squeeze_lambda(h.h, om, xy["alu"], points, stream))
+    rate["lambda"]["tc"] = points / timed(lambda: sq.squeeze_map_tc(h.h, 0, om, xy["tc"], points, TC, stream))
+    rate["nu"]["alu"] = points / timed(lambda: sq.squeeze_nu(h.h, xy["alu"], back["alu"], points, stream))
+    rate["nu"]["tc"] = points / timed(lambda: sq.squeeze_map_tc(h.h, 1, xy["alu"], back["tc"], points, TC, stream))
+    maps_exact = (torch.equal(xy["alu"], xy["tc"]) and torch.equal(back["alu"], back["tc"])
+                  and torch.equal(back["alu"], om))
+    del om, xy, back
+    a = torch.empty(h.cells, dtype=torch.uint8, device=dev)
+    sq.squeeze_init_bernoulli(h.h, a, w.seed, I.p_q24(w.p))
+    outs = {}
+    for name, kind in (("alu", sq.SQUEEZE_MAP_ALU), ("tc", TC), ("tiled", sq.SQUEEZE_STEP_TILED)):
+        outs[name] = torch.empty_like(a)
+        t = timed(lambda: sq.squeeze_step(h.h, a, outs[name], 1, kind, stream), reps=1)
+        rate["step"][name] = h.cells / t
+    step_exact = torch.equal(outs["alu"], outs["tc"]) and torch.equal(outs["alu"], outs["tiled"])
+    status = sq.squeeze_device_status(h.h)
+    h.close()
+    del a, outs
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "points": points, "unit": "points/s (steps: cell-updates/s)",
+            "lambda": rate["lambda"], "nu": rate["nu"], "step": rate["step"],
+            "bit_exact": bool(maps_exact and step_exact and status == 0),
+            "tc": "tcgen05.mma kind::f16, bf16 digits x radix-256 weight limbs, fp32 accumulate; "
+                  "column sums < 2^21"}
 
 
 if __name__ == "__main__":
