@@ -36,8 +36,8 @@ COMPARE = I.TRIANGLE_R16
 METRIC = "cell-updates/s"
 STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2201_00613_gb300", "csrc", "step_tiled.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-CPU_SAMPLE_LEVEL = 13   # oracle sample: the level-13 top-left sub-replica of the r = 20 box
-CPU_SAMPLE_STEPS = 200
+CPU_SAMPLE_LEVEL = 14   # oracle sample: the level-14 top-left sub-replica of the r = 20 box
+CPU_SAMPLE_STEPS = 800   # about 15 s of work on 16 cores
 
 
 def parse():
@@ -136,8 +136,8 @@ class ClockSampler:
 
 def cpu_oracle_baseline(seconds_hint=True):
     """The oracle as it stands, on all host cores, on a bounded sample of the
-    workload: the level-13 top-left sub-replica of the level-20 box with the
-    same seeded start, CPU_SAMPLE_STEPS box steps."""
+    workload: the level-CPU_SAMPLE_LEVEL top-left sub-replica of the level-20
+    box with the same seeded start, CPU_SAMPLE_STEPS box steps."""
     import oracle
     f, r = WORKLOAD.fractal, CPU_SAMPLE_LEVEL
     m = oracle.member_grid(f, r)
