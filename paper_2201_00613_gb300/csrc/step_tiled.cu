@@ -313,7 +313,7 @@ template <int kTW>
 __device__ __forceinline__ uint32_t pack_row(const TiledDev &p, const uint32_t *stage32,
                                              uint32_t o, bool live, uint32_t valid) {
   const uint32_t nwin = kTW ? (3u + (uint32_t)kTW + 3u) / 4u : p.nwin;
-  uint32_t acc = 0;
+  uint32_t acc = 0, acc1 = 0;
   if (live) {
     const uint32_t *w = stage32 + (o >> 2);
     uint32_t sh = (o & 3u) * 8u;
@@ -321,8 +321,11 @@ __device__ __forceinline__ uint32_t pack_row(const TiledDev &p, const uint32_t *
 #pragma unroll
     for (int j = 0; j < 9; ++j) wv[j] = (uint32_t)j < nwin ? w[j] : 0u;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc += (__funnelshift_r(wv[j], wv[j + 1], sh) & 0x01010101u) << j;
-    acc &= valid;
+    for (int j = 0; j < 8; j += 2) {   // two independent chains; the bits do not overlap
+      acc |= (__funnelshift_r(wv[j], wv[j + 1], sh) & 0x01010101u) << j;
+      acc1 |= (__funnelshift_r(wv[j + 1], wv[j + 2], sh) & 0x01010101u) << (j + 1);
+    }
+    acc = (acc | acc1) & valid;
   }
   return acc;
 }
@@ -611,7 +614,8 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       // aligned pieces of 8/4/2/1 bytes (lane 2k + side).
       fence_async_smem();
       __syncwarp();
-      if (lane < 3u * kRowsInFlight) {  // lanes [0, R): bulk stores; [R, 3R): edges
+      // (With a carried chunk at both ends no row has an edge piece.)
+      if (lane < (has_prev && gives ? 1u : 3u) * kRowsInFlight) {  // [0, R): bulk; [R, 3R): edges
         const uint32_t k = lane < (uint32_t)kRowsInFlight ? lane : (lane - kRowsInFlight) >> 1;
         const uint32_t ly = ly0 + k * nw;
         if (ly < p.TH) {
