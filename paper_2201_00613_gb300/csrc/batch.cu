@@ -21,7 +21,6 @@ struct squeeze_batch {
   std::vector<squeeze_batch_item> items;
   TileLayout lay;
   bool life;
-  uint32_t TW;              // common tile-row width, 0 when the items differ
   int threads, grid, ctas_per_sm;
   bool use_graph;
   uint32_t parity;          // 0: states are in buffer 0, 1: in buffer 1
@@ -96,7 +95,6 @@ int setup(squeeze_batch *b) {
   std::vector<uint8_t *> buf0(count), buf1(count);
   std::vector<uint64_t> cells(count), groups(count);
   b->life = true;
-  b->TW = 0;
   bool first = true;
   for (uint32_t i = 0; i < count; ++i) {
     squeeze_handle *h = b->items[i].h;
@@ -107,8 +105,6 @@ int setup(squeeze_batch *b) {
     if (rc) return rc;
     TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
     b->lay = first ? l : sq_tile_layout_max(b->lay, l);
-    if (first) b->TW = sp.TW;
-    else if (b->TW != sp.TW) b->TW = 0;
     first = false;
     b->life = b->life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
     buf0[i] = b->items[i].d_buf0;
@@ -117,7 +113,7 @@ int setup(squeeze_batch *b) {
     groups[i] = sp.groups;
   }
   if (b->lay.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
-  int occ = sq_batch_occupancy(b->life, b->TW, b->threads, b->lay.smem);
+  int occ = sq_batch_occupancy(b->life, b->threads, b->lay.smem);
   if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
   int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
   int sms = 0;
@@ -150,8 +146,8 @@ int setup(squeeze_batch *b) {
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
   for (uint64_t t = 0; t < n_steps; ++t) {
     int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, b->d_work, b->d_sched, b->lay,
-                             b->grid, b->threads, b->life, b->TW,
-                             (uint32_t)((b->parity + t) & 1u), st);
+                             b->grid, b->threads, b->life, (uint32_t)((b->parity + t) & 1u),
+                             st);
     if (rc) return rc;
   }
   return SQUEEZE_OK;

@@ -152,6 +152,7 @@ struct TiledDev {
   Rule rule;
   uint32_t L, TW, TH, cells, nhalo, dir_mask, slots;
   uint32_t valid;            // packed-word bits that hold a real cell (lx < TW)
+  uint32_t rpw;              // tile rows per slot word: 32 / TW for TW = 8, 16, else 1
   uint32_t nwin;             // aligned 32-bit words covering one tile row
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
@@ -181,7 +182,7 @@ struct TileLayout {
 // Geometry and launch shape of a tiled-step program, independent of where its
 // tables live.
 struct TileSpec {
-  uint32_t L, TW, TH, cells, slots, nhalo, ndirs, dir_mask;
+  uint32_t L, TW, TH, rpw, cells, slots, nhalo, ndirs, dir_mask;
   uint8_t dir_list[9];
   uint32_t halo_start[10];
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
@@ -282,10 +283,10 @@ int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t 
 // The handle's prepared tiled program (sq_tiled_prepare first).
 int sq_tiled_describe(const squeeze_handle *h, sq::TiledDev *d, sq::TileSpec *sp);
 // CTAs per SM of the batched kernel instance for this shape (0 if it cannot run).
-int sq_batch_occupancy(bool life, uint32_t TW, int threads, uint32_t smem);
+int sq_batch_occupancy(bool life, int threads, uint32_t smem);
 int sq_batch_launch(const sq::TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const sq::BatchWork *d_work, const uint32_t *d_sched,
-                    const sq::TileLayout &lay, int grid, int threads, bool life, uint32_t TW,
+                    const sq::TileLayout &lay, int grid, int threads, bool life,
                     uint32_t parity, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);

@@ -290,20 +290,31 @@ __device__ __forceinline__ uint64_t tile_base(const TiledDev &p, uint32_t TW, ui
 }
 
 // Halo words h0 .. h1-1 (one direction): bit `lane` of word h is the state of
-// halo reference h of the lane's adjacent tile t (dead for t = ~0).
+// halo reference h of the lane's adjacent tile t (dead for t = ~0).  The
+// bytes are loaded four at a time before their ballots, so the loads of a
+// direction with many halo cells overlap.
 __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint32_t t,
                                             uint32_t h0, uint32_t h1, const uint32_t *hoff,
                                             uint32_t *words, const uint8_t *in, unsigned lane) {
   const uint64_t base = tile_base(p, TW, t);
-  for (uint32_t h = h0; h < h1; ++h) {
-    bool alive = false;
-    if (base != ~0ull) {
-      const uint64_t a = base + hoff[h];
-      if (a < p.total) alive = __ldg(in + a) & 1u;
-      else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+  for (uint32_t h = h0; h < h1; h += 4) {
+    uint32_t v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      v[i] = 0;
+      if (h + i < h1 && base != ~0ull) {
+        const uint64_t a = base + hoff[h + i];
+        if (a < p.total) v[i] = __ldg(in + a);
+        else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+      }
     }
-    const uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
-    if (lane == 0) words[h] = word;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (h + i < h1) {
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, v[i] & 1u);
+        if (lane == 0) words[h + i] = word;
+      }
+    }
   }
 }
 
@@ -328,6 +339,35 @@ __device__ __forceinline__ uint32_t pack_row(const TiledDev &p, const uint32_t *
     acc = (acc | acc1) & valid;
   }
   return acc;
+}
+
+// Pack a tile row of kTW (8 or 16) bytes that starts on a kTW-byte boundary
+// of the staging buffer: kTW / 4 whole words, bit 8b + j <- byte 4j + b.
+template <int kTW>
+__device__ __forceinline__ uint32_t pack_aligned(const uint32_t *stage32, uint32_t o) {
+  uint32_t acc = 0;
+  if constexpr (kTW == 8) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(stage32 + (o >> 2));
+    acc = (w.x & 0x01010101u) | ((w.y & 0x01010101u) << 1);
+  } else if constexpr (kTW == 16) {
+    const uint4 w = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2));
+    acc = (w.x & 0x01010101u) | ((w.y & 0x01010101u) << 1) | ((w.z & 0x01010101u) << 2) |
+          ((w.w & 0x01010101u) << 3);
+  }
+  return acc;
+}
+
+// The inverse of pack_aligned: the low kTW / 4 bit planes of y, as whole words.
+template <int kTW>
+__device__ __forceinline__ void unpack_aligned(uint32_t *stage32w, uint32_t o, uint32_t y) {
+  if constexpr (kTW == 8) {
+    *reinterpret_cast<uint2 *>(stage32w + (o >> 2)) =
+        make_uint2(y & 0x01010101u, (y >> 1) & 0x01010101u);
+  } else if constexpr (kTW == 16) {
+    *reinterpret_cast<uint4 *>(stage32w + (o >> 2)) =
+        make_uint4(y & 0x01010101u, (y >> 1) & 0x01010101u, (y >> 2) & 0x01010101u,
+                   (y >> 3) & 0x01010101u);
+  }
 }
 
 // Unpack a packed row word y into bytes and write them at staging offset o;
@@ -435,8 +475,14 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
                                            uint64_t g_end, uint64_t g_stride,
                                            unsigned char *smem, const uint32_t *keep,
                                            const uint32_t *rot, uint32_t &it) {
+  // Tile rows per slot word (kTW = 8, 16: the rows of 4 or 2 tile rows share
+  // one word), slot rows in flight per warp, and tile rows per write-back batch.
+  constexpr uint32_t kRPW = kTW == 8 ? 4u : (kTW == 16 ? 2u : 1u);
+  constexpr int kR = kRPW > 1 ? 2 : kRowsInFlight;
+  constexpr uint32_t kRR = (uint32_t)kR * kRPW;
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
+  const uint32_t VR = p.TH / kRPW;   // slot rows
   const SmemPtrs q = carve(smem, lay);
   const size_t win_bytes = lay.win_bytes, stage_bytes = lay.stage_bytes;
   uint32_t *hoff = q.hoff;
@@ -528,20 +574,36 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 
     // Pack the own tile rows into words (lane = tile) and transpose them so
     // that lane L holds local cell (ly, lx(L)) of all 32 tiles.
-    for (uint32_t ly0 = warp; ly0 < p.TH; ly0 += kRowsInFlight * nw) {
-      uint32_t acc[kRowsInFlight];
+    for (uint32_t v0r = warp; v0r < VR; v0r += kR * nw) {
+      uint32_t acc[kR];
 #pragma unroll
-      for (int k = 0; k < kRowsInFlight; ++k) {
-        const uint32_t ly = ly0 + k * nw;
-        const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
-        if (lane == 0 && ly < p.TH) rowa[b * p.TH + ly] = (uint8_t)a;
-        acc[k] = pack_row<kTW>(p, stage32, ly * p.pitch + a + lane * TW, ly < p.TH && lane < ntiles,
-                               valid);
+      for (int k = 0; k < kR; ++k) {
+        const uint32_t vr = v0r + k * nw;
+        if constexpr (kRPW == 1) {
+          const uint32_t ly = vr;
+          const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+          if (lane == 0 && ly < p.TH) rowa[b * p.TH + ly] = (uint8_t)a;
+          acc[k] = pack_row<kTW>(p, stage32, ly * p.pitch + a + lane * TW,
+                                 ly < p.TH && lane < ntiles, valid);
+        } else {
+          acc[k] = 0;
+          if (vr < VR) {
+#pragma unroll
+            for (uint32_t i = 0; i < kRPW; ++i) {
+              const uint32_t ly = vr * kRPW + i;
+              const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+              if (lane == 0) rowa[b * p.TH + ly] = (uint8_t)a;
+              if (lane < ntiles)
+                acc[k] |= pack_aligned<kTW>(stage32, ly * p.pitch + a + lane * (uint32_t)kTW)
+                          << (i * (uint32_t)(kTW / 4));
+            }
+          }
+        }
       }
-      transpose32_n<kRowsInFlight>(acc, keep, rot);
+      transpose32_n<kR>(acc, keep, rot);
 #pragma unroll
-      for (int k = 0; k < kRowsInFlight; ++k)
-        if (ly0 + k * nw < p.TH) win[(ly0 + k * nw) * 32u + lane] = acc[k];
+      for (int k = 0; k < kR; ++k)
+        if (v0r + k * nw < VR) win[(v0r + k * nw) * 32u + lane] = acc[k];
     }
     if (warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp];
@@ -564,13 +626,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
                         &mbar[b ^ 1u], lane);
 
     // Rule, inverse transpose and write-back of the own rows.
-    for (uint32_t ly0 = warp; ly0 < p.TH; ly0 += kRowsInFlight * nw) {
-      uint32_t y[kRowsInFlight];
+    for (uint32_t v0r = warp; v0r < VR; v0r += kR * nw) {
+      uint32_t y[kR];
 #pragma unroll
-      for (int k = 0; k < kRowsInFlight; ++k) {
-        const uint32_t c = (ly0 + k * nw) * 32u + lane;
+      for (int k = 0; k < kR; ++k) {
+        const uint32_t c = (v0r + k * nw) * 32u + lane;
         uint32_t next = 0;
-        if (ly0 + k * nw < p.TH) {
+        if (v0r + k * nw < VR) {
           const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(p.refs) + c);
           const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
           uint32_t n[8];
@@ -583,22 +645,35 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         }
         y[k] = next;
       }
-      transpose32_n<kRowsInFlight>(y, keep, rot);
-      uint32_t arow[kRowsInFlight];
+      transpose32_n<kR>(y, keep, rot);
 #pragma unroll
-      for (int k = 0; k < kRowsInFlight; ++k) {
-        const uint32_t ly = ly0 + k * nw;
-        arow[k] = ly < p.TH ? rowa[b * p.TH + ly] : 0u;
-        if (ly < p.TH)
-          unpack_row<kTW>(stage32w, stage, y[k] & valid, ly * p.pitch + arow[k] + lane * TW, TW,
-                          lane, ntiles);
+      for (int k = 0; k < kR; ++k) {
+        const uint32_t vr = v0r + k * nw;
+        if constexpr (kRPW == 1) {
+          const uint32_t ly = vr;
+          if (ly < p.TH)
+            unpack_row<kTW>(stage32w, stage, y[k] & valid,
+                            ly * p.pitch + rowa[b * p.TH + ly] + lane * TW, TW, lane, ntiles);
+        } else if (vr < VR && lane < ntiles) {
+#pragma unroll
+          for (uint32_t i = 0; i < kRPW; ++i) {
+            const uint32_t ly = vr * kRPW + i;
+            unpack_aligned<kTW>(stage32w, ly * p.pitch + rowa[b * p.TH + ly] + lane * (uint32_t)kTW,
+                                y[k] >> (i * (uint32_t)(kTW / 4)));
+          }
+        }
       }
       __syncwarp();
+      // Tile row of entry rr of this write-back batch (rr < kRR), or >= TH.
+      auto row_of = [&](uint32_t rr) -> uint32_t {
+        const uint32_t vr = v0r + (rr / kRPW) * nw;
+        return vr < VR ? vr * kRPW + rr % kRPW : p.TH;
+      };
       // Carried chunks: take the previous group's tail bytes in front of the
       // row (staging offsets [0, a)), hand this row's tail on.
       if (has_prev || gives) {
-        for (uint32_t e = lane; e < 16u * kRowsInFlight; e += 32u) {
-          const uint32_t k = e >> 4, i = e & 15u, ly = ly0 + k * nw;
+        for (uint32_t e = lane; e < 16u * kRR; e += 32u) {
+          const uint32_t i = e & 15u, ly = row_of(e >> 4);
           if (ly < p.TH) {
             const uint32_t a = rowa[b * p.TH + ly], end = a + seg;
             uint8_t *sb = stage + ly * p.pitch;
@@ -615,9 +690,8 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       fence_async_smem();
       __syncwarp();
       // (With a carried chunk at both ends no row has an edge piece.)
-      if (lane < (has_prev && gives ? 1u : 3u) * kRowsInFlight) {  // [0, R): bulk; [R, 3R): edges
-        const uint32_t k = lane < (uint32_t)kRowsInFlight ? lane : (lane - kRowsInFlight) >> 1;
-        const uint32_t ly = ly0 + k * nw;
+      if (lane < (has_prev && gives ? 1u : 3u) * kRR) {  // [0, RR): bulk; [RR, 3RR): edges
+        const uint32_t ly = row_of(lane < kRR ? lane : (lane - kRR) >> 1);
         if (ly < p.TH) {
           const uint32_t a = rowa[b * p.TH + ly], end = a + seg;
           const uint32_t v0 = has_prev ? 0u : a, v1 = gives ? (end & ~15u) : end;
@@ -625,12 +699,12 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
           const bool split = m0 < m1;
           uint8_t *g0 = out + (G.row0 + (uint64_t)ly * W - a);  // staging offset 0 in HBM
           const uint8_t *s0 = stage + ly * p.pitch;
-          if (lane < (uint32_t)kRowsInFlight) {
+          if (lane < kRR) {
             if (split) bulk_store(g0 + m0, s0 + m0, m1 - m0);
           } else {
             // side 0: [v0, m0) or all of [v0, v1) when there is no middle;
             // side 1: [m1, v1).
-            const bool side = (lane - kRowsInFlight) & 1u;
+            const bool side = (lane - kRR) & 1u;
             uint32_t lo = side ? m1 : v0, hi = side ? v1 : (split ? m0 : v1);
             if (side && !split) hi = lo = 0;
             while (lo < hi) {
@@ -650,7 +724,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
           }
         }
       }
-      if (lane < (uint32_t)kRowsInFlight) bulk_commit();
+      if (lane < kRR) bulk_commit();
     }
   }
 }
@@ -684,8 +758,9 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
 
 // One step of many instances (each with its own fractal, level and
 // buffers) in a single persistent launch.  parity selects the step's input:
-// buffer 0 on even steps, buffer 1 on odd ones.
-template <bool kLife, int kTW>
+// buffer 0 on even steps, buffer 1 on odd ones.  Each schedule entry runs the
+// instantiation for its instance's tile-row width.
+template <bool kLife>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
     const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
     uint8_t *const *__restrict__ buf1, const BatchWork *__restrict__ work,
@@ -697,10 +772,17 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
   uint32_t it = 0;
   for (uint32_t e = sched_start[blockIdx.x]; e < sched_start[blockIdx.x + 1]; ++e) {
     const BatchWork w = work[e];
+    const TiledDev &d = devs[w.instance];
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
-    run_groups<kLife, kTW>(devs[w.instance], lay, in, out, w.g_first, w.g_end, 1, smem, keep,
-                           rot, it);
+    const uint32_t kind = d.rpw == 4 ? 8u : (d.rpw == 2 ? 16u : (d.TW == 27 || d.TW == 25 ? d.TW : 0u));
+    switch (kind) {
+      case 27: run_groups<kLife, 27>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+      case 25: run_groups<kLife, 25>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+      case 8: run_groups<kLife, 8>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+      case 16: run_groups<kLife, 16>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+      default: run_groups<kLife, 0>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+    }
   }
   bulk_wait_all();
 }
@@ -732,23 +814,22 @@ __global__ void build_adjacency_kernel(FracDev f, TiledDev p, uint32_t *__restri
 
 // ---- host side: the level-L neighbour program ------------------------------
 
-const void *batch_kernel_for(bool life, uint32_t TW) {
-  if (life) {
-    if (TW == 27) return (const void *)step_batch_kernel<true, 27>;
-    if (TW == 25) return (const void *)step_batch_kernel<true, 25>;
-    return (const void *)step_batch_kernel<true, 0>;
-  }
-  if (TW == 27) return (const void *)step_batch_kernel<false, 27>;
-  if (TW == 25) return (const void *)step_batch_kernel<false, 25>;
-  return (const void *)step_batch_kernel<false, 0>;
+const void *batch_kernel_for(bool life) {
+  return life ? (const void *)step_batch_kernel<true> : (const void *)step_batch_kernel<false>;
 }
 
-const void *tiled_kernel_for(bool life, uint32_t TW) {
+// The instantiation for a program: rows shared by slot words (rpw 4 or 2)
+// have their own, as have the common widths 27 (triangle) and 25 (Vicsek).
+const void *tiled_kernel_for(bool life, uint32_t TW, uint32_t rpw) {
   if (life) {
+    if (rpw == 4) return (const void *)step_tiled_kernel<true, 8>;
+    if (rpw == 2) return (const void *)step_tiled_kernel<true, 16>;
     if (TW == 27) return (const void *)step_tiled_kernel<true, 27>;
     if (TW == 25) return (const void *)step_tiled_kernel<true, 25>;
     return (const void *)step_tiled_kernel<true, 0>;
   }
+  if (rpw == 4) return (const void *)step_tiled_kernel<false, 8>;
+  if (rpw == 2) return (const void *)step_tiled_kernel<false, 16>;
   if (TW == 27) return (const void *)step_tiled_kernel<false, 27>;
   if (TW == 25) return (const void *)step_tiled_kernel<false, 25>;
   return (const void *)step_tiled_kernel<false, 0>;
@@ -801,6 +882,14 @@ uint32_t pitch_for(uint32_t TW) { return (32u * TW + 15u + 15u) / 16u * 16u; }
 // Slot of local cell lx inside its row word (the pack's bit order).
 inline uint32_t lane_of(uint32_t lx) { return 8u * (lx & 3u) + (lx >> 2); }
 
+// Tile rows that share one slot word: 32 / TW for the power-of-two widths 8 and
+// 16 when TH is a multiple of it (such rows start at multiples of TW, so the
+// kernel reads and writes them as whole aligned words), else 1.
+uint32_t rows_per_word(uint32_t TW, uint32_t TH) {
+  if ((TW == 8 || TW == 16) && TH % (32 / TW) == 0) return 32 / TW;
+  return 1;
+}
+
 // Local lambda of the level-L fractal: compact (lx, ly) -> expanded (X, Y).
 void local_lambda(const FracDev &f, uint32_t L, uint32_t lx, uint32_t ly, uint32_t &X,
                   uint32_t &Y) {
@@ -838,7 +927,8 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   d.nhalo = sp.nhalo;
   d.nwin = (3u + sp.TW + 3u) / 4u;
   d.valid = 0;
-  for (uint32_t lx = 0; lx < sp.TW; ++lx) d.valid |= 1u << lane_of(lx);
+  for (uint32_t lx = 0; lx < sp.rpw * sp.TW; ++lx) d.valid |= 1u << lane_of(lx);
+  d.rpw = sp.rpw;
   d.dir_mask = sp.dir_mask;
   d.ndirs = sp.ndirs;
   for (int i = 0; i < 9; ++i) d.dir_list[i] = sp.dir_list[i];
@@ -937,7 +1027,9 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
   if (TW64 > 32 || TH64 > 4096) return SQUEEZE_ERR_UNSUPPORTED;  // a tile row must fit one word
   uint32_t TW = (uint32_t)TW64, TH = (uint32_t)TH64;
-  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH * 32;
+  // Narrow power-of-two rows share a slot word: 32 / TW tile rows per word.
+  const uint32_t rpw = rows_per_word(TW, TH);
+  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH / rpw * 32;
   if ((uint64_t)side * side > B.box_cap || cells > B.cells_cap || slots > B.slots_cap)
     return SQUEEZE_ERR_UNSUPPORTED;
   if ((uint64_t)TH * f.W > 0xFFFFFFFFull) return SQUEEZE_ERR_UNSUPPORTED;
@@ -948,7 +1040,9 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
     local_lambda(f, L, c % TW, c / TW, B.X[c], B.Y[c]);
     inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
-  auto slot_of = [&](uint32_t c) { return (c / TW) * 32u + lane_of(c % TW); };
+  auto slot_of = [&](uint32_t c) {
+    return (c / TW / rpw) * 32u + lane_of((c / TW % rpw) * TW + c % TW);
+  };
   const uint32_t kNone = 0xFFFFFFFFu;
   uint32_t *refs = B.refs;
   for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;
@@ -1018,6 +1112,7 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.L = L;
   sp.TW = TW;
   sp.TH = TH;
+  sp.rpw = rpw;
   sp.cells = cells;
   sp.slots = slots;
   sp.nhalo = nhalo;
@@ -1030,9 +1125,15 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.smem = smem_for(slots, nhalo, TH, sp.pitch);
   if (sp.groups >= (1ull << 32) || sp.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
+  // Shared slot words: two slot rows per warp, 4..8 warps.
   int best_w = 8;
-  for (int w = 12; w >= 6; --w)
-    if ((TH + w - 1) / w * w - TH < (TH + best_w - 1) / best_w * best_w - TH) best_w = w;
+  if (rpw > 1) {
+    const int vr = (int)(TH / rpw);
+    best_w = (vr + 1) / 2 < 4 ? 4 : ((vr + 1) / 2 > 8 ? 8 : (vr + 1) / 2);
+  } else {
+    for (int w = 12; w >= 6; --w)
+      if ((TH + w - 1) / w * w - TH < (TH + best_w - 1) / best_w * best_w - TH) best_w = w;
+  }
   sp.threads = 32 * best_w;
   return SQUEEZE_OK;
 }
@@ -1044,7 +1145,7 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return sq_cuda_fail(e);
   for (int life = 0; life < 2; ++life) {
-    const void *fn = tiled_kernel_for(life != 0, sp.TW);
+    const void *fn = tiled_kernel_for(life != 0, sp.TW, sp.rpw);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
     int n = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
@@ -1071,7 +1172,7 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   TiledDev dd = d;
   TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
   void *args[] = {&dd, &lay, &in, &out};
-  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW), dim3(life ? sp.grid : sp.grid_rule),
+  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw), dim3(life ? sp.grid : sp.grid_rule),
                            dim3(sp.threads), args, sp.smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
@@ -1154,8 +1255,8 @@ int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
   return SQUEEZE_OK;
 }
 
-int sq_batch_occupancy(bool life, uint32_t TW, int threads, uint32_t smem) {
-  const void *fn = batch_kernel_for(life, TW);
+int sq_batch_occupancy(bool life, int threads, uint32_t smem) {
+  const void *fn = batch_kernel_for(life);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -1166,11 +1267,10 @@ int sq_batch_occupancy(bool life, uint32_t TW, int threads, uint32_t smem) {
 
 int sq_batch_launch(const TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const BatchWork *d_work, const uint32_t *d_sched, const TileLayout &lay,
-                    int grid, int threads, bool life, uint32_t TW, uint32_t parity,
-                    cudaStream_t st) {
+                    int grid, int threads, bool life, uint32_t parity, cudaStream_t st) {
   TileLayout l = lay;
   void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity};
-  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, TW), dim3(grid), dim3(threads), args, l.smem, st));
+  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life), dim3(grid), dim3(threads), args, l.smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }

@@ -162,6 +162,31 @@ def test_tiled_every_tile_level_s3(f, r, levels):
         assert_status_ok(h)
 
 
+# Fractals whose tile rows are 8 or 16 cells wide, where 4 or 2 tile rows share
+# one slot word: a two-replica diagonal (k = 2: widths 8 at L = 5, 6 and 16 at
+# L = 7, 8), the hole-free s = 2 fractal (k = 4: width 16 at L = 3, 4), the
+# hole-free s = 4 fractal (k = 16: width 16, one row at L = 1, 16 rows at L = 2)
+# and the carpet at r = 8 (width 8, 8 rows at L = 2; 16 groups per band, so a
+# CTA's run hands row ends from group to group).
+DIAG2 = I.Fractal("diagonal2", 2, 2, ((0, 0), (1, 1)))
+FULL4 = I.Fractal("full4", 4, 16, tuple((x, y) for y in range(4) for x in range(4)))
+
+
+@pytest.mark.parametrize("f,r,levels", [(DIAG2, 12, [4, 5, 6, 7, 8]), (I.FULL2, 9, [2, 3, 4]),
+                                        (FULL4, 5, [1, 2]), (I.CARPET, 8, [1, 2])],
+                         ids=["diagonal2", "full2", "full4", "carpet8"])
+def test_tiled_shared_slot_words(f, r, levels):
+    with sq.Handle(f, r) as h:
+        c0 = I.bernoulli_bytes(9, h.cells, 0.5)
+        want = oracle.run_compact(f, r, c0, 3)
+        for level in levels:
+            sq.squeeze_set_tiled_level(h.h, level)
+            assert np.array_equal(run_steps(h, c0, 3, sq.SQUEEZE_STEP_TILED), want), level
+            assert np.array_equal(run_steps(h, c0, 1, sq.SQUEEZE_STEP_TILED),
+                                  oracle.run_compact(f, r, c0, 1)), level
+        assert_status_ok(h)
+
+
 @pytest.mark.parametrize("rule", [(1 << 3, (1 << 2) | (1 << 3)), (1 << 2, 0), ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),
                                   (0b000111000, 0b111000111), (1, 1 << 8)],
                          ids=["b3s23", "seeds", "highlife", "mixed", "b0s8"])
