@@ -155,8 +155,9 @@ int squeeze_step_host(squeeze_handle *h, const uint8_t *h_in, uint8_t *h_out,
  * k^ceil(L/2) x k^floor(L/2) compact rectangle), or a negative code when the
  * tiled kernel is not available (then AUTO runs the per-cell ALU kernel).
  * squeeze_set_tiled_level() overrides the choice: 0 < L <= r, else
- * INVALID_ARG; a tile row wider than 32 cells (k^ceil(L/2) > 32) gives
- * UNSUPPORTED. */
+ * INVALID_ARG; a tile row wider than 32 cells (k^ceil(L/2) > 32) other than
+ * exactly 64 cells, or a level whose tile program does not fit the kernel's
+ * shared memory, gives UNSUPPORTED. */
 int squeeze_tiled_level(const squeeze_handle *h);
 int squeeze_set_tiled_level(squeeze_handle *h, uint32_t level);
 

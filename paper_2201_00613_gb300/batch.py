@@ -48,10 +48,15 @@ class MixedBatch:
             self.handles.append(h)
             self.buf0.append(a)
             self.buf1.append(b)
-        self.batch = sq.squeeze_batch_create(
-            [(h.h, a, b) for h, a, b in zip(self.handles, self.buf0, self.buf1)])
-        if threads != 288 or ctas_per_sm or not use_graph:
-            sq.squeeze_batch_configure(self.batch, threads, ctas_per_sm, use_graph)
+        self.batch = None
+        try:
+            self.batch = sq.squeeze_batch_create(
+                [(h.h, a, b) for h, a, b in zip(self.handles, self.buf0, self.buf1)])
+            if threads != 288 or ctas_per_sm or not use_graph:
+                sq.squeeze_batch_configure(self.batch, threads, ctas_per_sm, use_graph)
+        except Exception:
+            self.close()
+            raise
         self.steps_done = 0
 
     @property
@@ -92,8 +97,15 @@ def _device_key() -> str:
 
 
 def time_config(instances, levels, threads, ctas_per_sm, steps=6) -> float:
-    """Seconds per batched step of one configuration (after a warm-up)."""
-    with MixedBatch(instances, levels=levels, threads=threads, ctas_per_sm=ctas_per_sm) as mb:
+    """Seconds per batched step of one configuration (after a warm-up); inf when
+    the library cannot run that configuration (UNSUPPORTED)."""
+    try:
+        mb = MixedBatch(instances, levels=levels, threads=threads, ctas_per_sm=ctas_per_sm)
+    except sq.SqueezeError as e:
+        if e.code != sq.SQUEEZE_ERR_UNSUPPORTED:
+            raise
+        return float("inf")
+    with mb:
         mb.run(2)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -108,7 +120,8 @@ def time_config(instances, levels, threads, ctas_per_sm, steps=6) -> float:
 def _level_candidates(f, max_r):
     out = []
     for L in range(1, max_r + 1):
-        if f.k ** ((L + 1) // 2) > 32:
+        width = f.k ** ((L + 1) // 2)   # tile-row width: one slot word, or exactly two
+        if width > 64 or (32 < width < 64):
             break
         out.append(L)
     return out[-3:]

@@ -46,7 +46,8 @@ namespace sq {
 namespace {
 
 constexpr int kTiledMaxThreads = 384;
-constexpr size_t kTiledSmemCap = 56 * 1024;
+constexpr size_t kTiledSmemCap = 56 * 1024;     // default level: 4 CTAs per SM
+constexpr size_t kTiledSmemLimit = 200 * 1024;  // any level: one CTA per SM
 
 __device__ __forceinline__ void flag(int *status, int code) { atomicCAS(status, 0, code); }
 
@@ -357,6 +358,29 @@ __device__ __forceinline__ uint32_t pack_aligned(const uint32_t *stage32, uint32
   return acc;
 }
 
+// Pack one 32-byte half of a 64-byte tile row (16-byte aligned): 8 words.
+__device__ __forceinline__ uint32_t pack_half64(const uint32_t *stage32, uint32_t o) {
+  const uint4 lo = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2));
+  const uint4 hi = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2) + 4);
+  const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+  uint32_t acc = 0, acc1 = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    acc |= (w[j] & 0x01010101u) << j;
+    acc1 |= (w[j + 1] & 0x01010101u) << (j + 1);
+  }
+  return acc | acc1;
+}
+
+// The inverse of pack_half64.
+__device__ __forceinline__ void unpack_half64(uint32_t *stage32w, uint32_t o, uint32_t y) {
+  uint32_t u[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) u[t] = (y >> t) & 0x01010101u;
+  *reinterpret_cast<uint4 *>(stage32w + (o >> 2)) = make_uint4(u[0], u[1], u[2], u[3]);
+  *reinterpret_cast<uint4 *>(stage32w + (o >> 2) + 4) = make_uint4(u[4], u[5], u[6], u[7]);
+}
+
 // The inverse of pack_aligned: the low kTW / 4 bit planes of y, as whole words.
 template <int kTW>
 __device__ __forceinline__ void unpack_aligned(uint32_t *stage32w, uint32_t o, uint32_t y) {
@@ -477,12 +501,18 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
                                            const uint32_t *rot, uint32_t &it) {
   // Tile rows per slot word (kTW = 8, 16: the rows of 4 or 2 tile rows share
   // one word), slot rows in flight per warp, and tile rows per write-back batch.
+  // (kTW = 64: each tile row is two slot words, its left and right halves; a
+  // warp keeps both halves of its rows.)  Units are what a warp owns: slot
+  // rows (kWPR = 1) or tile rows (kWPR = 2).
   constexpr uint32_t kRPW = kTW == 8 ? 4u : (kTW == 16 ? 2u : 1u);
-  constexpr int kR = kRPW > 1 ? 2 : kRowsInFlight;
-  constexpr uint32_t kRR = (uint32_t)kR * kRPW;
+  constexpr uint32_t kWPR = kTW == 64 ? 2u : 1u;
+  constexpr int kR = kRPW > 1 ? 2 : (kWPR > 1 ? 4 : kRowsInFlight);
+  constexpr uint32_t kRR = kRPW > 1 ? (uint32_t)kR * kRPW : (uint32_t)kR / kWPR;
+  constexpr uint32_t kU = (uint32_t)kR / kWPR;   // units per pass
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
-  const uint32_t VR = p.TH / kRPW;   // slot rows
+  const uint32_t VR = p.TH * kWPR / kRPW;   // slot rows
+  const uint32_t NU = VR / kWPR;            // units
   const SmemPtrs q = carve(smem, lay);
   const size_t win_bytes = lay.win_bytes, stage_bytes = lay.stage_bytes;
   uint32_t *hoff = q.hoff;
@@ -493,6 +523,10 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const unsigned nthreads = blockDim.x, nw = nthreads >> 5;
+  // Slot row of entry k of the pass that starts at unit u0.
+  auto vrow = [&](uint32_t u0, int k) -> uint32_t {
+    return kWPR * (u0 + ((uint32_t)k / kWPR) * nw) + (uint32_t)k % kWPR;
+  };
   __syncthreads();  // the previous call (another instance) is done with every buffer
   for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
   if (tid == 0) {
@@ -574,12 +608,20 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 
     // Pack the own tile rows into words (lane = tile) and transpose them so
     // that lane L holds local cell (ly, lx(L)) of all 32 tiles.
-    for (uint32_t v0r = warp; v0r < VR; v0r += kR * nw) {
+    for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
       uint32_t acc[kR];
 #pragma unroll
       for (int k = 0; k < kR; ++k) {
-        const uint32_t vr = v0r + k * nw;
-        if constexpr (kRPW == 1) {
+        const uint32_t vr = vrow(u0, k);
+        if constexpr (kWPR > 1) {
+          acc[k] = 0;
+          if (vr < VR) {
+            const uint32_t ly = vr / kWPR, a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+            if (lane == 0 && (vr % kWPR) == 0) rowa[b * p.TH + ly] = (uint8_t)a;
+            if (lane < ntiles)
+              acc[k] = pack_half64(stage32, ly * p.pitch + a + lane * 64u + (vr % kWPR) * 32u);
+          }
+        } else if constexpr (kRPW == 1) {
           const uint32_t ly = vr;
           const uint32_t a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
           if (lane == 0 && ly < p.TH) rowa[b * p.TH + ly] = (uint8_t)a;
@@ -603,7 +645,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       transpose32_n<kR>(acc, keep, rot);
 #pragma unroll
       for (int k = 0; k < kR; ++k)
-        if (v0r + k * nw < VR) win[(v0r + k * nw) * 32u + lane] = acc[k];
+        if (vrow(u0, k) < VR) win[vrow(u0, k) * 32u + lane] = acc[k];
     }
     if (warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp];
@@ -626,13 +668,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
                         &mbar[b ^ 1u], lane);
 
     // Rule, inverse transpose and write-back of the own rows.
-    for (uint32_t v0r = warp; v0r < VR; v0r += kR * nw) {
+    for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
       uint32_t y[kR];
 #pragma unroll
       for (int k = 0; k < kR; ++k) {
-        const uint32_t c = (v0r + k * nw) * 32u + lane;
+        const uint32_t c = vrow(u0, k) * 32u + lane;
         uint32_t next = 0;
-        if (v0r + k * nw < VR) {
+        if (vrow(u0, k) < VR) {
           const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(p.refs) + c);
           const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
           uint32_t n[8];
@@ -648,8 +690,14 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       transpose32_n<kR>(y, keep, rot);
 #pragma unroll
       for (int k = 0; k < kR; ++k) {
-        const uint32_t vr = v0r + k * nw;
-        if constexpr (kRPW == 1) {
+        const uint32_t vr = vrow(u0, k);
+        if constexpr (kWPR > 1) {
+          if (vr < VR && lane < ntiles) {
+            const uint32_t ly = vr / kWPR;
+            unpack_half64(stage32w, ly * p.pitch + rowa[b * p.TH + ly] + lane * 64u +
+                                        (vr % kWPR) * 32u, y[k]);
+          }
+        } else if constexpr (kRPW == 1) {
           const uint32_t ly = vr;
           if (ly < p.TH)
             unpack_row<kTW>(stage32w, stage, y[k] & valid,
@@ -666,8 +714,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       __syncwarp();
       // Tile row of entry rr of this write-back batch (rr < kRR), or >= TH.
       auto row_of = [&](uint32_t rr) -> uint32_t {
-        const uint32_t vr = v0r + (rr / kRPW) * nw;
-        return vr < VR ? vr * kRPW + rr % kRPW : p.TH;
+        if constexpr (kRPW > 1) {
+          const uint32_t vr = u0 + (rr / kRPW) * nw;
+          return vr < VR ? vr * kRPW + rr % kRPW : p.TH;
+        } else {
+          const uint32_t ly = u0 + rr * nw;   // a unit is a tile row
+          return ly < p.TH ? ly : p.TH;
+        }
       };
       // Carried chunks: take the previous group's tail bytes in front of the
       // row (staging offsets [0, a)), hand this row's tail on.
@@ -775,12 +828,14 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
     const TiledDev &d = devs[w.instance];
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
-    const uint32_t kind = d.rpw == 4 ? 8u : (d.rpw == 2 ? 16u : (d.TW == 27 || d.TW == 25 ? d.TW : 0u));
+    const uint32_t kind =
+        d.rpw == 4 ? 8u : (d.rpw == 2 ? 16u : (d.TW == 27 || d.TW == 25 || d.TW == 64 ? d.TW : 0u));
     switch (kind) {
       case 27: run_groups<kLife, 27>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
       case 25: run_groups<kLife, 25>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
       case 8: run_groups<kLife, 8>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
       case 16: run_groups<kLife, 16>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
+      case 64: run_groups<kLife, 64>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
       default: run_groups<kLife, 0>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
     }
   }
@@ -818,18 +873,21 @@ const void *batch_kernel_for(bool life) {
   return life ? (const void *)step_batch_kernel<true> : (const void *)step_batch_kernel<false>;
 }
 
-// The instantiation for a program: rows shared by slot words (rpw 4 or 2)
-// have their own, as have the common widths 27 (triangle) and 25 (Vicsek).
+// The instantiation for a program: rows shared by slot words (rpw 4 or 2) and
+// rows of two slot words (width 64) have their own, as have the common widths
+// 27 (triangle) and 25 (Vicsek).
 const void *tiled_kernel_for(bool life, uint32_t TW, uint32_t rpw) {
   if (life) {
     if (rpw == 4) return (const void *)step_tiled_kernel<true, 8>;
     if (rpw == 2) return (const void *)step_tiled_kernel<true, 16>;
+    if (TW == 64) return (const void *)step_tiled_kernel<true, 64>;
     if (TW == 27) return (const void *)step_tiled_kernel<true, 27>;
     if (TW == 25) return (const void *)step_tiled_kernel<true, 25>;
     return (const void *)step_tiled_kernel<true, 0>;
   }
   if (rpw == 4) return (const void *)step_tiled_kernel<false, 8>;
   if (rpw == 2) return (const void *)step_tiled_kernel<false, 16>;
+  if (TW == 64) return (const void *)step_tiled_kernel<false, 64>;
   if (TW == 27) return (const void *)step_tiled_kernel<false, 27>;
   if (TW == 25) return (const void *)step_tiled_kernel<false, 25>;
   return (const void *)step_tiled_kernel<false, 0>;
@@ -927,7 +985,7 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   d.nhalo = sp.nhalo;
   d.nwin = (3u + sp.TW + 3u) / 4u;
   d.valid = 0;
-  for (uint32_t lx = 0; lx < sp.rpw * sp.TW; ++lx) d.valid |= 1u << lane_of(lx);
+  for (uint32_t lx = 0; lx < sp.rpw * sp.TW && lx < 32; ++lx) d.valid |= 1u << lane_of(lx);
   d.rpw = sp.rpw;
   d.dir_mask = sp.dir_mask;
   d.ndirs = sp.ndirs;
@@ -959,9 +1017,17 @@ void sq_tiled_free(TiledProgram *p) {
   delete p;
 }
 
+uint32_t count_halo(const FracDev &f, uint32_t L);
+
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
-  return level >= 1 && level <= h->f.r && ipow(h->f.k, (level + 1) / 2) <= 32 &&
-         ipow(h->f.k, level / 2) <= 4096;
+  const uint64_t TW = ipow(h->f.k, (level + 1) / 2), TH = ipow(h->f.k, level / 2);
+  const uint64_t side = ipow(h->f.s, level);
+  if (level < 1 || level > h->f.r || (TW > 32 && TW != 64) || TH > 4096 || side * side > (1ull << 24))
+    return false;
+  // the program's shared memory must fit one CTA
+  const uint32_t slots = (uint32_t)TH * (TW == 64 ? 64u : 32u);
+  return smem_for(slots, count_halo(h->f, level), (uint32_t)TH, pitch_for((uint32_t)TW)) <=
+         kTiledSmemLimit;
 }
 
 // Largest level whose tile rows fit one 32-bit word and whose shared memory
@@ -1003,8 +1069,8 @@ int sq_tiled_default_level_for(const FracDev &f) {
   int best = -1;
   for (uint32_t L = 1; L <= f.r; ++L) {
     uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2), side = ipow(f.s, L);
-    if (TW > 32 || TH > 4096 || side * side > (1ull << 24)) break;
-    uint32_t slots = (uint32_t)TH * 32;
+    if ((TW > 32 && TW != 64) || TH > 4096 || side * side > (1ull << 24)) break;
+    uint32_t slots = (uint32_t)TH * (TW == 64 ? 64 : 32);
     size_t sm = smem_for(slots, count_halo(f, L), (uint32_t)TH, pitch_for((uint32_t)TW));
     if (sm <= kTiledSmemCap) best = (int)L;
   }
@@ -1015,7 +1081,7 @@ void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
   uint64_t TW = ipow(f.k, (L + 1) / 2), TH = ipow(f.k, L / 2), side = ipow(f.s, L);
   z.box = side * side;
   z.cells = TW * TH;
-  z.slots = TH * 32;
+  z.slots = TH * (TW == 64 ? 64 : 32);
   z.halo = 8 * z.cells;
 }
 
@@ -1025,11 +1091,13 @@ void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
 int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp) {
   if (L == 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
   uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
-  if (TW64 > 32 || TH64 > 4096) return SQUEEZE_ERR_UNSUPPORTED;  // a tile row must fit one word
+  // a tile row must fit one slot word, or be exactly two (width 64)
+  if ((TW64 > 32 && TW64 != 64) || TH64 > 4096) return SQUEEZE_ERR_UNSUPPORTED;
   uint32_t TW = (uint32_t)TW64, TH = (uint32_t)TH64;
-  // Narrow power-of-two rows share a slot word: 32 / TW tile rows per word.
-  const uint32_t rpw = rows_per_word(TW, TH);
-  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH / rpw * 32;
+  // Narrow power-of-two rows share a slot word: 32 / TW tile rows per word;
+  // 64-wide rows take two words (left and right half).
+  const uint32_t rpw = rows_per_word(TW, TH), wpr = TW == 64 ? 2u : 1u;
+  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L), slots = TH * wpr / rpw * 32;
   if ((uint64_t)side * side > B.box_cap || cells > B.cells_cap || slots > B.slots_cap)
     return SQUEEZE_ERR_UNSUPPORTED;
   if ((uint64_t)TH * f.W > 0xFFFFFFFFull) return SQUEEZE_ERR_UNSUPPORTED;
@@ -1041,6 +1109,7 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
     inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
   auto slot_of = [&](uint32_t c) {
+    if (wpr == 2) return (c / TW * 2u + c % TW / 32u) * 32u + lane_of(c % TW % 32u);
     return (c / TW / rpw) * 32u + lane_of((c / TW % rpw) * TW + c % TW);
   };
   const uint32_t kNone = 0xFFFFFFFFu;
@@ -1123,11 +1192,14 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.groups = (uint64_t)sp.groups_per_band * sp.tiles_y;
   sp.pitch = pitch_for(TW);
   sp.smem = smem_for(slots, nhalo, TH, sp.pitch);
-  if (sp.groups >= (1ull << 32) || sp.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
+  if (sp.groups >= (1ull << 32) || sp.smem > kTiledSmemLimit) return SQUEEZE_ERR_UNSUPPORTED;
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
   // Shared slot words: two slot rows per warp, 4..8 warps.
   int best_w = 8;
-  if (rpw > 1) {
+  if (wpr > 1) {
+    // two tile rows (four slot rows) per warp and pass
+    best_w = (int)((TH + 1) / 2) < 4 ? 4 : ((int)((TH + 1) / 2) > 8 ? 8 : (int)((TH + 1) / 2));
+  } else if (rpw > 1) {
     const int vr = (int)(TH / rpw);
     best_w = (vr + 1) / 2 < 4 ? 4 : ((vr + 1) / 2 > 8 ? 8 : (vr + 1) / 2);
   } else {

@@ -163,17 +163,18 @@ def test_tiled_every_tile_level_s3(f, r, levels):
 
 
 # Fractals whose tile rows are 8 or 16 cells wide, where 4 or 2 tile rows share
-# one slot word: a two-replica diagonal (k = 2: widths 8 at L = 5, 6 and 16 at
-# L = 7, 8), the hole-free s = 2 fractal (k = 4: width 16 at L = 3, 4), the
-# hole-free s = 4 fractal (k = 16: width 16, one row at L = 1, 16 rows at L = 2)
-# and the carpet at r = 8 (width 8, 8 rows at L = 2; 16 groups per band, so a
-# CTA's run hands row ends from group to group).
+# one slot word, or 64 cells wide, where a row takes two slot words: a
+# two-replica diagonal (k = 2: widths 8 at L = 5, 6, 16 at L = 7, 8 and 64 at
+# L = 11, 12), the hole-free s = 2 fractal (k = 4: width 16 at L = 3, 4, 64 at
+# L = 5), the hole-free s = 4 fractal (k = 16: width 16, one row at L = 1, 16
+# rows at L = 2) and the carpet at r = 8 (width 8, 8 rows at L = 2; width 64 at
+# L = 3; several groups per band, so a CTA's run hands row ends on).
 DIAG2 = I.Fractal("diagonal2", 2, 2, ((0, 0), (1, 1)))
 FULL4 = I.Fractal("full4", 4, 16, tuple((x, y) for y in range(4) for x in range(4)))
 
 
-@pytest.mark.parametrize("f,r,levels", [(DIAG2, 12, [4, 5, 6, 7, 8]), (I.FULL2, 9, [2, 3, 4]),
-                                        (FULL4, 5, [1, 2]), (I.CARPET, 8, [1, 2])],
+@pytest.mark.parametrize("f,r,levels", [(DIAG2, 12, [4, 5, 6, 7, 8, 11]), (I.FULL2, 9, [2, 3, 4, 5]),
+                                        (FULL4, 5, [1, 2]), (I.CARPET, 8, [1, 2, 3])],
                          ids=["diagonal2", "full2", "full4", "carpet8"])
 def test_tiled_shared_slot_words(f, r, levels):
     with sq.Handle(f, r) as h:
@@ -185,6 +186,11 @@ def test_tiled_shared_slot_words(f, r, levels):
             assert np.array_equal(run_steps(h, c0, 1, sq.SQUEEZE_STEP_TILED),
                                   oracle.run_compact(f, r, c0, 1)), level
         assert_status_ok(h)
+        if f is DIAG2:
+            # 64 rows of 64 cells: the staging buffers alone exceed one CTA's shared memory
+            with pytest.raises(sq.SqueezeError) as e:
+                sq.squeeze_set_tiled_level(h.h, 12)
+            assert e.value.code == sq.SQUEEZE_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("rule", [(1 << 3, (1 << 2) | (1 << 3)), (1 << 2, 0), ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),
