@@ -118,11 +118,17 @@ def time_config(instances, levels, threads, ctas_per_sm, steps=6) -> float:
 
 
 def _level_candidates(f, max_r):
+    """The three largest tile levels the library accepts for fractal f."""
     out = []
     for L in range(1, max_r + 1):
         width = f.k ** ((L + 1) // 2)   # tile-row width: one slot word, or exactly two
         if width > 64 or (32 < width < 64):
             break
+        with sq.Handle(f, L) as h:      # the program's size depends on f and L only
+            try:
+                sq.squeeze_set_tiled_level(h.h, L)
+            except sq.SqueezeError:
+                break
         out.append(L)
     return out[-3:]
 
