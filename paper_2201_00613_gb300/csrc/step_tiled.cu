@@ -291,17 +291,32 @@ __device__ __forceinline__ uint64_t tile_base(const TiledDev &p, uint32_t TW, ui
 }
 
 // Halo words h0 .. h1-1 (one direction): bit `lane` of word h is the state of
-// halo reference h of the lane's adjacent tile t (dead for t = ~0).  The
-// bytes are loaded four at a time before their ballots, so the loads of a
-// direction with many halo cells overlap.
+// halo reference h of the lane's adjacent tile t (dead for t = ~0).  With
+// kBatch > 1 the bytes are loaded kBatch at a time before their ballots, so
+// the loads of a direction with many halo cells overlap (the carpet's sides);
+// directions with one or two cells (triangle, Vicsek) take the plain loop.
+template <int kBatch>
 __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint32_t t,
                                             uint32_t h0, uint32_t h1, const uint32_t *hoff,
                                             uint32_t *words, const uint8_t *in, unsigned lane) {
   const uint64_t base = tile_base(p, TW, t);
-  for (uint32_t h = h0; h < h1; h += 4) {
-    uint32_t v[4];
+  if constexpr (kBatch == 1) {
+    for (uint32_t h = h0; h < h1; ++h) {
+      bool alive = false;
+      if (base != ~0ull) {
+        const uint64_t a = base + hoff[h];
+        if (a < p.total) alive = __ldg(in + a) & 1u;
+        else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+      }
+      const uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
+      if (lane == 0) words[h] = word;
+    }
+    return;
+  }
+  for (uint32_t h = h0; h < h1; h += kBatch) {
+    uint32_t v[kBatch];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kBatch; ++i) {
       v[i] = 0;
       if (h + i < h1 && base != ~0ull) {
         const uint64_t a = base + hoff[h + i];
@@ -310,7 +325,7 @@ __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kBatch; ++i) {
       if (h + i < h1) {
         const uint32_t word = __ballot_sync(0xFFFFFFFFu, v[i] & 1u);
         if (lane == 0) words[h + i] = word;
@@ -509,6 +524,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   constexpr int kR = kRPW > 1 ? 2 : (kWPR > 1 ? 4 : kRowsInFlight);
   constexpr uint32_t kRR = kRPW > 1 ? (uint32_t)kR * kRPW : (uint32_t)kR / kWPR;
   constexpr uint32_t kU = (uint32_t)kR / kWPR;   // units per pass
+  constexpr int kHaloBatch = kTW == 27 || kTW == 25 ? 1 : 4;
   const uint32_t slots = p.slots, nhalo = p.nhalo;
   const uint32_t TW = kTW ? (uint32_t)kTW : p.TW;
   const uint32_t VR = p.TH * kWPR / kRPW;   // slot rows
@@ -590,7 +606,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
     }
     for (uint32_t j = warp + nw; j < p.ndirs; j += nw)
-      gather_halo(p, TW, adjacent_of(p, G, j, lane), p.halo_start[j], p.halo_start[j + 1], hoff,
+      gather_halo<kHaloBatch>(p, TW, adjacent_of(p, G, j, lane), p.halo_start[j], p.halo_start[j + 1], hoff,
                   win + slots, in, lane);
 
     mbar_wait(&mbar[b], (it >> 1) & 1u, p.status);
@@ -657,7 +673,8 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         }
       }
       if (h0 + h_pre < p.halo_start[warp + 1])
-        gather_halo(p, TW, t_cur, h0 + h_pre, p.halo_start[warp + 1], hoff, win + slots, in, lane);
+        gather_halo<kHaloBatch>(p, TW, t_cur, h0 + h_pre, p.halo_start[warp + 1], hoff, win + slots,
+                                in, lane);
       t_cur = t_next;
     }
     // The only CTA barrier of the group: all words (rows and halo) are in
@@ -688,20 +705,26 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         y[k] = next;
       }
       transpose32_n<kR>(y, keep, rot);
+      // Row offsets first: a shared load after the unpack's stores would wait for them.
+      uint32_t arow[kR];
+#pragma unroll
+      for (int k = 0; k < kR; ++k) {
+        const uint32_t ly = kWPR > 1 ? vrow(u0, k) / kWPR : vrow(u0, k);
+        arow[k] = kRPW == 1 && vrow(u0, k) < VR ? rowa[b * p.TH + ly] : 0u;
+      }
 #pragma unroll
       for (int k = 0; k < kR; ++k) {
         const uint32_t vr = vrow(u0, k);
         if constexpr (kWPR > 1) {
           if (vr < VR && lane < ntiles) {
             const uint32_t ly = vr / kWPR;
-            unpack_half64(stage32w, ly * p.pitch + rowa[b * p.TH + ly] + lane * 64u +
-                                        (vr % kWPR) * 32u, y[k]);
+            unpack_half64(stage32w, ly * p.pitch + arow[k] + lane * 64u + (vr % kWPR) * 32u, y[k]);
           }
         } else if constexpr (kRPW == 1) {
           const uint32_t ly = vr;
           if (ly < p.TH)
-            unpack_row<kTW>(stage32w, stage, y[k] & valid,
-                            ly * p.pitch + rowa[b * p.TH + ly] + lane * TW, TW, lane, ntiles);
+            unpack_row<kTW>(stage32w, stage, y[k] & valid, ly * p.pitch + arow[k] + lane * TW, TW,
+                            lane, ntiles);
         } else if (vr < VR && lane < ntiles) {
 #pragma unroll
           for (uint32_t i = 0; i < kRPW; ++i) {
@@ -712,14 +735,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         }
       }
       __syncwarp();
-      // Tile row of entry rr of this write-back batch (rr < kRR), or >= TH.
+      // Tile row of entry rr of this write-back batch (rr < kRR); >= TH past the end.
       auto row_of = [&](uint32_t rr) -> uint32_t {
         if constexpr (kRPW > 1) {
           const uint32_t vr = u0 + (rr / kRPW) * nw;
           return vr < VR ? vr * kRPW + rr % kRPW : p.TH;
         } else {
-          const uint32_t ly = u0 + rr * nw;   // a unit is a tile row
-          return ly < p.TH ? ly : p.TH;
+          return u0 + rr * nw;   // a unit is a tile row (>= TH past the end)
         }
       };
       // Carried chunks: take the previous group's tail bytes in front of the
