@@ -1,6 +1,7 @@
 """Run the compact step on one level for profiler captures.
 
   python -m paper_2201_00613_gb300.profile_step --level 18 --steps 3 [--kind tiled|alu|tc]
+      [--fractal triangle|carpet|vicsek] [--maps N]
 
 Initialises the seeded Bernoulli(0.5) triangle state at the given level and
 runs `steps` steps, one kernel launch per step.  Used with ncu on a case that
@@ -24,9 +25,28 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--kind", default="tiled", choices=sorted(KINDS))
     p.add_argument("--fractal", default="triangle", choices=sorted(FRACTALS))
+    p.add_argument("--maps", type=int, default=0,
+                   help="first run lambda then nu over this many seeded points (with --kind tc "
+                        "on the tensor cores, else on the ALU)")
     a = p.parse_args(argv)
     f = FRACTALS[a.fractal]
     with sq.Handle(f, a.level) as h:
+        if a.maps:
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(I.R20_SAMPLE_SEED)
+            om = torch.randint(0, h.cells, (a.maps,), generator=gen, dtype=torch.int64, device="cuda")
+            xy = torch.empty((a.maps, 2), dtype=torch.int32, device="cuda")
+            back = torch.empty_like(om)
+            if a.kind == "tc":
+                sq.squeeze_map_tc(h.h, 0, om, xy, a.maps, sq.SQUEEZE_MAP_TC_BF16)
+                sq.squeeze_map_tc(h.h, 1, xy, back, a.maps, sq.SQUEEZE_MAP_TC_BF16)
+            else:
+                sq.squeeze_lambda(h.h, om, xy, a.maps)
+                sq.squeeze_nu(h.h, xy, back, a.maps)
+            torch.cuda.synchronize()
+            if not torch.equal(back, om):
+                print("nu(lambda(omega)) != omega")
+                return 1
         s0 = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
         s1 = torch.empty_like(s0)
         sq.squeeze_init_bernoulli(h.h, s0, 3, I.p_q24(0.5))
