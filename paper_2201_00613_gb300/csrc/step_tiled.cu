@@ -8,24 +8,26 @@
 // once, on the host, for the level-L fractal, and stored as a table of up to
 // 8 local neighbour references per local cell.  A neighbour that falls in an
 // adjacent level-L block is a "halo" reference (direction, local cell there);
-// whether that block is a tile, a hole or off the box is decided per tile on
-// the device by a carry walk over the tile's higher replica digits (the
-// digit-level form of nu, Sec. 3.4), which stops at the first level without
-// a carry.
+// whether that block is a tile, a hole or off the box is decided once per
+// handle on the device by a carry walk over each tile's higher replica digits
+// (the digit-level form of nu, Sec. 3.4, which stops at the first level
+// without a carry) and kept as an adjacency table.
 //
-// A CTA owns a group of up to 32 tiles lying side by side in compact x.  It
-// stages their bytes in shared memory; each lane packs one tile row (<= 32
-// cells) into a 32-bit word and a 5-stage shuffle butterfly transposes the
-// warp's 32 words, so that bit i of a word is the state of one local cell in
-// tile i.  The rule then runs on whole words with a bit-sliced adder (32
+// A CTA owns a group of up to 32 tiles lying side by side in compact x.  TMA
+// bulk copies stage their rows in shared memory; each lane packs one tile row
+// (<= 32 cells) into a 32-bit word and a 5-stage shuffle butterfly transposes
+// the warp's 32 words, so that bit i of a word is the state of one local cell
+// in tile i.  The rule then runs on whole words with a bit-sliced adder (32
 // cells per bitwise operation); the inverse transpose and an unaligned,
-// merged write-back return the bytes to the staging rows.  Reads and writes
-// of the compact buffers are coalesced 16-byte accesses; only halo bytes are
+// merged unpack return the bytes to the staging rows, and TMA bulk stores
+// write them back.  Rows 8 or 16 cells wide share a word (4 or 2 rows per
+// word); rows 64 cells wide take two words.  Only halo bytes are read with
 // single-byte loads.
 //
 // Bit order of a packed row word: bit 8b + j holds tile-row byte 4j + b (the
 // order the pack produces for free); the neighbour program is built in that
-// order, with slot p = 32 * ly + (8 * (lx & 3) + (lx >> 2)).
+// order, with slot p = 32 * ly + (8 * (lx & 3) + (lx >> 2)) for one row per
+// word (rows sharing a word or split over two words extend lx accordingly).
 #include <stdlib.h>
 #include <string.h>
 
@@ -496,9 +498,11 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
 // The caller is instantiated for the common tile-row widths so that the word
 // counts of a row are compile-time constants; kTW = 0 takes TW at run time.
 //
-// Work split inside the CTA: warp w owns rows ly = w, w + nw, ... of every
-// group, from packing through the rule to the write-back, and keeps
-// kRowsInFlight of them in flight.  The word array is double-buffered by
+// Work split inside the CTA: warp w owns units u = w, w + nw, ... of every
+// group (a unit is a slot row, i.e. one tile row or the rows sharing one
+// word, or for 64-wide rows one tile row of two slot rows), from packing
+// through the rule to the write-back, and keeps several slot rows in flight.
+// The word array is double-buffered by
 // group, so one CTA barrier per group suffices (before the rule reads the
 // words): a warp that passed it knows every warp finished the group before,
 // whose word buffer and staging buffer may then be reused.  Warp w also
