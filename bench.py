@@ -164,15 +164,26 @@ def run_reference(args, rank):
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
+    sample_s = float(cb["sample"].rsplit(", ", 1)[-1].rstrip(" s"))
+    config = workload_config(None)
+    config.update({"kernel": "cpu oracle (bounding box)", "sample": cb["sample"]})
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD.name, "fractal": "sierpinski_triangle s=2 k=3",
-                       "r": WORKLOAD.r, "cells": WORKLOAD.cells, "ca_steps_per_step": 1,
-                       "sample": cb["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sample_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": config,
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(level, world=1):
+    """The `config` object of both arms' JSON lines."""
+    w = WORKLOAD
+    return {"workload": w.name, "fractal": "sierpinski_triangle s=2 k=3 offsets (0,0),(1,0),(0,1)",
+            "r": w.r, "cells": w.fractal.cells(w.r), "p_alive": w.p, "seed": w.seed,
+            "ca_steps_per_step": w.n_steps, "kernel": "step_tiled", "tile_level": level,
+            "l2": "inputs larger than L2 (2 x 3.49 GB)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def replica_max(x, world, device):
@@ -291,11 +302,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic",
-            "config": {"workload": w.name, "fractal": "sierpinski_triangle s=2 k=3 offsets (0,0),(1,0),(0,1)",
-                       "r": w.r, "cells": cells, "p_alive": w.p, "seed": w.seed,
-                       "ca_steps_per_step": w.n_steps, "kernel": "step_tiled",
-                       "tile_level": level, "l2": "inputs larger than L2 (2 x 3.49 GB)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(level, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,

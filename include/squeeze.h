@@ -199,7 +199,10 @@ typedef struct {
 /* squeeze_batch_create -- validate the items, prepare every handle's tiled
  * program, build the schedule and copy the descriptors to the device.  The
  * handles' rules and tile levels are read now: later changes need a new
- * batch.  The handles and buffers must outlive the batch. */
+ * batch.  The handles and buffers must outlive the batch.  INVALID_ARG for a
+ * null, misaligned or overlapping item; UNSUPPORTED when the items' programs
+ * together need more shared memory than one CTA may use; OOM / CUDA when a
+ * device allocation or copy fails (nothing is left allocated then). */
 int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out);
 
 /* squeeze_batch_configure -- launch shape chosen by the autotuner: threads per
