@@ -134,6 +134,48 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def _cpu_model():
+    """CPU model from /proc/cpuinfo (model name on x86, implementer/part on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return None
+    for key in ("model name", "Model", "CPU part"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    return None
+
+
+_R10_TIMER = """
+import json, sys, time
+sys.path.insert(0, %r)
+import oracle
+from paper_2201_00613_gb300 import inputs as I
+w = I.TRIANGLE_R10
+m = oracle.member_grid(w.fractal, w.r)
+box = oracle.box_init(w.fractal, w.r, w.seed, I.p_q24(w.p))
+t0 = time.perf_counter()
+oracle.box_run(m, box, w.n_steps)
+dt = time.perf_counter() - t0
+print(json.dumps({"cells_per_s": w.fractal.cells(w.r) * w.n_steps / dt, "threads": oracle.threads()}))
+"""
+
+
+def oracle_r10_timing():
+    """The oracle on the small triangle workload (r = 10, 100 steps), on one
+    core and on all cores (separate processes: OpenMP fixes its thread count
+    at start-up)."""
+    out = {}
+    for name, env in (("one_core", {"OMP_NUM_THREADS": "1"}), ("all_cores", {})):
+        res = subprocess.run([sys.executable, "-c", _R10_TIMER % ROOT], capture_output=True,
+                             text=True, env=dict(os.environ, **env), timeout=300)
+        if res.returncode == 0 and res.stdout.strip():
+            out[name] = json.loads(res.stdout.strip().splitlines()[-1])
+    return out
+
+
 def cpu_oracle_baseline(seconds_hint=True):
     """The oracle as it stands, on all host cores, on a bounded sample of the
     workload: the level-CPU_SAMPLE_LEVEL top-left sub-replica of the level-20
@@ -295,6 +337,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_baseline()
+        cpu["cpu_model"] = _cpu_model()
+        cpu["sierpinski_triangle_r10_100_steps"] = oracle_r10_timing()
 
     if rank == 0:
         line = {
