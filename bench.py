@@ -367,7 +367,8 @@ def main():
 
 
 def bb_compare(sq, torch, dev, stream, steps=20):
-    """Compact tiled step vs the bounding-box kernel at level 16, same GPU.
+    """Compact tiled step vs the bounding-box kernel and the lambda(omega)
+    approach (compact threads over the expanded box) at level 16, same GPU.
     Compact state (86 MB) fits in L2, so L2 is flushed before every timed
     compact step; the box (2 x 4.29 GB) does not."""
     w = COMPARE
@@ -415,12 +416,25 @@ def bb_compare(sq, torch, dev, stream, steps=20):
     bb_ms = q0.elapsed_time(q1)
     bb = h.cells * steps / (bb_ms / 1e3)
     bb_gbs = 2 * h.side * h.side * steps / (bb_ms / 1e3) / 1e9
+    # the lambda(omega) approach on the same boxes (compact threads, expanded memory)
+    g1.copy_(g0)
+    sq.squeeze_lambda_step(h.h, g0, g1, 2, stream)
+    torch.cuda.synchronize()
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
+    sq.squeeze_lambda_step(h.h, g0, g1, steps, stream)
+    l1.record(stream)
+    torch.cuda.synchronize()
+    lam = h.cells * steps / (l0.elapsed_time(l1) / 1e3)
     out = {"workload": w.name, "r": w.r, "steps": steps,
            "compact_cell_updates_per_s": compact,
            "compact_l2": "flushed before every step",
            "compact_resident_cell_updates_per_s": resident,
            "bb_cell_updates_per_s": bb, "bb_box_gbs": bb_gbs,
+           "lambda_approach_cell_updates_per_s": lam,
            "speedup_compact_over_bb": compact / bb,
+           "speedup_compact_over_lambda_approach": compact / lam,
            "memory_bytes": {"compact": 2 * h.cells, "bb": 2 * h.side * h.side}}
     h.close()
     del g0, g1, a, b

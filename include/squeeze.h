@@ -176,6 +176,17 @@ int squeeze_bb_init(const squeeze_handle *h, uint8_t *d_grid, uint64_t seed, uin
 int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
                     uint64_t n_steps, void *stream);
 
+/* squeeze_lambda_step -- the lambda(omega) approach on the same box (Sec. 2):
+ * one thread per compact index omega maps it with lambda and reads its 8
+ * neighbours directly in the box, so no nu is needed but the memory is the
+ * whole n x n box.  Same box format as squeeze_bb_step (bit 0 alive, bit 1
+ * fractal cell, holes 0) and the same results.  Only fractal cells are
+ * written: the holes of d_grid1 must already be 0 (for instance a copy of
+ * the initial d_grid0).  The result is in d_grid0 when n_steps is even and
+ * in d_grid1 when odd; the grids must differ (else INVALID_ARG). */
+int squeeze_lambda_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
+                        uint64_t n_steps, void *stream);
+
 /* squeeze_bb_to_compact -- gather the alive bits of the box into compact order
  * (d_state, k^r bytes of 0/1), for comparing the two representations. */
 int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_t *d_state,

@@ -69,6 +69,8 @@ _SIGS = {
                          ctypes.c_void_p], ctypes.c_int),
     "squeeze_bb_to_compact": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p], ctypes.c_int),
+    "squeeze_lambda_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                             ctypes.c_void_p], ctypes.c_int),
     "squeeze_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)],
                              ctypes.c_int),
     "squeeze_batch_configure": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
@@ -216,6 +218,11 @@ def squeeze_bb_init(h, d_grid, seed: int, p_q24: int, stream=None):
 def squeeze_bb_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
     _check(_load().squeeze_bb_step(h, _ptr(d_grid0), _ptr(d_grid1), n_steps, _stream(stream)),
            "squeeze_bb_step")
+
+
+def squeeze_lambda_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
+    _check(_load().squeeze_lambda_step(h, _ptr(d_grid0), _ptr(d_grid1), n_steps,
+                                       _stream(stream)), "squeeze_lambda_step")
 
 
 def squeeze_bb_to_compact(h, d_grid, d_state, stream=None):

@@ -164,6 +164,41 @@ __global__ void bb_gather_kernel(FracDev f, const uint8_t *__restrict__ grid,
   }
 }
 
+// The lambda(omega) approach (Sec. 2, the compact thread grid over expanded
+// memory): one thread per compact index omega finds its cell with lambda, reads
+// its 8 Moore neighbours directly in the box (holes hold 0, points off the box
+// are skipped) and writes its new state at the same place of the second box.
+// No nu is needed, but the memory is the whole box; holes are never written.
+__global__ void lambda_step_kernel(FracDev f, Rule rule, const uint8_t *__restrict__ in,
+                                   uint8_t *__restrict__ out) {
+  __shared__ SmemTables t;
+  load_tables(t, f);
+  __syncthreads();
+  const uint32_t n = f.n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < f.cells;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t wx, wy, x, y;
+    if (i < (1ull << 32)) {
+      wy = fdiv(f.divW, (uint32_t)i);
+      wx = (uint32_t)i - wy * f.W;
+    } else {
+      wy = (uint32_t)(i / f.W);
+      wx = (uint32_t)(i - (uint64_t)wy * f.W);
+    }
+    lambda_alu(f, t, wx, wy, x, y);
+    uint32_t c = 0;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      if (d == 4) continue;
+      const int64_t qx = (int64_t)x + d % 3 - 1, qy = (int64_t)y + d / 3 - 1;
+      if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
+      c += in[(uint64_t)qy * n + (uint64_t)qx] & 1u;
+    }
+    const uint64_t at = (uint64_t)y * n + x;
+    out[at] = (uint8_t)(2u | apply_rule(rule, in[at] & 1u, c));
+  }
+}
+
 }  // namespace
 }  // namespace sq
 
@@ -194,6 +229,13 @@ int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, 
 int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,
                         cudaStream_t st) {
   bb_gather_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, grid, state);
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_launch_lambda_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
+                          cudaStream_t st) {
+  lambda_step_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, h->rule, in, out);
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }

@@ -260,6 +260,20 @@ int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
   return SQUEEZE_OK;
 }
 
+int squeeze_lambda_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
+                        uint64_t n_steps, void *stream) {
+  if (check_handle(h) || !d_grid0 || !d_grid1 || d_grid0 == d_grid1) return SQUEEZE_ERR_INVALID_ARG;
+  uint8_t *a = d_grid0, *b = d_grid1;
+  for (uint64_t t = 0; t < n_steps; ++t) {
+    int rc = sq_launch_lambda_step(h, a, b, (cudaStream_t)stream);
+    if (rc) return rc;
+    uint8_t *tmp = a;
+    a = b;
+    b = tmp;
+  }
+  return SQUEEZE_OK;
+}
+
 int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_t *d_state,
                           void *stream) {
   if (check_handle(h) || !d_grid || !d_state) return SQUEEZE_ERR_INVALID_ARG;

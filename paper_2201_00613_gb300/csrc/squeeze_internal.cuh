@@ -295,5 +295,7 @@ int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, voi
 int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uint32_t p_q24,
                       cudaStream_t st);
 int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
+int sq_launch_lambda_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
+                          cudaStream_t st);
 int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,
                         cudaStream_t st);

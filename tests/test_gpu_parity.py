@@ -320,6 +320,36 @@ def test_bb_matches_oracle(f, r):
             assert np.array_equal(st.cpu().numpy(), oracle.box_to_compact(f, r, want))
 
 
+@pytest.mark.parametrize("f,r", [(I.TRIANGLE, 10), (I.TRIANGLE, 3), (I.CARPET, 5), (I.VICSEK, 6),
+                                 (I.TRIANGLE_PAPER, 8)],
+                         ids=["triangle10", "triangle3", "carpet5", "vicsek6", "paper8"])
+def test_lambda_approach_matches_oracle(f, r):
+    """The lambda(omega) comparator: compact threads over the expanded box."""
+    seed, pq = 11, I.p_q24(0.45)
+    with sq.Handle(f, r) as h:
+        n = h.side
+        g0 = torch.empty(n * n, dtype=torch.uint8, device=DEV)
+        sq.squeeze_bb_init(h.h, g0, seed, pq)
+        g1 = g0.clone()                     # holes of the second box must be 0
+        box = oracle.box_init(f, r, seed, pq)
+        m = oracle.member_grid(f, r)
+        st = torch.empty(h.cells, dtype=torch.uint8, device=DEV)
+        done = 0
+        for steps in (1, 2, 7):
+            sq.squeeze_lambda_step(h.h, g0, g1, steps - done)
+            if (steps - done) % 2:
+                g0, g1 = g1, g0
+            done = steps
+            want = oracle.box_run(m, box, steps)
+            got = g0.cpu().numpy().reshape(n, n)
+            assert np.array_equal(got & 1, want) and np.array_equal(got >> 1, m), steps
+            sq.squeeze_bb_to_compact(h.h, g0, st)
+            assert np.array_equal(st.cpu().numpy(), oracle.box_to_compact(f, r, want)), steps
+        with pytest.raises(sq.SqueezeError):
+            sq.squeeze_lambda_step(h.h, g0, g0, 1)
+        assert_status_ok(h)
+
+
 # --------------------------------------------------------------------------
 # full-size levels: cross-kernel equality plus sampled light cones
 
@@ -337,19 +367,26 @@ def test_r16_compact_equals_bb_and_light_cone():
         sq.squeeze_bb_init(h.h, g0, w.seed, pq)
         st = torch.empty_like(a)
         alu_a, alu_b = c0.clone(), torch.empty_like(a)
+        l0 = g0.clone()          # the lambda(omega) approach on its own pair of boxes
+        l1 = g0.clone()
         done = 0
         for t in (1, 10, 100):
             sq.squeeze_step(h.h, a, b, t - done, sq.SQUEEZE_STEP_TILED)
             sq.squeeze_bb_step(h.h, g0, g1, t - done)
             sq.squeeze_step(h.h, alu_a, alu_b, t - done, sq.SQUEEZE_MAP_ALU)
+            sq.squeeze_lambda_step(h.h, l0, l1, t - done)
             if (t - done) % 2:
                 a, b = b, a
                 g0, g1 = g1, g0
                 alu_a, alu_b = alu_b, alu_a
+                l0, l1 = l1, l0
             done = t
             sq.squeeze_bb_to_compact(h.h, g0, st)
             assert torch.equal(a, st), t
             assert torch.equal(a, alu_a), t
+            sq.squeeze_bb_to_compact(h.h, l0, st)
+            assert torch.equal(a, st), t
+        del l0, l1
         # light cone at T = 100 on sampled cells
         om = I.random_ints(21, 96, h.cells).astype(np.uint64)
         xy = oracle.lam(f, r, om)
