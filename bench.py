@@ -10,7 +10,8 @@ ranks; the roofline of the step kernel against the measured HBM copy
 bandwidth; the end-to-end rate through the C ABI from and to pinned host
 memory; the same-GPU bounding-box comparison at level 16; the integer-ALU
 maps and per-cell step against their tensor-core (tcgen05) forms at level 20;
-the CPU oracle on a bounded sample; SM clocks sampled during the timed region.
+the block-level layouts at level 16; the CPU oracle on a bounded sample; SM
+clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl squeeze|reference]
 """
@@ -329,10 +330,11 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- same-GPU bounding box at level 16 ----------------------------------
-    compare = maps = None
+    compare = maps = blocks = None
     if not args.no_compare:
         compare = bb_compare(sq, torch, dev, stream)
         maps = map_compare(sq, torch, dev, stream)
+        blocks = block_compare(sq, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -359,6 +361,7 @@ def main():
             "device_status": status,
             "bb_compare": compare,
             "map_compare": maps,
+            "block_compare": blocks,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -438,6 +441,33 @@ def bb_compare(sq, torch, dev, stream, steps=20):
            "memory_bytes": {"compact": 2 * h.cells, "bb": 2 * h.side * h.side}}
     h.close()
     del g0, g1, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def block_compare(sq, torch, dev, stream, steps=20):
+    """Block-level layouts (rho x rho micro-boxes, rho = 2^b) at level 16: bytes
+    per state and cell-updates/s of the block step, next to the compact layout."""
+    w = COMPARE
+    out = {"workload": w.name, "r": w.r, "steps": steps, "unit": "cell-updates/s", "levels": []}
+    with sq.Handle(w.fractal, w.r) as h:
+        for b in range(0, 6):
+            nbytes = sq.squeeze_block_bytes(h.h, b)
+            x = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            y = torch.empty_like(x)
+            sq.squeeze_block_init(h.h, b, x, w.seed, I.p_q24(w.p), stream)
+            sq.squeeze_block_step(h.h, b, x, y, 2, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sq.squeeze_block_step(h.h, b, x, y, steps, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["levels"].append({"rho": 2 ** b, "bytes_per_state": nbytes,
+                                  "cell_updates_per_s": h.cells * steps / (e0.elapsed_time(e1) / 1e3)})
+            del x, y
+        out["status"] = sq.squeeze_device_status(h.h)
     torch.cuda.empty_cache()
     return out
 

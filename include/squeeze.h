@@ -237,6 +237,35 @@ int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream);
 /* squeeze_batch_destroy -- free the batch (not the handles or buffers). */
 int squeeze_batch_destroy(squeeze_batch *b);
 
+/* ---- block-level layout (Sec. 3.5) ----------------------------------------
+ * With rho = s^b, the state is stored as k^(r-b) blocks in the compact order
+ * of level r - b (row-major, k^ceil((r-b)/2) blocks per row), each block the
+ * rho x rho expanded micro-box of its level-b sub-replica, holes included as
+ * 0: k^(r-b) * rho^2 bytes (one byte per cell, alive iff bit 0).  b = 0 is
+ * the compact layout.  b must satisfy b <= r (else INVALID_ARG) and
+ * rho <= 32 (else UNSUPPORTED).  The paper has this layout as its block
+ * variant of Squeeze; the results equal those of the compact layout. */
+
+/* squeeze_block_bytes -- bytes of one block-layout state at level b. */
+int squeeze_block_bytes(const squeeze_handle *h, uint32_t b, uint64_t *bytes);
+
+/* squeeze_block_init -- the seeded Bernoulli start of squeeze_init_bernoulli
+ * (same cells alive) in block layout; micro-box holes are written as 0. */
+int squeeze_block_init(const squeeze_handle *h, uint32_t b, uint8_t *d_blocks, uint64_t seed,
+                       uint32_t p_q24, void *stream);
+
+/* squeeze_block_step -- n_steps rule steps in block layout (one thread per
+ * micro-box cell; neighbours across a block border through the 8 adjacent
+ * blocks, found with lambda and nu at block level).  Result in d_blocks0
+ * when n_steps is even, d_blocks1 when odd; the buffers must differ. */
+int squeeze_block_step(const squeeze_handle *h, uint32_t b, uint8_t *d_blocks0,
+                       uint8_t *d_blocks1, uint64_t n_steps, void *stream);
+
+/* squeeze_block_to_compact -- the same state in compact order (k^r bytes of
+ * 0/1), for comparing layouts. */
+int squeeze_block_to_compact(const squeeze_handle *h, uint32_t b, const uint8_t *d_blocks,
+                             uint8_t *d_state, void *stream);
+
 /* ---- allocation-free step ------------------------------------------------- */
 
 /* squeeze_step_noalloc -- one tiled step (as squeeze_step with

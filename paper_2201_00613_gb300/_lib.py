@@ -71,6 +71,14 @@ _SIGS = {
                                ctypes.c_void_p], ctypes.c_int),
     "squeeze_lambda_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                              ctypes.c_void_p], ctypes.c_int),
+    "squeeze_block_bytes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)],
+                            ctypes.c_int),
+    "squeeze_block_init": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                            ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_block_step": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_block_to_compact": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "squeeze_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)],
                              ctypes.c_int),
     "squeeze_batch_configure": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
@@ -218,6 +226,27 @@ def squeeze_bb_init(h, d_grid, seed: int, p_q24: int, stream=None):
 def squeeze_bb_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
     _check(_load().squeeze_bb_step(h, _ptr(d_grid0), _ptr(d_grid1), n_steps, _stream(stream)),
            "squeeze_bb_step")
+
+
+def squeeze_block_bytes(h, b: int) -> int:
+    out = ctypes.c_uint64(0)
+    _check(_load().squeeze_block_bytes(h, b, ctypes.byref(out)), "squeeze_block_bytes")
+    return out.value
+
+
+def squeeze_block_init(h, b: int, d_blocks, seed: int, p_q24: int, stream=None):
+    _check(_load().squeeze_block_init(h, b, _ptr(d_blocks), seed, p_q24, _stream(stream)),
+           "squeeze_block_init")
+
+
+def squeeze_block_step(h, b: int, d_blocks0, d_blocks1, n_steps: int, stream=None):
+    _check(_load().squeeze_block_step(h, b, _ptr(d_blocks0), _ptr(d_blocks1), n_steps,
+                                      _stream(stream)), "squeeze_block_step")
+
+
+def squeeze_block_to_compact(h, b: int, d_blocks, d_state, stream=None):
+    _check(_load().squeeze_block_to_compact(h, b, _ptr(d_blocks), _ptr(d_state),
+                                            _stream(stream)), "squeeze_block_to_compact")
 
 
 def squeeze_lambda_step(h, d_grid0, d_grid1, n_steps: int, stream=None):
