@@ -242,8 +242,8 @@ int squeeze_batch_destroy(squeeze_batch *b);
  * of level r - b (row-major, k^ceil((r-b)/2) blocks per row), each block the
  * rho x rho expanded micro-box of its level-b sub-replica, holes included as
  * 0: k^(r-b) * rho^2 bytes (one byte per cell, alive iff bit 0).  b = 0 is
- * the compact layout.  b must satisfy b <= r (else INVALID_ARG) and
- * rho <= 32 (else UNSUPPORTED).  The paper has this layout as its block
+ * the compact layout.  b must satisfy b <= r (else INVALID_ARG), rho <= 32
+ * and k^(r-b) < 2^32 blocks (else UNSUPPORTED).  The paper has this layout as its block
  * variant of Squeeze; the results equal those of the compact layout. */
 
 /* squeeze_block_bytes -- bytes of one block-layout state at level b. */

@@ -8,7 +8,9 @@
 // bytes (Sec. 3.5; r_b = r - log_s rho).  A cell's neighbours inside its own
 // block are direct; those across the block border are found through the 8
 // neighbouring blocks, which lambda and nu at block level (Secs. 3.3, 3.4 on
-// the level-r_b fractal) give once per block.  rho = 1 is the compact layout.
+// the level-r_b fractal) give once per block.  The step stages each block with
+// a one-cell ring in shared memory and applies the rule there.  rho = 1 is
+// the compact layout.
 #include "squeeze_internal.cuh"
 
 namespace sq {
@@ -17,12 +19,13 @@ namespace {
 constexpr uint32_t kMaxRho = 32;          // largest micro-box side
 constexpr int kBlockThreads = 256;
 constexpr uint32_t kMaxBlocksPerCta = 28;  // neighbour tables in shared memory
+constexpr uint32_t kTileBytes = 2048;      // micro-boxes with their rings, per CTA pass
 
 struct BlockDev {
   FracDev fb;                 // the level-r_b fractal of blocks
   uint32_t b, rho, rho2;      // block level, micro-box side, cells per block
   uint32_t bpc;               // blocks per CTA pass
-  FastDiv div_rho, div_rho2;
+  FastDiv div_rho, div_rho2, div_side, div_side2;   // rho, rho^2, rho + 2, (rho + 2)^2
   uint8_t mask[kMaxRho * kMaxRho];  // micro-box membership (level-b pattern), row-major
 };
 
@@ -31,8 +34,8 @@ struct BlockDev {
 // off the box.
 __device__ inline uint32_t neighbour_block(const FracDev &fb, const SmemTables &t, uint64_t omega,
                                           int d) {
-  uint32_t wy = (uint32_t)(omega / fb.W), wx = (uint32_t)(omega - (uint64_t)wy * fb.W);
   if (d == 4) return (uint32_t)omega;
+  const uint32_t wy = fdiv(fb.divW, (uint32_t)omega), wx = (uint32_t)omega - wy * fb.W;
   uint32_t X, Y, nx, ny;
   lambda_alu(fb, t, wx, wy, X, Y);
   if (!nu_alu(fb, t, (int32_t)X + d % 3 - 1, (int32_t)Y + d / 3 - 1, nx, ny)) return ~0u;
@@ -45,41 +48,46 @@ __global__ void __launch_bounds__(kBlockThreads) block_step_kernel(BlockDev B, R
   __shared__ SmemTables t;
   __shared__ uint32_t nb[kMaxBlocksPerCta][9];
   __shared__ uint8_t m[kMaxRho * kMaxRho];
+  // each block's micro-box with a one-cell ring from its neighbours, (rho + 2)^2 bytes
+  __shared__ uint8_t tile[kTileBytes];
   load_tables(t, B.fb);
   for (uint32_t i = threadIdx.x; i < B.rho2; i += blockDim.x) m[i] = B.mask[i];
   const uint64_t nblocks = B.fb.cells;
-  const uint32_t rho = B.rho, rho2 = B.rho2, bpc = B.bpc;
+  const uint32_t rho = B.rho, rho2 = B.rho2, bpc = B.bpc, side = rho + 2, side2 = side * side;
   for (uint64_t base = (uint64_t)blockIdx.x * bpc; base < nblocks;
        base += (uint64_t)gridDim.x * bpc) {
-    __syncthreads();  // tables loaded / previous pass done with nb
+    __syncthreads();  // tables loaded / previous pass done with nb and the tiles
     if (threadIdx.x < bpc * 9) {
       const uint32_t j = threadIdx.x / 9, d = threadIdx.x % 9;
       nb[j][d] = base + j < nblocks ? neighbour_block(B.fb, t, base + j, (int)d) : ~0u;
+    }
+    __syncthreads();
+    // Fill the tiles: consecutive threads take consecutive bytes of a tile row.
+    for (uint32_t c = threadIdx.x; c < bpc * side2; c += blockDim.x) {
+      const uint32_t j = fdiv(B.div_side2, c), e = c - j * side2;
+      const uint32_t ty = fdiv(B.div_side, e), tx = e - ty * side;
+      const int qx = (int)tx - 1, qy = (int)ty - 1;
+      const int bx = qx < 0 ? -1 : (qx >= (int)rho ? 1 : 0);
+      const int by = qy < 0 ? -1 : (qy >= (int)rho ? 1 : 0);
+      const uint32_t nbo = base + j < nblocks ? nb[j][(by + 1) * 3 + (bx + 1)] : ~0u;
+      uint8_t v = 0;
+      if (nbo != ~0u) {
+        const uint32_t q = (uint32_t)((qy - by * (int)rho) * (int)rho + (qx - bx * (int)rho));
+        v = in[(uint64_t)nbo * rho2 + q] & 1u;
+      }
+      tile[c] = v;
     }
     __syncthreads();
     for (uint32_t c = threadIdx.x; c < bpc * rho2; c += blockDim.x) {
       const uint32_t j = fdiv(B.div_rho2, c), cell = c - j * rho2;
       const uint64_t omega = base + j;
       if (omega >= nblocks) break;
-      const uint64_t at = omega * rho2 + cell;
-      if (!m[cell]) {  // a hole of the micro-box stays 0
-        out[at] = 0;
-        continue;
-      }
-      const int ly = (int)fdiv(B.div_rho, cell), lx = (int)cell - ly * (int)rho;
-      uint32_t count = 0;
-#pragma unroll
-      for (int d = 0; d < 9; ++d) {
-        if (d == 4) continue;
-        const int qx = lx + d % 3 - 1, qy = ly + d / 3 - 1;
-        const int bx = qx < 0 ? -1 : (qx >= (int)rho ? 1 : 0);
-        const int by = qy < 0 ? -1 : (qy >= (int)rho ? 1 : 0);
-        const uint32_t nbo = nb[j][(by + 1) * 3 + (bx + 1)];
-        if (nbo == ~0u) continue;
-        const uint32_t q = (uint32_t)((qy - by * (int)rho) * (int)rho + (qx - bx * (int)rho));
-        count += in[(uint64_t)nbo * rho2 + q] & 1u;
-      }
-      out[at] = (uint8_t)apply_rule(rule, in[at] & 1u, count);
+      const uint32_t ly = fdiv(B.div_rho, cell), lx = cell - ly * rho;
+      const uint8_t *w = tile + j * side2 + ly * side + lx;   // the 3 x 3 window's top-left
+      const uint32_t count = w[0] + w[1] + w[2] + w[side] + w[side + 2] + w[2 * side] +
+                             w[2 * side + 1] + w[2 * side + 2];
+      out[omega * rho2 + cell] =
+          m[cell] ? (uint8_t)apply_rule(rule, w[side + 1], count) : (uint8_t)0;
     }
   }
 }
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(kBlockThreads) block_init_kernel(BlockDev B, u
     const uint32_t cell = (uint32_t)(i - omega * B.rho2);
     uint8_t v = 0;
     if (B.mask[cell]) {
-      const uint32_t wy = (uint32_t)(omega / B.fb.W), wx = (uint32_t)(omega - (uint64_t)wy * B.fb.W);
+      const uint32_t wy = fdiv(B.fb.divW, (uint32_t)omega), wx = (uint32_t)omega - wy * B.fb.W;
       uint32_t X, Y;
       lambda_alu(B.fb, t, wx, wy, X, Y);
       v = bernoulli_cell(seed, p_q24, X * B.rho + cell % B.rho, Y * B.rho + cell / B.rho);
@@ -144,13 +152,18 @@ int make_block_dev(const squeeze_handle *h, uint32_t b, BlockDev &B) {
   memset(&B, 0, sizeof(B));
   int rc = sq_fill_fractal(f.s, f.k, offsets, f.r - b, B.fb);
   if (rc) return rc;
+  if (B.fb.cells >= (1ull << 32)) return SQUEEZE_ERR_UNSUPPORTED;   // block indices are 32-bit
   B.b = b;
   B.rho = (uint32_t)rho;
   B.rho2 = (uint32_t)(rho * rho);
-  uint32_t bpc = kBlockThreads / B.rho2;
+  // as many blocks per pass as their tiles fit (<= 28: one neighbour lookup per thread)
+  uint32_t bpc = kTileBytes / ((B.rho + 2) * (B.rho + 2));
   B.bpc = bpc < 1 ? 1 : (bpc > kMaxBlocksPerCta ? kMaxBlocksPerCta : bpc);
   B.div_rho = make_fastdiv(B.rho);
   B.div_rho2 = make_fastdiv(B.rho2);
+  B.div_side = make_fastdiv(B.rho + 2);
+  B.div_side2 = make_fastdiv((B.rho + 2) * (B.rho + 2));
+  if ((uint64_t)B.bpc * (B.rho + 2) * (B.rho + 2) > kTileBytes) return SQUEEZE_ERR_UNSUPPORTED;
   // micro-box membership: every base-s digit pair of (x, y) below level b is an offset
   for (uint32_t y = 0; y < rho; ++y)
     for (uint32_t x = 0; x < rho; ++x) {
