@@ -64,6 +64,8 @@ def _load():
             lib.orc_box_init.argtypes = [u32, u32, p, u32, u64, u32, p]
             lib.orc_lightcone.argtypes = [u32, u32, p, u32, u64, u32, i64, u32, u32, p, i64, p]
             lib.orc_threads.restype = ctypes.c_int
+            lib.orc_box_run_nbhd.argtypes = [i64, p, p, p, i64, u32, u32, u32]
+            lib.orc_heat_run.argtypes = [i64, p, p, p, i64, ctypes.c_double, u32]
             _lib = lib
     return _lib
 
@@ -147,6 +149,32 @@ def box_run(member_box: np.ndarray, box: np.ndarray, steps: int, rule=B3S23) -> 
     a = np.array(box, dtype=np.uint8, order="C", copy=True)
     b = np.empty_like(a)
     _load().orc_box_run(n, _ptr(m), _ptr(a), _ptr(b), int(steps), rule[0], rule[1])
+    return a
+
+
+MOORE = 0x1EF
+VON_NEUMANN = 0xAA
+
+
+def box_run_nbhd(member_box: np.ndarray, box: np.ndarray, steps: int, rule=B3S23,
+                 nbhd: int = MOORE) -> np.ndarray:
+    """box_run counting only the neighbours in `nbhd` (bit (dy+1)*3+(dx+1))."""
+    n = member_box.shape[0]
+    m = np.ascontiguousarray(member_box, dtype=np.uint8)
+    a = np.array(box, dtype=np.uint8, order="C", copy=True)
+    b = np.empty_like(a)
+    _load().orc_box_run_nbhd(n, _ptr(m), _ptr(a), _ptr(b), int(steps), rule[0], rule[1], nbhd)
+    return a
+
+
+def heat_run(member_box: np.ndarray, u: np.ndarray, steps: int, alpha: float,
+             nbhd: int = VON_NEUMANN) -> np.ndarray:
+    """Explicit heat steps on the fractal graph in fp64 (n x n box, holes 0)."""
+    n = member_box.shape[0]
+    m = np.ascontiguousarray(member_box, dtype=np.uint8)
+    a = np.array(u, dtype=np.float64, order="C", copy=True)
+    b = np.empty_like(a)
+    _load().orc_heat_run(n, _ptr(m), _ptr(a), _ptr(b), int(steps), float(alpha), nbhd)
     return a
 
 

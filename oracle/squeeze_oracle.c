@@ -232,6 +232,75 @@ void orc_box_run(int64_t n, const uint8_t *member, uint8_t *a, uint8_t *b, int64
 }
 
 /* ------------------------------------------------------------------------- */
+/* Other neighbourhoods and a PDE on the fractal (Sec. 1 names stencil
+ * simulations, cellular automata and PDE solvers as the uses of the compact
+ * maps).  A neighbourhood is a 9-bit mask over the 3 x 3 block: bit
+ * (dy + 1) * 3 + (dx + 1) selects offset (dx, dy); bit 4 (the cell itself)
+ * is ignored.  Moore is 0x1EF, von Neumann 0xAA.                            */
+
+static int orc_in_nbhd(uint32_t nbhd, int dx, int dy) {
+    return (dx || dy) && ((nbhd >> ((dy + 1) * 3 + (dx + 1))) & 1u);
+}
+
+/* One outer-totalistic step counting only the fractal neighbours in `nbhd`. */
+void orc_box_step_nbhd(int64_t n, const uint8_t *member, const uint8_t *in, uint8_t *out,
+                       uint32_t birth, uint32_t survive, uint32_t nbhd) {
+#pragma omp parallel for schedule(static)
+    for (int64_t y = 0; y < n; ++y)
+        for (int64_t x = 0; x < n; ++x) {
+            int64_t p = y * n + x;
+            if (!member[p]) { out[p] = 0; continue; }
+            uint32_t c = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!orc_in_nbhd(nbhd, dx, dy)) continue;
+                    int64_t qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
+                    int64_t q = qy * n + qx;
+                    if (member[q] && (in[q] & 1u)) ++c;
+                }
+            uint32_t mask = (in[p] & 1u) ? survive : birth;
+            out[p] = (uint8_t)((mask >> c) & 1u);
+        }
+}
+
+void orc_box_run_nbhd(int64_t n, const uint8_t *member, uint8_t *a, uint8_t *b, int64_t steps,
+                      uint32_t birth, uint32_t survive, uint32_t nbhd) {
+    for (int64_t t = 0; t < steps; ++t) {
+        orc_box_step_nbhd(n, member, a, b, birth, survive, nbhd);
+        uint8_t *tmp = a; a = b; b = tmp;
+    }
+    if (steps % 2) memcpy(b, a, (size_t)(n * n));
+}
+
+/* Explicit Euler steps of the heat equation on the fractal graph, in fp64:
+ * u'(p) = u(p) + alpha * sum over fractal neighbours q of p in `nbhd` of
+ * (u(q) - u(p)); cells off the fractal stay 0.  Result left in `a`.        */
+void orc_heat_run(int64_t n, const uint8_t *member, double *a, double *b, int64_t steps,
+                  double alpha, uint32_t nbhd) {
+    for (int64_t t = 0; t < steps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (int64_t y = 0; y < n; ++y)
+            for (int64_t x = 0; x < n; ++x) {
+                int64_t p = y * n + x;
+                if (!member[p]) { b[p] = 0.0; continue; }
+                double flow = 0.0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!orc_in_nbhd(nbhd, dx, dy)) continue;
+                        int64_t qx = x + dx, qy = y + dy;
+                        if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
+                        int64_t q = qy * n + qx;
+                        if (member[q]) flow += a[q] - a[p];
+                    }
+                b[p] = a[p] + alpha * flow;
+            }
+        double *tmp = a; a = b; b = tmp;
+    }
+    if (steps % 2) memcpy(b, a, (size_t)(n * n) * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------- */
 /* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the stream seeded with `seed`
  * returns, as its output number i (i = 0, 1, ...), mix(seed + (i+1) * gamma)
  * with gamma = 0x9E3779B97F4A7C15 and mix the variant-13 finaliser.          */

@@ -329,3 +329,109 @@ def test_state_is_bit_zero_of_each_byte():
     rng = np.random.default_rng(3)
     raw = rng.integers(0, 256, f.k ** r).astype(np.uint8)
     assert np.array_equal(oracle.run_compact(f, r, raw, 3), oracle.run_compact(f, r, raw & 1, 3))
+
+
+# --------------------------------------------------------------------------
+# Other neighbourhoods and the heat equation (Sec. 1: stencil simulations,
+# cellular automata and PDE solvers on compact fractals)
+
+PLUS = np.array([[0, 1, 0], [1, 0, 1], [0, 1, 0]])
+
+
+def _brute_nbhd_step(member, box, birth, survive, offsets):
+    n = member.shape[0]
+    out = np.zeros_like(box)
+    for y in range(n):
+        for x in range(n):
+            if not member[y, x]:
+                continue
+            c = 0
+            for dx, dy in offsets:
+                qx, qy = x + dx, y + dy
+                if 0 <= qx < n and 0 <= qy < n and member[qy, qx] and box[qy, qx] & 1:
+                    c += 1
+            out[y, x] = ((survive if box[y, x] & 1 else birth) >> c) & 1
+    return out
+
+
+def test_moore_mask_equals_the_life_oracle():
+    f, r = I.TRIANGLE, 6
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, 4, I.p_q24(0.5))
+    assert np.array_equal(oracle.box_run_nbhd(m, box, 5, nbhd=oracle.MOORE), oracle.box_run(m, box, 5))
+
+
+@pytest.mark.parametrize("rule", [oracle.B3S23, ((1 << 1) | (1 << 3), (1 << 1) | (1 << 2))],
+                         ids=["b3s23", "b13s12"])
+def test_von_neumann_on_the_full_box_is_the_textbook_stencil(rule):
+    f, r = I.FULL2, 6
+    n = f.s ** r
+    m = oracle.member_grid(f, r)
+    assert m.all()
+    box = (np.random.default_rng(3).random((n, n)) < 0.4).astype(np.uint8)
+    want = box.copy()
+    for _ in range(4):
+        c = convolve2d(want, PLUS, mode="same", boundary="fill")
+        want = np.where(want == 1, (rule[1] >> c) & 1, (rule[0] >> c) & 1).astype(np.uint8)
+    assert np.array_equal(oracle.box_run_nbhd(m, box, 4, rule, oracle.VON_NEUMANN), want)
+
+
+def test_von_neumann_on_the_triangle_by_brute_force():
+    f, r = I.TRIANGLE, 4
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, 9, I.p_q24(0.6))
+    want = box.copy()
+    for _ in range(3):
+        want = _brute_nbhd_step(m, want, 1 << 2, (1 << 1) | (1 << 2), [(0, -1), (-1, 0), (1, 0), (0, 1)])
+    assert np.array_equal(oracle.box_run_nbhd(m, box, 3, ((1 << 2), (1 << 1) | (1 << 2)),
+                                              oracle.VON_NEUMANN), want)
+
+
+def test_heat_constant_field_and_conservation():
+    f, r = I.TRIANGLE, 7
+    m = oracle.member_grid(f, r)
+    u = np.where(m == 1, 2.5, 0.0)
+    assert np.array_equal(oracle.heat_run(m, u, 10, 0.2), u)
+    rng = np.random.default_rng(5)
+    u = np.where(m == 1, rng.random(m.shape), 0.0)
+    v = oracle.heat_run(m, u, 25, 0.2)
+    assert abs(v.sum() - u.sum()) <= 1e-10 * u.sum()     # the graph Laplacian conserves heat
+    assert np.all(v[m == 0] == 0.0)
+    assert v[m == 1].max() <= u[m == 1].max() + 1e-12   # maximum principle for alpha * 4 <= 1
+    assert v[m == 1].min() >= u[m == 1].min() - 1e-12
+
+
+def test_heat_on_the_full_box_is_the_five_point_stencil():
+    f, r = I.FULL2, 5
+    n = f.s ** r
+    m = oracle.member_grid(f, r)
+    u = np.random.default_rng(6).random((n, n))
+    alpha = 0.15
+    want = u.copy()
+    for _ in range(6):
+        p = np.pad(want, 1)
+        deg = np.pad(np.ones((n, n)), 1)
+        flow = p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:]
+        d = deg[:-2, 1:-1] + deg[2:, 1:-1] + deg[1:-1, :-2] + deg[1:-1, 2:]
+        want = want + alpha * (flow - d * want)
+    assert np.allclose(oracle.heat_run(m, u, 6, alpha), want, rtol=0, atol=1e-12)
+
+
+def test_heat_on_the_triangle_by_brute_force():
+    f, r = I.TRIANGLE, 3
+    n = f.s ** r
+    m = oracle.member_grid(f, r)
+    u = np.where(m == 1, np.arange(n * n, dtype=np.float64).reshape(n, n) % 7, 0.0)
+    want = u.copy()
+    for _ in range(3):
+        nxt = np.zeros_like(want)
+        for y in range(n):
+            for x in range(n):
+                if not m[y, x]:
+                    continue
+                flow = sum(want[y + dy, x + dx] - want[y, x]
+                           for dx, dy in ((0, -1), (-1, 0), (1, 0), (0, 1))
+                           if 0 <= x + dx < n and 0 <= y + dy < n and m[y + dy, x + dx])
+                nxt[y, x] = want[y, x] + 0.25 * flow
+        want = nxt
+    assert np.allclose(oracle.heat_run(m, u, 3, 0.25), want, rtol=0, atol=1e-12)
