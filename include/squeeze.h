@@ -176,6 +176,29 @@ int squeeze_bb_init(const squeeze_handle *h, uint8_t *d_grid, uint64_t seed, uin
 int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
                     uint64_t n_steps, void *stream);
 
+/* ---- other neighbourhoods and a PDE (Sec. 1) -------------------------------
+ * Sec. 1 names stencil simulations, cellular automata and PDE solvers as the
+ * uses of the compact maps. */
+
+/* squeeze_set_neighbourhood -- the neighbourhood every step counts over: a
+ * 9-bit mask over the 3 x 3 block, bit (dy+1)*3 + (dx+1) selecting offset
+ * (dx, dy); SQUEEZE_MOORE (the default) or SQUEEZE_VON_NEUMANN, or any other
+ * set of offsets.  Bit 4 (the cell itself) must be 0; masks of 9 or more
+ * bits are INVALID_ARG.  Rebuilds the tiled program on the next tiled step. */
+#define SQUEEZE_MOORE 0x1EF
+#define SQUEEZE_VON_NEUMANN 0xAA
+int squeeze_set_neighbourhood(squeeze_handle *h, uint32_t mask);
+
+/* squeeze_heat_step -- n_steps explicit Euler steps of the heat equation on
+ * the fractal graph, in fp32: u'(p) = u(p) + alpha * sum over the fractal
+ * neighbours q of p (the handle's neighbourhood) of (u(q) - u(p)).  Holes and
+ * points off the box have no edge, so the sum of u is conserved; with
+ * alpha * (neighbours) <= 1 no value leaves the range of the start.
+ *   d_u0, d_u1  k^r floats each, 4-byte aligned, not overlapping; the result
+ *               is in d_u0 when n_steps is even and in d_u1 when odd. */
+int squeeze_heat_step(const squeeze_handle *h, float *d_u0, float *d_u1, uint64_t n_steps,
+                      float alpha, void *stream);
+
 /* squeeze_lambda_step -- the lambda(omega) approach on the same box (Sec. 2):
  * one thread per compact index omega maps it with lambda and reads its 8
  * neighbours directly in the box, so no nu is needed but the memory is the

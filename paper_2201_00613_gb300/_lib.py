@@ -27,6 +27,9 @@ SQUEEZE_MAP_ALU = 2
 SQUEEZE_MAP_TC_BF16 = 3
 SQUEEZE_MAP_TC_I8 = 4
 
+SQUEEZE_MOORE = 0x1EF
+SQUEEZE_VON_NEUMANN = 0xAA
+
 _lock = threading.Lock()
 _lib = None
 
@@ -71,6 +74,9 @@ _SIGS = {
                                ctypes.c_void_p], ctypes.c_int),
     "squeeze_lambda_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                              ctypes.c_void_p], ctypes.c_int),
+    "squeeze_set_neighbourhood": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_heat_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                           ctypes.c_float, ctypes.c_void_p], ctypes.c_int),
     "squeeze_block_bytes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)],
                             ctypes.c_int),
     "squeeze_block_init": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
@@ -247,6 +253,15 @@ def squeeze_block_step(h, b: int, d_blocks0, d_blocks1, n_steps: int, stream=Non
 def squeeze_block_to_compact(h, b: int, d_blocks, d_state, stream=None):
     _check(_load().squeeze_block_to_compact(h, b, _ptr(d_blocks), _ptr(d_state),
                                             _stream(stream)), "squeeze_block_to_compact")
+
+
+def squeeze_set_neighbourhood(h, mask: int):
+    _check(_load().squeeze_set_neighbourhood(h, mask), "squeeze_set_neighbourhood")
+
+
+def squeeze_heat_step(h, d_u0, d_u1, n_steps: int, alpha: float, stream=None):
+    _check(_load().squeeze_heat_step(h, _ptr(d_u0), _ptr(d_u1), n_steps, alpha, _stream(stream)),
+           "squeeze_heat_step")
 
 
 def squeeze_lambda_step(h, d_grid0, d_grid1, n_steps: int, stream=None):

@@ -35,8 +35,8 @@ __global__ void bb_init_kernel(FracDev f, uint8_t *__restrict__ grid, uint64_t s
   }
 }
 
-// Generic byte-per-thread step (any n).
-__global__ void bb_step_simple(uint32_t n, Rule rule, const uint8_t *__restrict__ in,
+// Generic byte-per-thread step (any n, any neighbourhood mask).
+__global__ void bb_step_simple(uint32_t n, Rule rule, uint32_t nbhd, const uint8_t *__restrict__ in,
                                uint8_t *__restrict__ out) {
   uint64_t total = (uint64_t)n * n;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
@@ -50,7 +50,7 @@ __global__ void bb_step_simple(uint32_t n, Rule rule, const uint8_t *__restrict_
     uint32_t c = 0;
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        if (!dx && !dy) continue;
+        if ((!dx && !dy) || !((nbhd >> ((dy + 1) * 3 + (dx + 1))) & 1u)) continue;
         int64_t qx = (int64_t)x + dx, qy = (int64_t)y + dy;
         if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
         c += in[(uint64_t)qy * n + qx] & 1u;
@@ -189,7 +189,7 @@ __global__ void lambda_step_kernel(FracDev f, Rule rule, const uint8_t *__restri
     uint32_t c = 0;
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
-      if (d == 4) continue;
+      if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
       const int64_t qx = (int64_t)x + d % 3 - 1, qy = (int64_t)y + d / 3 - 1;
       if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
       c += in[(uint64_t)qy * n + (uint64_t)qx] & 1u;
@@ -214,13 +214,14 @@ int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uin
 
 int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st) {
   uint32_t n = h->f.n;
-  if (n % 16 == 0 && ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0)) {
+  if (h->f.nbhd == kMoore && n % 16 == 0 && ((uintptr_t)in % 16 == 0) &&
+      ((uintptr_t)out % 16 == 0)) {
     uint32_t nchunks = n / 16;
     dim3 grid((nchunks + kBBThreads - 1) / kBBThreads, (n + kBBRows - 1) / kBBRows);
     bb_step_swar<<<grid, kBBThreads, 0, st>>>(n, h->rule, in, out);
   } else {
     uint64_t total = (uint64_t)n * n;
-    bb_step_simple<<<grid_for(total, 256), 256, 0, st>>>(n, h->rule, in, out);
+    bb_step_simple<<<grid_for(total, 256), 256, 0, st>>>(n, h->rule, h->f.nbhd, in, out);
   }
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;

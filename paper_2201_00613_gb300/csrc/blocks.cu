@@ -26,6 +26,7 @@ struct BlockDev {
   uint32_t b, rho, rho2;      // block level, micro-box side, cells per block
   uint32_t bpc;               // blocks per CTA pass
   FastDiv div_rho, div_rho2, div_side, div_side2;   // rho, rho^2, rho + 2, (rho + 2)^2
+  uint32_t nbhd;              // the cell neighbourhood (the block lookups always use Moore)
   uint8_t mask[kMaxRho * kMaxRho];  // micro-box membership (level-b pattern), row-major
 };
 
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(kBlockThreads) block_step_kernel(BlockDev B, R
   for (uint32_t i = threadIdx.x; i < B.rho2; i += blockDim.x) m[i] = B.mask[i];
   const uint64_t nblocks = B.fb.cells;
   const uint32_t rho = B.rho, rho2 = B.rho2, bpc = B.bpc, side = rho + 2, side2 = side * side;
+  const uint32_t nbhd = B.nbhd;
   for (uint64_t base = (uint64_t)blockIdx.x * bpc; base < nblocks;
        base += (uint64_t)gridDim.x * bpc) {
     __syncthreads();  // tables loaded / previous pass done with nb and the tiles
@@ -84,8 +86,16 @@ __global__ void __launch_bounds__(kBlockThreads) block_step_kernel(BlockDev B, R
       if (omega >= nblocks) break;
       const uint32_t ly = fdiv(B.div_rho, cell), lx = cell - ly * rho;
       const uint8_t *w = tile + j * side2 + ly * side + lx;   // the 3 x 3 window's top-left
-      const uint32_t count = w[0] + w[1] + w[2] + w[side] + w[side + 2] + w[2 * side] +
-                             w[2 * side + 1] + w[2 * side + 2];
+      uint32_t count;
+      if (nbhd == kMoore) {
+        count = w[0] + w[1] + w[2] + w[side] + w[side + 2] + w[2 * side] + w[2 * side + 1] +
+                w[2 * side + 2];
+      } else {
+        count = 0;
+#pragma unroll
+        for (int d = 0; d < 9; ++d)
+          if (d != 4 && ((nbhd >> d) & 1u)) count += w[(d / 3) * side + d % 3];
+      }
       out[omega * rho2 + cell] =
           m[cell] ? (uint8_t)apply_rule(rule, w[side + 1], count) : (uint8_t)0;
     }
@@ -154,6 +164,7 @@ int make_block_dev(const squeeze_handle *h, uint32_t b, BlockDev &B) {
   if (rc) return rc;
   if (B.fb.cells >= (1ull << 32)) return SQUEEZE_ERR_UNSUPPORTED;   // block indices are 32-bit
   B.b = b;
+  B.nbhd = f.nbhd;
   B.rho = (uint32_t)rho;
   B.rho2 = (uint32_t)(rho * rho);
   // as many blocks per pass as their tiles fit (<= 28: one neighbour lookup per thread)

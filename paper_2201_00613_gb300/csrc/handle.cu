@@ -50,6 +50,7 @@ int sq_fill_fractal(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r, 
   f.divk = sq::make_fastdiv(k);
   f.divs = sq::make_fastdiv(s);
   f.divW = sq::make_fastdiv((uint32_t)W);
+  f.nbhd = sq::kMoore;
   memset(f.hnu, sq::kHole, sizeof(f.hnu));
   for (uint32_t b = 0; b < k; ++b) {
     uint32_t tx = offsets[2 * b], ty = offsets[2 * b + 1];
@@ -138,6 +139,19 @@ int squeeze_set_rule(squeeze_handle *h, uint32_t birth, uint32_t survive) {
     return SQUEEZE_ERR_INVALID_ARG;
   h->rule.birth = birth;
   h->rule.survive = survive;
+  return SQUEEZE_OK;
+}
+
+int squeeze_set_neighbourhood(squeeze_handle *h, uint32_t mask) {
+  if (check_handle(h) || mask >= (1u << 9) || (mask & (1u << 4))) return SQUEEZE_ERR_INVALID_ARG;
+  if (mask == h->f.nbhd) return SQUEEZE_OK;
+  if (h->tiled) {  // the tiled program holds the neighbour references: rebuild it
+    cudaError_t e = cudaDeviceSynchronize();
+    sq_tiled_free(h->tiled);
+    h->tiled = nullptr;
+    if (e != cudaSuccess) return sq_cuda_fail(e);
+  }
+  h->f.nbhd = mask;
   return SQUEEZE_OK;
 }
 
@@ -254,6 +268,23 @@ int squeeze_bb_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
     int rc = sq_launch_bb_step(h, a, b, (cudaStream_t)stream);
     if (rc) return rc;
     uint8_t *tmp = a;
+    a = b;
+    b = tmp;
+  }
+  return SQUEEZE_OK;
+}
+
+int squeeze_heat_step(const squeeze_handle *h, float *d_u0, float *d_u1, uint64_t n_steps,
+                      float alpha, void *stream) {
+  if (check_handle(h) || !d_u0 || !d_u1 || d_u0 == d_u1) return SQUEEZE_ERR_INVALID_ARG;
+  if (((uintptr_t)d_u0 | (uintptr_t)d_u1) & 3u) return SQUEEZE_ERR_INVALID_ARG;
+  const uint64_t n = h->f.cells;
+  if (d_u0 < d_u1 ? d_u0 + n > d_u1 : d_u1 + n > d_u0) return SQUEEZE_ERR_INVALID_ARG;
+  float *a = d_u0, *b = d_u1;
+  for (uint64_t t = 0; t < n_steps; ++t) {
+    int rc = sq_launch_heat_step(h, a, b, alpha, (cudaStream_t)stream);
+    if (rc) return rc;
+    float *tmp = a;
     a = b;
     b = tmp;
   }

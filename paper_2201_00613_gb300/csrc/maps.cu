@@ -81,12 +81,40 @@ __global__ void step_alu_kernel(FracDev f, Rule rule, const uint8_t *__restrict_
     uint32_t c = 0;
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
-      if (d == 4) continue;
+      if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
       int32_t qx = (int32_t)x + d % 3 - 1, qy = (int32_t)y + d / 3 - 1;
       uint32_t nx, ny;
       if (nu_alu(f, t, qx, qy, nx, ny)) c += in[(uint64_t)ny * f.W + nx] & 1u;
     }
     out[i] = (uint8_t)apply_rule(rule, in[i] & 1u, c);
+  }
+}
+
+// Explicit heat diffusion on the fractal graph (Sec. 1 names PDE solvers
+// among the uses of the compact maps): one thread per compact cell finds its
+// place with lambda and its neighbours (the handle's neighbourhood) with nu;
+// holes and points off the box have no edge.  u'(p) = u(p) + alpha * sum over
+// neighbours q of (u(q) - u(p)), in fp32.
+__global__ void heat_step_kernel(FracDev f, float alpha, const float *__restrict__ in,
+                                 float *__restrict__ out) {
+  __shared__ SmemTables t;
+  load_tables(t, f);
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < f.cells;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t wx, wy, x, y;
+    split_omega(f, i, wx, wy);
+    lambda_alu(f, t, wx, wy, x, y);
+    const float u = in[i];
+    float flow = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
+      uint32_t nx, ny;
+      if (nu_alu(f, t, (int32_t)x + d % 3 - 1, (int32_t)y + d / 3 - 1, nx, ny))
+        flow += in[(uint64_t)ny * f.W + nx] - u;
+    }
+    out[i] = u + alpha * flow;
   }
 }
 
@@ -119,6 +147,13 @@ int sq_launch_init(const squeeze_handle *h, uint8_t *state, uint64_t seed, uint3
 int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                        cudaStream_t st) {
   step_alu_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, h->rule, in, out);
+  SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_launch_heat_step(const squeeze_handle *h, const float *in, float *out, float alpha,
+                        cudaStream_t st) {
+  heat_step_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, alpha, in, out);
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }

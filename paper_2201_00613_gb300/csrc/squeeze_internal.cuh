@@ -63,7 +63,11 @@ struct FracDev {
   uint8_t taux[256];   // H_lambda: tau(beta) = (taux[beta], tauy[beta])
   uint8_t tauy[256];
   uint8_t hnu[256];    // H_nu[theta_y * s + theta_x] = beta, or kHole
+  uint32_t nbhd;       // neighbourhood: bit (dy+1)*3+(dx+1) selects offset (dx, dy)
 };
+
+constexpr uint32_t kMoore = 0x1EFu;       // all 8 offsets
+constexpr uint32_t kVonNeumann = 0xAAu;   // the 4 orthogonal offsets
 
 // Tables staged in shared memory by the per-cell kernels.
 struct SmemTables {
@@ -295,6 +299,8 @@ int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, voi
 int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uint32_t p_q24,
                       cudaStream_t st);
 int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
+int sq_launch_heat_step(const squeeze_handle *h, const float *in, float *out, float alpha,
+                        cudaStream_t st);
 int sq_launch_lambda_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                           cudaStream_t st);
 int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,

@@ -1150,7 +1150,8 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
       int64_t qx = (int64_t)B.X[c] + d % 3 - 1, qy = (int64_t)B.Y[c] + d / 3 - 1;
       int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
       int64_t lxp = qx - (int64_t)bx * side, lyp = qy - (int64_t)by * side;
-      int32_t target = inv[(size_t)lyp * side + lxp];
+      // an offset outside the neighbourhood refers to the zero word, like a hole
+      int32_t target = ((f.nbhd >> d) & 1u) ? inv[(size_t)lyp * side + lxp] : -1;
       uint32_t ref = kNone;
       if (target >= 0) {
         if (bx == 0 && by == 0) {

@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(128) tc_kernel(FracDev f, Rule rule, const voi
       const uint32_t d = j < 4 ? j : j + 1;   // skip the centre of the 3 x 3 block
       const int32_t qx = (int32_t)x + (int32_t)(d % 3) - 1, qy = (int32_t)y + (int32_t)(d / 3) - 1;
       const bool ok = nu_row(f, hnu, qx, qy, tile0 + (j >> 1) * kTileBytes, tid, j & 1u);
-      okmask |= (ok ? 1u : 0u) << j;
+      okmask |= (ok && ((f.nbhd >> d) & 1u) ? 1u : 0u) << j;
     }
     sync_for_mma();
     if (*abort_flag) break;
