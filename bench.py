@@ -10,8 +10,9 @@ ranks; the roofline of the step kernel against the measured HBM copy
 bandwidth; the end-to-end rate through the C ABI from and to pinned host
 memory; the same-GPU bounding-box comparison at level 16; the integer-ALU
 maps and per-cell step against their tensor-core (tcgen05) forms at level 20;
-the block-level layouts at level 16; the CPU oracle on a bounded sample; SM
-clocks sampled during the timed region.
+the block-level layouts at level 16; the von Neumann tiled step and fp32 heat
+diffusion; the CPU oracle on a bounded sample; SM clocks sampled during the
+timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl squeeze|reference]
 """
@@ -142,10 +143,18 @@ def _cpu_model():
             info = f.read()
     except OSError:
         return None
-    for key in ("model name", "Model", "CPU part"):
-        for line in info.splitlines():
-            if line.startswith(key):
-                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    parts = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1",
+             "0xd8e": "Neoverse N3", "0xd84": "Neoverse V3"}
+    if "CPU part" in fields:
+        impl = {"0x41": "Arm"}.get(fields.get("CPU implementer", ""), fields.get("CPU implementer", ""))
+        return ("%s %s (part %s)" % (impl, parts.get(fields["CPU part"], "core"), fields["CPU part"])).strip()
     return None
 
 
@@ -330,11 +339,12 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- same-GPU bounding box at level 16 ----------------------------------
-    compare = maps = blocks = None
+    compare = maps = blocks = workloads = None
     if not args.no_compare:
         compare = bb_compare(sq, torch, dev, stream)
         maps = map_compare(sq, torch, dev, stream)
         blocks = block_compare(sq, torch, dev, stream)
+        workloads = workload_compare(sq, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -362,6 +372,7 @@ def main():
             "bb_compare": compare,
             "map_compare": maps,
             "block_compare": blocks,
+            "workload_compare": workloads,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -441,6 +452,44 @@ def bb_compare(sq, torch, dev, stream, steps=20):
            "memory_bytes": {"compact": 2 * h.cells, "bb": 2 * h.side * h.side}}
     h.close()
     del g0, g1, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def workload_compare(sq, torch, dev, stream):
+    """Other neighbourhood workloads: the tiled step over the von Neumann
+    neighbourhood at level 20, and fp32 heat diffusion (per-cell lambda / nu)
+    at level 16."""
+    def timed(fn, steps):
+        fn(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+    out = {"unit": "cell-updates/s"}
+    w = WORKLOAD
+    with sq.Handle(w.fractal, w.r) as h:
+        sq.squeeze_set_neighbourhood(h.h, sq.SQUEEZE_VON_NEUMANN)
+        a = torch.empty(h.cells, dtype=torch.uint8, device=dev)
+        b = torch.empty_like(a)
+        sq.squeeze_init_bernoulli(h.h, a, w.seed, I.p_q24(w.p))
+        t = timed(lambda n: sq.squeeze_step(h.h, a, b, n, sq.SQUEEZE_STEP_TILED, stream), 10)
+        out["von_neumann_tiled_" + w.name] = h.cells * 10 / t
+        del a, b
+    c = COMPARE
+    with sq.Handle(c.fractal, c.r) as h:
+        sq.squeeze_set_neighbourhood(h.h, sq.SQUEEZE_VON_NEUMANN)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(c.seed)
+        u = torch.rand(h.cells, generator=gen, device=dev)
+        v = torch.empty_like(u)
+        t = timed(lambda n: sq.squeeze_heat_step(h.h, u, v, n, 0.25, stream), 10)
+        out["heat_fp32_von_neumann_" + c.name] = h.cells * 10 / t
+        out["status"] = sq.squeeze_device_status(h.h)
     torch.cuda.empty_cache()
     return out
 
