@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     if force or stale:
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -66,6 +66,7 @@ def _load():
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_box_run_nbhd.argtypes = [i64, p, p, p, i64, u32, u32, u32]
             lib.orc_heat_run.argtypes = [i64, p, p, p, i64, ctypes.c_double, u32]
+            lib.orc_ising_run.argtypes = [i64, p, p, i64, u64, ctypes.c_double, u32]
             _lib = lib
     return _lib
 
@@ -175,6 +176,17 @@ def heat_run(member_box: np.ndarray, u: np.ndarray, steps: int, alpha: float,
     a = np.array(u, dtype=np.float64, order="C", copy=True)
     b = np.empty_like(a)
     _load().orc_heat_run(n, _ptr(m), _ptr(a), _ptr(b), int(steps), float(alpha), nbhd)
+    return a
+
+
+def ising_run(member_box: np.ndarray, box: np.ndarray, sweeps: int, seed: int,
+              temperature: float, nbhd: int = VON_NEUMANN) -> np.ndarray:
+    """Checkerboard Metropolis sweeps of Ising spins (bit 0 = up) on the fractal graph."""
+    n = member_box.shape[0]
+    m = np.ascontiguousarray(member_box, dtype=np.uint8)
+    a = np.array(box, dtype=np.uint8, order="C", copy=True)
+    _load().orc_ising_run(n, _ptr(m), _ptr(a), int(sweeps), seed & (2**64 - 1),
+                          float(temperature), nbhd)
     return a
 
 

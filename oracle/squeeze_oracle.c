@@ -38,6 +38,7 @@
  */
 #include <stdint.h>
 #include <stdlib.h>
+#include <math.h>
 #include <string.h>
 
 #ifdef _OPENMP
@@ -298,6 +299,62 @@ void orc_heat_run(int64_t n, const uint8_t *member, double *a, double *b, int64_
         double *tmp = a; a = b; b = tmp;
     }
     if (steps % 2) memcpy(b, a, (size_t)(n * n) * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ising spins on the fractal graph (Sec. 1 names spin-model simulations):
+ * spin +1 where bit 0 is set, -1 otherwise, coupling J = 1 between fractal
+ * neighbours of the mask (which must join only cells of opposite parity of
+ * x + y, e.g. von Neumann).  One sweep is two half-sweeps, cells with
+ * (x + y) even first, then odd.  Half-sweep number t (t = 0, 1, ... counted
+ * from the first sweep of the call) draws from the SplitMix64 stream seeded
+ * with d_t = splitmix64(seed, t); cell (x, y) takes output number
+ * y * 2^32 + x of that stream.  With h the sum of the neighbour spins and
+ * dE = 2 * s * h, the spin flips iff dE <= 0 or (draw >> 40) < floor(exp(-dE
+ * / T) * 2^24) (Metropolis acceptance in 24-bit fixed point).              */
+static uint64_t orc_splitmix64_local(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void orc_ising_run(int64_t n, const uint8_t *member, uint8_t *box, int64_t sweeps,
+                   uint64_t seed, double temperature, uint32_t nbhd) {
+    /* acceptance thresholds for dE = 2, 4, ..., 16 (index dE / 2) */
+    uint64_t thr[9];
+    thr[0] = 1ull << 24;
+    for (int e = 1; e <= 8; ++e) {
+        double a = temperature > 0.0 ? exp(-(2.0 * e) / temperature) : 0.0;
+        thr[e] = (uint64_t)floor(a * 16777216.0);
+    }
+    for (int64_t t = 0; t < 2 * sweeps; ++t) {
+        const int64_t parity = t & 1;
+        const uint64_t d = orc_splitmix64_local(seed, (uint64_t)t);
+#pragma omp parallel for schedule(static)
+        for (int64_t y = 0; y < n; ++y)
+            for (int64_t x = (y + parity) & 1; x < n; x += 2) {
+                int64_t p = y * n + x;
+                if (!member[p]) continue;
+                int h = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!orc_in_nbhd(nbhd, dx, dy)) continue;
+                        int64_t qx = x + dx, qy = y + dy;
+                        if (qx < 0 || qy < 0 || qx >= n || qy >= n) continue;
+                        int64_t q = qy * n + qx;
+                        if (member[q]) h += (box[q] & 1u) ? 1 : -1;
+                    }
+                const int sp = (box[p] & 1u) ? 1 : -1;
+                const int e2 = sp * h;                  /* dE / 2 */
+                int flip = e2 <= 0;
+                if (!flip) {
+                    uint64_t draw = orc_splitmix64_local(d, ((uint64_t)y << 32) | (uint64_t)x);
+                    flip = (draw >> 40) < thr[e2];
+                }
+                if (flip) box[p] = (uint8_t)((box[p] & 1u) ? 0 : 1);
+            }
+    }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -435,3 +435,59 @@ def test_heat_on_the_triangle_by_brute_force():
                 nxt[y, x] = want[y, x] + 0.25 * flow
         want = nxt
     assert np.allclose(oracle.heat_run(m, u, 3, 0.25), want, rtol=0, atol=1e-12)
+
+
+# Ising spins (Sec. 1: spin-model simulations), checkerboard Metropolis with
+# counter-based draws.
+
+def _energy(m, box):
+    s = np.where(box & 1, 1, -1) * m
+    return -int((s[:, 1:] * s[:, :-1]).sum() + (s[1:, :] * s[:-1, :]).sum())
+
+
+def test_ising_infinite_temperature_flips_every_spin_once_per_sweep():
+    f, r = I.TRIANGLE, 6
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, 2, I.p_q24(0.5))
+    got = oracle.ising_run(m, box, 1, seed=8, temperature=1e300)
+    assert np.array_equal(got, np.where(m == 1, 1 - box, 0))
+    assert np.array_equal(oracle.ising_run(m, box, 2, seed=8, temperature=1e300), box)
+
+
+def test_ising_zero_temperature():
+    f, r = I.FULL2, 5
+    n = f.s ** r
+    m = oracle.member_grid(f, r)
+    up = np.ones((n, n), dtype=np.uint8)
+    assert np.array_equal(oracle.ising_run(m, up, 3, seed=1, temperature=0.0), up)
+    one_down = up.copy()
+    one_down[9, 14] = 0
+    assert np.array_equal(oracle.ising_run(m, one_down, 1, seed=1, temperature=0.0), up)
+    box = (np.random.default_rng(4).random((n, n)) < 0.5).astype(np.uint8)
+    e = [_energy(m, box)]
+    for _ in range(5):
+        box = oracle.ising_run(m, box, 1, seed=len(e), temperature=0.0)
+        e.append(_energy(m, box))
+    assert all(b <= a for a, b in zip(e, e[1:]))
+
+
+def test_ising_by_brute_force_on_the_triangle():
+    f, r, T, seed = I.TRIANGLE, 3, 2.0, 77
+    n = f.s ** r
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, 5, I.p_q24(0.5))
+    thr = [2 ** 24] + [int(np.floor(np.exp(-2.0 * e / T) * 2 ** 24)) for e in range(1, 9)]
+    want = box.copy()
+    for t in range(2 * 3):
+        d = oracle.splitmix64(seed, t)
+        for y in range(n):
+            for x in range(n):
+                if (x + y) % 2 != t % 2 or not m[y, x]:
+                    continue
+                h = sum(1 if want[y + dy, x + dx] & 1 else -1
+                        for dx, dy in ((0, -1), (-1, 0), (1, 0), (0, 1))
+                        if 0 <= x + dx < n and 0 <= y + dy < n and m[y + dy, x + dx])
+                e2 = (1 if want[y, x] & 1 else -1) * h
+                if e2 <= 0 or (oracle.splitmix64(d, (y << 32) | x) >> 40) < thr[e2]:
+                    want[y, x] ^= 1
+    assert np.array_equal(oracle.ising_run(m, box, 3, seed, T), want)
