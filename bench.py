@@ -458,8 +458,8 @@ def bb_compare(sq, torch, dev, stream, steps=20):
 
 def workload_compare(sq, torch, dev, stream):
     """Other neighbourhood workloads: the tiled step over the von Neumann
-    neighbourhood at level 20, and fp32 heat diffusion (per-cell lambda / nu)
-    at level 16."""
+    neighbourhood at level 20; fp32 heat diffusion and Ising Metropolis sweeps
+    (per-cell lambda / nu) at level 16."""
     def timed(fn, steps):
         fn(1)
         torch.cuda.synchronize()
@@ -489,6 +489,11 @@ def workload_compare(sq, torch, dev, stream):
         v = torch.empty_like(u)
         t = timed(lambda n: sq.squeeze_heat_step(h.h, u, v, n, 0.25, stream), 10)
         out["heat_fp32_von_neumann_" + c.name] = h.cells * 10 / t
+        del u, v
+        spins = torch.empty(h.cells, dtype=torch.uint8, device=dev)
+        sq.squeeze_init_bernoulli(h.h, spins, c.seed, I.p_q24(0.5))
+        t = timed(lambda n: sq.squeeze_ising_sweep(h.h, spins, n, n, 2.269, stream), 10)
+        out["ising_sweep_von_neumann_" + c.name] = h.cells * 10 / t
         out["status"] = sq.squeeze_device_status(h.h)
     torch.cuda.empty_cache()
     return out

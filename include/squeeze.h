@@ -199,6 +199,20 @@ int squeeze_set_neighbourhood(squeeze_handle *h, uint32_t mask);
 int squeeze_heat_step(const squeeze_handle *h, float *d_u0, float *d_u1, uint64_t n_steps,
                       float alpha, void *stream);
 
+/* squeeze_ising_sweep -- n_sweeps checkerboard Metropolis sweeps of Ising
+ * spins (coupling 1) on the fractal graph, in place: spin +1 where bit 0 of
+ * d_state (k^r bytes) is set, and the result is written as 0/1.  A sweep
+ * updates the cells with x + y even, then those with x + y odd; half-sweep
+ * number t of the call (t = 0 .. 2 n_sweeps - 1) draws from the SplitMix64
+ * stream seeded with SplitMix64 output t of `seed`, cell (x, y) taking output
+ * y * 2^32 + x.  With dE = 2 s * (sum of neighbour spins) the spin flips iff
+ * dE <= 0 or (draw >> 40) < floor(exp(-dE / temperature) * 2^24).  The
+ * handle's neighbourhood must join only cells of opposite parity (a subset
+ * of von Neumann; else UNSUPPORTED); temperature >= 0 (0: only dE <= 0
+ * flips; else INVALID_ARG).  Give each call its own seed. */
+int squeeze_ising_sweep(const squeeze_handle *h, uint8_t *d_state, uint64_t n_sweeps,
+                        uint64_t seed, double temperature, void *stream);
+
 /* squeeze_lambda_step -- the lambda(omega) approach on the same box (Sec. 2):
  * one thread per compact index omega maps it with lambda and reads its 8
  * neighbours directly in the box, so no nu is needed but the memory is the

@@ -75,6 +75,8 @@ _SIGS = {
     "squeeze_lambda_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                              ctypes.c_void_p], ctypes.c_int),
     "squeeze_set_neighbourhood": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_ising_sweep": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                             ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
     "squeeze_heat_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                            ctypes.c_float, ctypes.c_void_p], ctypes.c_int),
     "squeeze_block_bytes": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)],
@@ -257,6 +259,11 @@ def squeeze_block_to_compact(h, b: int, d_blocks, d_state, stream=None):
 
 def squeeze_set_neighbourhood(h, mask: int):
     _check(_load().squeeze_set_neighbourhood(h, mask), "squeeze_set_neighbourhood")
+
+
+def squeeze_ising_sweep(h, d_state, n_sweeps: int, seed: int, temperature: float, stream=None):
+    _check(_load().squeeze_ising_sweep(h, _ptr(d_state), n_sweeps, seed & (2**64 - 1),
+                                       temperature, _stream(stream)), "squeeze_ising_sweep")
 
 
 def squeeze_heat_step(h, d_u0, d_u1, n_steps: int, alpha: float, stream=None):

@@ -291,6 +291,14 @@ int squeeze_heat_step(const squeeze_handle *h, float *d_u0, float *d_u1, uint64_
   return SQUEEZE_OK;
 }
 
+int squeeze_ising_sweep(const squeeze_handle *h, uint8_t *d_state, uint64_t n_sweeps,
+                        uint64_t seed, double temperature, void *stream) {
+  if (check_handle(h) || !d_state || !(temperature >= 0.0)) return SQUEEZE_ERR_INVALID_ARG;
+  // checkerboard updates need a neighbourhood that joins opposite parities only
+  if (h->f.nbhd & ~sq::kVonNeumann) return SQUEEZE_ERR_UNSUPPORTED;
+  return sq_launch_ising(h, d_state, n_sweeps, seed, temperature, (cudaStream_t)stream);
+}
+
 int squeeze_lambda_step(const squeeze_handle *h, uint8_t *d_grid0, uint8_t *d_grid1,
                         uint64_t n_steps, void *stream) {
   if (check_handle(h) || !d_grid0 || !d_grid1 || d_grid0 == d_grid1) return SQUEEZE_ERR_INVALID_ARG;

@@ -5,6 +5,8 @@
 //     forms the 8 Moore neighbours in a virtual expanded space, maps each back
 //     with nu (holes and points off the box are dead) and applies the rule
 //     into the second buffer (Sec. 3.2 neighbourhood exploration, Sec. 4).
+#include <math.h>
+
 #include "squeeze_internal.cuh"
 
 namespace sq {
@@ -118,6 +120,47 @@ __global__ void heat_step_kernel(FracDev f, float alpha, const float *__restrict
   }
 }
 
+// Ising spins on the fractal graph (Sec. 1 names spin-model simulations): one
+// half-sweep of checkerboard Metropolis updates, in place.  Spin +1 where bit
+// 0 is set; cells with (x + y) % 2 == parity update from their neighbours
+// (the mask joins only cells of the other parity, so nothing they read
+// changes); dE / 2 = s * (sum of neighbour spins); the spin flips iff
+// dE <= 0 or (draw >> 40) < thr[dE / 2], the draw being output number
+// y * 2^32 + x of the SplitMix64 stream seeded with this half-sweep's seed.
+struct IsingThr {
+  uint32_t thr[9];   // floor(exp(-2 e / T) * 2^24) for dE / 2 = e = 1..8; thr[0] unused
+};
+
+__global__ void ising_half_kernel(FracDev f, uint8_t *__restrict__ state, uint32_t parity,
+                                  uint64_t half_seed, IsingThr T) {
+  __shared__ SmemTables t;
+  load_tables(t, f);
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < f.cells;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t wx, wy, x, y;
+    split_omega(f, i, wx, wy);
+    lambda_alu(f, t, wx, wy, x, y);
+    if (((x + y) & 1u) != parity) continue;
+    int h = 0;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
+      uint32_t nx, ny;
+      if (nu_alu(f, t, (int32_t)x + d % 3 - 1, (int32_t)y + d / 3 - 1, nx, ny))
+        h += (state[(uint64_t)ny * f.W + nx] & 1u) ? 1 : -1;
+    }
+    const uint8_t v = state[i];
+    const int e2 = ((v & 1u) ? 1 : -1) * h;
+    bool flip = e2 <= 0;
+    if (!flip) {
+      const uint64_t draw = splitmix64_at(half_seed, ((uint64_t)y << 32) | x);
+      flip = (draw >> 40) < (uint64_t)T.thr[e2];
+    }
+    if (flip) state[i] = (uint8_t)((v & 1u) ^ 1u);
+  }
+}
+
 }  // namespace
 }  // namespace sq
 
@@ -155,5 +198,19 @@ int sq_launch_heat_step(const squeeze_handle *h, const float *in, float *out, fl
                         cudaStream_t st) {
   heat_step_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(h->f, alpha, in, out);
   SQ_CUDA(cudaGetLastError());
+  return SQUEEZE_OK;
+}
+
+int sq_launch_ising(const squeeze_handle *h, uint8_t *state, uint64_t n_sweeps, uint64_t seed,
+                    double temperature, cudaStream_t st) {
+  IsingThr T;
+  T.thr[0] = 1u << 24;
+  for (int e = 1; e <= 8; ++e)
+    T.thr[e] = temperature > 0.0 ? (uint32_t)floor(exp(-(2.0 * e) / temperature) * 16777216.0) : 0u;
+  for (uint64_t t = 0; t < 2 * n_sweeps; ++t) {
+    ising_half_kernel<<<grid_for(h->f.cells, 256), 256, 0, st>>>(
+        h->f, state, (uint32_t)(t & 1u), splitmix64_at(seed, t), T);
+    SQ_CUDA(cudaGetLastError());
+  }
   return SQUEEZE_OK;
 }

@@ -301,6 +301,8 @@ int sq_launch_bb_init(const squeeze_handle *h, uint8_t *grid, uint64_t seed, uin
 int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_heat_step(const squeeze_handle *h, const float *in, float *out, float alpha,
                         cudaStream_t st);
+int sq_launch_ising(const squeeze_handle *h, uint8_t *state, uint64_t n_sweeps, uint64_t seed,
+                    double temperature, cudaStream_t st);
 int sq_launch_lambda_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                           cudaStream_t st);
 int sq_launch_bb_gather(const squeeze_handle *h, const uint8_t *grid, uint8_t *state,

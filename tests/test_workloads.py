@@ -153,3 +153,34 @@ def test_heat_constant_field_and_checks():
         with pytest.raises(sq.SqueezeError) as e:
             sq.squeeze_heat_step(h.h, a, a, 1, 0.2)
         assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("temperature", [0.0, 1.5, 2.269, 5.0, 1e300],
+                         ids=["T0", "T1.5", "Tc", "T5", "Tinf"])
+@pytest.mark.parametrize("f,r", [(I.TRIANGLE, 8), (I.CARPET, 4), (I.VICSEK, 5), (I.FULL2, 6)],
+                         ids=["triangle", "carpet", "vicsek", "full2"])
+def test_ising_sweeps_match_the_oracle(f, r, temperature):
+    """Metropolis decisions are integers (24-bit thresholds from the same double
+    formula on both sides), so every spin must agree."""
+    seed = 1234
+    m = oracle.member_grid(f, r)
+    box = oracle.box_init(f, r, 21, I.p_q24(0.5))
+    want = oracle.box_to_compact(f, r, oracle.ising_run(m, box, 4, seed, temperature))
+    with sq.Handle(f, r) as h:
+        sq.squeeze_set_neighbourhood(h.h, sq.SQUEEZE_VON_NEUMANN)
+        st = to_dev(oracle.box_to_compact(f, r, box))
+        sq.squeeze_ising_sweep(h.h, st, 4, seed, temperature)
+        assert np.array_equal(st.cpu().numpy(), want)
+        assert sq.squeeze_device_status(h.h) == sq.SQUEEZE_OK
+
+
+def test_ising_checks():
+    with sq.Handle(I.TRIANGLE, 6) as h:
+        st = torch.zeros(h.cells, dtype=torch.uint8, device=DEV)
+        with pytest.raises(sq.SqueezeError) as e:   # Moore joins cells of equal parity
+            sq.squeeze_ising_sweep(h.h, st, 1, 1, 2.0)
+        assert e.value.code == sq.SQUEEZE_ERR_UNSUPPORTED
+        sq.squeeze_set_neighbourhood(h.h, sq.SQUEEZE_VON_NEUMANN)
+        with pytest.raises(sq.SqueezeError) as e:
+            sq.squeeze_ising_sweep(h.h, st, 1, 1, -1.0)
+        assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
