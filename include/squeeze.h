@@ -4,22 +4,27 @@
  * The library runs the neighbourhood step of Squeeze (Quezada, Navarro,
  * Hitschfeld, Bustos, arXiv 2201.00613) on an NBB fractal that is stored only
  * in compact form: lambda maps a compact index to expanded space (Sec. 3.3),
- * the 8 Moore neighbours are formed there, nu maps each back to a compact
- * index or rejects it as a hole (Sec. 3.4), and a Life-like rule writes the
- * next state into a second compact buffer (Sec. 4).
+ * the neighbours (the 8 Moore neighbours unless another neighbourhood is set)
+ * are formed there, nu maps each back to a compact index or rejects it as a
+ * hole (Sec. 3.4), and a Life-like rule writes the next state into a second
+ * compact buffer (Sec. 4).  Comparators (bounding box, the lambda(omega)
+ * approach, the block-level layout, tensor-core maps) and other workloads
+ * (heat diffusion, Ising spins) share the same handle.
  *
  * Conventions for every entry point:
  *   - Return value: SQUEEZE_OK (0) or a negative SQUEEZE_ERR_* code.  Nothing
  *     throws, exits or traps; squeeze_status_string() describes a code.
  *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
  *     pointers owned by the caller.  The library keeps no reference to either
- *     after the call returns.
+ *     after the call returns, except a batch, which keeps its items' buffers
+ *     until squeeze_batch_destroy().
  *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
  *     legacy default stream).  Argument errors are reported synchronously;
  *     errors found on the device are latched in a per-handle status word and
  *     reported by squeeze_device_status().
- *   - The handle owns only small per-fractal tables in device memory,
- *     allocated by squeeze_create() and freed by squeeze_destroy().
+ *   - The handle owns small per-fractal tables and, once the tiled step has
+ *     run, its neighbour program and adjacency table (4 bytes per tile and
+ *     direction) in device memory, freed by squeeze_destroy().
  *
  * Compact layout (Sec. 3.1): level mu odd unrolls along x, even along y, so
  * the compact rectangle has W = k^ceil(r/2) columns and H = k^floor(r/2)
