@@ -94,8 +94,8 @@ __global__ void step_alu_kernel(FracDev f, Rule rule, const uint8_t *__restrict_
 
 // Explicit heat diffusion on the fractal graph (Sec. 1 names PDE solvers
 // among the uses of the compact maps): one thread per compact cell finds its
-// place with lambda and its neighbours (the handle's neighbourhood) with nu;
-// holes and points off the box have no edge.  u'(p) = u(p) + alpha * sum over
+// neighbours (the handle's neighbourhood) by the carry walk of nu from its own
+// digits (neighbour_omega); holes and points off the box have no edge.  u'(p) = u(p) + alpha * sum over
 // neighbours q of (u(q) - u(p)), in fp32.
 __global__ void heat_step_kernel(FracDev f, float alpha, const float *__restrict__ in,
                                  float *__restrict__ out) {
@@ -104,16 +104,15 @@ __global__ void heat_step_kernel(FracDev f, float alpha, const float *__restrict
   __syncthreads();
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < f.cells;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t wx, wy, x, y;
+    uint32_t wx, wy;
     split_omega(f, i, wx, wy);
-    lambda_alu(f, t, wx, wy, x, y);
     const float u = in[i];
     float flow = 0.0f;
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
       if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
       uint32_t nx, ny;
-      if (nu_alu(f, t, (int32_t)x + d % 3 - 1, (int32_t)y + d / 3 - 1, nx, ny))
+      if (neighbour_omega(f, t, wx, wy, d % 3 - 1, d / 3 - 1, nx, ny))
         flow += in[(uint64_t)ny * f.W + nx] - u;
     }
     out[i] = u + alpha * flow;
@@ -147,7 +146,7 @@ __global__ void ising_half_kernel(FracDev f, uint8_t *__restrict__ state, uint32
     for (int d = 0; d < 9; ++d) {
       if (d == 4 || !((f.nbhd >> d) & 1u)) continue;
       uint32_t nx, ny;
-      if (nu_alu(f, t, (int32_t)x + d % 3 - 1, (int32_t)y + d / 3 - 1, nx, ny))
+      if (neighbour_omega(f, t, wx, wy, d % 3 - 1, d / 3 - 1, nx, ny))
         h += (state[(uint64_t)ny * f.W + nx] & 1u) ? 1 : -1;
     }
     const uint8_t v = state[i];

@@ -130,6 +130,47 @@ __device__ inline bool nu_alu(const FracDev &f, const SmemTables &t, int32_t x, 
   return true;
 }
 
+// Compact position (nwx, nwy) of the point (dx, dy) away (|dx|, |dy| <= 1)
+// from the fractal cell at compact position (wx, wy), or false for a hole or
+// a point off the box.  nu of the moved point differs from the cell's own
+// digits only up to the level where the carries of dx and dy stop, so the
+// walk (the digit form of nu, Sec. 3.4) runs from level 1 only that far: it
+// reads the cell's replica digit beta_mu, moves its offset tau(beta_mu) by the
+// carries, looks up the new replica through H_nu (a hole ends the walk) and
+// corrects that level's term of the compact index.
+__device__ inline bool neighbour_omega(const FracDev &f, const SmemTables &t, uint32_t wx,
+                                       uint32_t wy, int dx, int dy, uint32_t &nwx,
+                                       uint32_t &nwy) {
+  uint32_t rx = wx, ry = wy;
+  nwx = wx;
+  nwy = wy;
+  uint64_t weight_x = 1, weight_y = 1;
+  int cx = dx, cy = dy;
+  for (uint32_t mu = 1; mu <= f.r; ++mu) {
+    if (cx == 0 && cy == 0) return true;
+    const bool odd = mu & 1u;
+    uint32_t &src = odd ? rx : ry;
+    const uint32_t q = fdiv(f.divk, src), beta = src - q * f.k;
+    src = q;
+    int xd = (int)t.taux[beta] + cx, yd = (int)t.tauy[beta] + cy;
+    cx = xd < 0 ? -1 : (xd >= (int)f.s ? 1 : 0);
+    cy = yd < 0 ? -1 : (yd >= (int)f.s ? 1 : 0);
+    xd -= cx * (int)f.s;
+    yd -= cy * (int)f.s;
+    const uint32_t id = t.hnu[yd * f.s + xd];
+    if (id == kHole) return false;
+    const int64_t delta = (int64_t)id - (int64_t)beta;
+    if (odd) {
+      nwx = (uint32_t)((int64_t)nwx + delta * (int64_t)weight_x);
+      weight_x *= f.k;
+    } else {
+      nwy = (uint32_t)((int64_t)nwy + delta * (int64_t)weight_y);
+      weight_y *= f.k;
+    }
+  }
+  return cx == 0 && cy == 0;   // a carry out of the top level leaves the box
+}
+
 __device__ __host__ inline uint32_t apply_rule(const Rule &rule, bool alive, uint32_t c) {
   return ((alive ? rule.survive : rule.birth) >> c) & 1u;
 }
