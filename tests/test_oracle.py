@@ -491,3 +491,19 @@ def test_ising_by_brute_force_on_the_triangle():
                 if e2 <= 0 or (oracle.splitmix64(d, (y << 32) | x) >> 40) < thr[e2]:
                     want[y, x] ^= 1
     assert np.array_equal(oracle.ising_run(m, box, 3, seed, T), want)
+
+
+def test_heat_two_cell_closed_form():
+    """Two diagonal cells (s = 2, k = 2, r = 1): Moore joins them, von Neumann
+    does not.  Under Moore their difference shrinks by (1 - 2 alpha) per step
+    and their sum stays."""
+    f = I.Fractal("diagonal2", 2, 2, ((0, 0), (1, 1)))
+    m = oracle.member_grid(f, 1)
+    assert m.tolist() == [[1, 0], [0, 1]]
+    u = np.array([[1.0, 0.0], [0.0, 0.25]])
+    alpha, steps = 0.1, 7
+    got = oracle.heat_run(m, u, steps, alpha, oracle.MOORE)
+    diff = 0.75 * (1 - 2 * alpha) ** steps
+    assert got[0, 0] == pytest.approx((1.25 + diff) / 2, abs=1e-14)
+    assert got[1, 1] == pytest.approx((1.25 - diff) / 2, abs=1e-14)
+    assert np.array_equal(oracle.heat_run(m, u, steps, alpha, oracle.VON_NEUMANN), u)

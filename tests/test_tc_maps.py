@@ -153,3 +153,21 @@ def test_tc_argument_checks():
             sq.squeeze_map_tc(h.h, 0, d[1:].view(torch.uint8)[3:], d, 1, TC)
         assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
         sq.squeeze_map_tc(h.h, 1, d, d, 0, TC)   # zero points: nothing enqueued
+
+
+def test_tc_step_other_rules_and_neighbourhood():
+    f, r = I.TRIANGLE, 9
+    c0 = I.bernoulli_bytes(31, f.k ** r, 0.5)
+    with sq.Handle(f, r) as h:
+        for rule, nbhd in ((((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)), sq.SQUEEZE_MOORE),
+                           (((1 << 1), (1 << 1) | (1 << 2)), sq.SQUEEZE_VON_NEUMANN)):
+            sq.squeeze_set_rule(h.h, *rule)
+            sq.squeeze_set_neighbourhood(h.h, nbhd)
+            m = oracle.member_grid(f, r)
+            want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
+                m, oracle.compact_to_box(f, r, c0), 4, rule, nbhd))
+            a = to_dev(c0)
+            b = torch.empty_like(a)
+            sq.squeeze_step(h.h, a, b, 4, TC)
+            assert np.array_equal(a.cpu().numpy(), want), (rule, nbhd)
+        assert sq.squeeze_device_status(h.h) == sq.SQUEEZE_OK
