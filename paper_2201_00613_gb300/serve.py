@@ -10,7 +10,9 @@ that no active request overshoots.  Requests that arrive while a round is on
 the GPU join at the next round boundary, so their work overlaps with that of
 the requests already running.  A finished request's state stays on the
 device; its latency is the time from arrival to the end of its last round.
-All computation runs in the CUDA library; this module only schedules.
+All computation runs in the CUDA library; this module only schedules.  The
+device side sits behind a small backend object (DeviceBackend), so the
+scheduling can be exercised without a GPU.
 """
 from __future__ import annotations
 
@@ -19,74 +21,109 @@ import statistics
 import time
 from collections import deque
 
-import torch
-
-from . import _lib as sq
-from . import inputs as I
-
 
 @dataclasses.dataclass
 class Slot:
     request: object
     handle: object
-    cur: torch.Tensor     # holds the current state
-    other: torch.Tensor
+    cur: object           # buffer that holds the current state
+    other: object
     remaining: int
     admitted_s: float
     done_s: float = -1.0
+
+
+class DeviceBackend:
+    """The device operations the loop needs, through the C ABI and torch."""
+
+    def __init__(self, device="cuda"):
+        import torch
+
+        from . import _lib as sq
+        from . import inputs as I
+        self.torch, self.sq, self.I = torch, sq, I
+        self.device = torch.device(device)
+
+    def free_bytes(self) -> int:
+        return self.torch.cuda.mem_get_info(self.device)[0]
+
+    def handle(self, inst, level):
+        h = self.sq.Handle(inst.fractal, inst.r)
+        if level:
+            try:
+                self.sq.squeeze_set_tiled_level(h.h, min(level, inst.r))
+            except self.sq.SqueezeError:
+                pass   # keep the default level
+        return h
+
+    def cells(self, handle) -> int:
+        return handle.cells
+
+    def start(self, handle, inst):
+        a = self.torch.empty(handle.cells, dtype=self.torch.uint8, device=self.device)
+        b = self.torch.empty_like(a)
+        self.sq.squeeze_init_bernoulli(handle.h, a, inst.seed, self.I.p_q24(inst.p))
+        return a, b
+
+    def batch(self, slots):
+        batch = self.sq.squeeze_batch_create([(s.handle.h, s.cur, s.other) for s in slots])
+        self.sq.squeeze_batch_configure(batch, 288, 0, False)  # round lengths vary: no graphs
+        return batch
+
+    def run(self, batch, k: int):
+        self.sq.squeeze_batch_run(batch, k)
+        self.torch.cuda.current_stream(self.device).synchronize()
+
+    def destroy(self, batch):
+        self.sq.squeeze_batch_destroy(batch)
+
+    def close_handle(self, handle):
+        handle.close()
 
 
 class RequestLoop:
     """Continuous-batching loop on one device."""
 
     def __init__(self, device="cuda", max_slots=64, chunk=25, reserve_bytes=4 << 30,
-                 keep_results=False, levels=None):
-        self.device = torch.device(device)
+                 keep_results=False, levels=None, backend=None):
+        self.backend = backend if backend is not None else DeviceBackend(device)
         self.max_slots = max_slots
         self.chunk = chunk
         self.reserve = reserve_bytes
         self.keep = keep_results
         self.levels = levels or {}
         self.finished = []
-        self.handles = {}   # (fractal name, r) -> Handle, shared by the requests of that shape
+        self.handles = {}   # (fractal name, r) -> handle, shared by the requests of that shape
         self.rounds = 0
         self.batches_built = 0
         self.refused_for_memory = 0
 
     def _fits(self, inst) -> bool:
-        free, _ = torch.cuda.mem_get_info(self.device)
         need = 2 * inst.fractal.cells(inst.r) + (1 << 20)
-        return free - need >= self.reserve
+        return self.backend.free_bytes() - need >= self.reserve
 
     def _handle(self, inst):
         key = (inst.fractal.name, inst.r)
         h = self.handles.get(key)
         if h is None:
-            h = sq.Handle(inst.fractal, inst.r)
-            lvl = self.levels.get(inst.fractal.name)
-            if lvl:
-                try:
-                    sq.squeeze_set_tiled_level(h.h, min(lvl, inst.r))
-                except sq.SqueezeError:
-                    pass
+            h = self.backend.handle(inst, self.levels.get(inst.fractal.name))
             self.handles[key] = h
         return h
 
     def close(self):
         for h in self.handles.values():
-            h.close()
+            self.backend.close_handle(h)
         self.handles = {}
 
     def _admit(self, req, now):
         inst = req.instance
         h = self._handle(inst)
-        a = torch.empty(h.cells, dtype=torch.uint8, device=self.device)
-        b = torch.empty_like(a)
-        sq.squeeze_init_bernoulli(h.h, a, inst.seed, I.p_q24(inst.p))
+        a, b = self.backend.start(h, inst)
         return Slot(req, h, a, b, req.n_steps, now)
 
     def run(self, requests, max_seconds=None):
         """Serve `requests` (sorted by arrival); returns a summary dict."""
+        be = self.backend
         pending = deque(sorted(requests, key=lambda r: r.arrival_s))
         active = []
         batch, members = None, ()
@@ -108,20 +145,18 @@ class RequestLoop:
             ids = tuple(id(s) for s in active)
             if ids != members:
                 if batch:
-                    sq.squeeze_batch_destroy(batch)
-                batch = sq.squeeze_batch_create([(s.handle.h, s.cur, s.other) for s in active])
-                sq.squeeze_batch_configure(batch, 288, 0, False)  # round lengths vary: no graphs
+                    be.destroy(batch)
+                batch = be.batch(active)
                 members = ids
                 self.batches_built += 1
             k = min(self.chunk, min(s.remaining for s in active))
-            sq.squeeze_batch_run(batch, k)
-            torch.cuda.current_stream(self.device).synchronize()
+            be.run(batch, k)
             self.rounds += 1
             end = time.perf_counter() - t0
             still = []
             for s in active:
                 s.remaining -= k
-                cell_updates += k * s.handle.cells
+                cell_updates += k * be.cells(s.handle)
                 if k % 2:
                     s.cur, s.other = s.other, s.cur
                 if s.remaining == 0:
@@ -132,7 +167,7 @@ class RequestLoop:
             if len(still) != len(active):
                 # the batch's parity restarts with the next membership; buffers
                 # are passed as (current, other) again then.
-                sq.squeeze_batch_destroy(batch)
+                be.destroy(batch)
                 batch, members = None, ()
                 for s in active:
                     if s.remaining == 0 and not self.keep:
@@ -140,7 +175,7 @@ class RequestLoop:
                         s.cur = None
             active = still
         if batch:
-            sq.squeeze_batch_destroy(batch)
+            be.destroy(batch)
         makespan = time.perf_counter() - t0
         lat = [s.done_s - s.request.arrival_s for s in self.finished]
         lat.sort()

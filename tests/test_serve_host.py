@@ -1,0 +1,111 @@
+"""The request loop's scheduling, on the CPU, with a stand-in device backend.
+
+The backend counts the CA steps applied to each request's state and the
+memory its buffers hold, so the loop's decisions can be checked exactly:
+every request gets exactly its number of steps, no round overshoots a
+request or exceeds the chunk, the slot limit and the memory reserve hold,
+and requests that arrive later still finish.
+"""
+import weakref
+
+from paper_2201_00613_gb300 import inputs as I
+from paper_2201_00613_gb300.serve import RequestLoop
+
+
+class _State:
+    """A request's state: the steps applied so far (both buffers share it)."""
+
+    def __init__(self, backend, nbytes):
+        self.steps = 0
+        backend.live += nbytes
+        weakref.finalize(self, backend.release, nbytes)
+
+
+class FakeBackend:
+    def __init__(self, total_bytes=1 << 50):
+        self.total = total_bytes
+        self.live = 0
+        self.max_live = 0
+        self.batch_sizes = []
+        self.round_lengths = []
+        self.handles_closed = 0
+
+    def release(self, nbytes):
+        self.live -= nbytes
+
+    def free_bytes(self):
+        return self.total - self.live
+
+    def handle(self, inst, level):
+        return (inst.fractal.name, inst.r, inst.fractal.cells(inst.r))
+
+    def cells(self, handle):
+        return handle[2]
+
+    def start(self, handle, inst):
+        st = _State(self, 2 * handle[2])
+        self.max_live = max(self.max_live, self.live)
+        return st, st
+
+    def batch(self, slots):
+        self.batch_sizes.append(len(slots))
+        return [s.cur for s in slots]
+
+    def run(self, batch, k):
+        self.round_lengths.append(k)
+        for st in batch:
+            st.steps += k
+
+    def destroy(self, batch):
+        batch.clear()
+
+    def close_handle(self, handle):
+        self.handles_closed += 1
+
+
+LEVELS = {"sierpinski_triangle": (4, 9), "sierpinski_carpet": (2, 4), "vicsek": (3, 6)}
+
+
+def test_every_request_gets_exactly_its_steps():
+    reqs = I.request_stream(seed=3, count=60, rate_per_s=1e5, levels=LEVELS, steps=(1, 40))
+    be = FakeBackend()
+    loop = RequestLoop(max_slots=8, chunk=7, keep_results=True, backend=be)
+    out = loop.run(reqs)
+    assert out["requests"] == len(reqs)
+    assert sorted(s.request.rid for s in loop.finished) == list(range(len(reqs)))
+    for s in loop.finished:
+        assert s.cur.steps == s.request.n_steps, s.request.rid
+        assert s.remaining == 0 and s.done_s >= s.admitted_s
+    assert max(be.batch_sizes) <= 8
+    assert max(be.round_lengths) <= 7 and min(be.round_lengths) >= 1
+    assert out["rounds"] == len(be.round_lengths)
+    assert out["cell_updates"] == sum(r.instance.fractal.cells(r.instance.r) * r.n_steps
+                                      for r in reqs)
+    assert out["latency_p50_s"] <= out["latency_p99_s"]
+    loop.close()
+    assert be.handles_closed == len({(r.instance.fractal.name, r.instance.r) for r in reqs})
+
+
+def test_admission_holds_the_memory_reserve():
+    f, r = I.TRIANGLE, 6
+    reqs = [I.Request(i, 0.0, I.Instance(f, r, i), 5 + i % 3) for i in range(12)]
+    # the loop asks for the two buffers plus 1 MiB of headroom: room for three at a time
+    be = FakeBackend(total_bytes=(1 << 20) + 3 * 2 * f.cells(r) + 100)
+    loop = RequestLoop(max_slots=16, chunk=4, reserve_bytes=0, backend=be)
+    out = loop.run(reqs, max_seconds=30)
+    assert out["requests"] == len(reqs)
+    assert be.max_live <= 3 * 2 * f.cells(r)
+    assert max(be.batch_sizes) <= 3
+    assert out["refused_for_memory"] > 0
+
+
+def test_late_arrivals_join_and_finish():
+    f = I.VICSEK
+    reqs = [I.Request(0, 0.0, I.Instance(f, 5, 1), 30),
+            I.Request(1, 0.02, I.Instance(f, 4, 2), 3),
+            I.Request(2, 0.04, I.Instance(f, 3, 3), 1)]
+    be = FakeBackend()
+    loop = RequestLoop(max_slots=4, chunk=2, keep_results=True, backend=be)
+    out = loop.run(reqs, max_seconds=30)
+    assert out["requests"] == 3
+    assert {s.request.rid: s.cur.steps for s in loop.finished} == {0: 30, 1: 3, 2: 1}
