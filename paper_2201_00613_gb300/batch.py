@@ -167,7 +167,7 @@ def autotune(instances, use_cache=True, log=None) -> dict:
                                    "ctas_per_sm": best["ctas_per_sm"]}
     for threads in (192, 256, 288):
         for ctas in (0, 2, 3):
-            if threads == best["threads"] and ctas == best["ctas_per_sm"]:
+            if (threads, ctas) == (288, 0):   # the shape the level search already timed
                 continue
             t = time_config(instances, best["levels"], threads, ctas)
             trials.append(({"levels": best["levels"], "threads": threads, "ctas_per_sm": ctas}, t))
