@@ -7,10 +7,10 @@
 // rho x rho expanded micro-box, holes included (as 0): k^(r - b) * rho^2
 // bytes (Sec. 3.5; r_b = r - log_s rho).  A cell's neighbours inside its own
 // block are direct; those across the block border are found through the 8
-// neighbouring blocks, which lambda and nu at block level (Secs. 3.3, 3.4 on
-// the level-r_b fractal) give once per block.  The step stages each block with
-// a one-cell ring in shared memory and applies the rule there.  rho = 1 is
-// the compact layout.
+// neighbouring blocks, which nu at block level (Sec. 3.4 on the level-r_b
+// fractal, as a carry walk from the block's digits) gives once per block.
+// The step stages each block with a one-cell ring in shared memory and
+// applies the rule there.  rho = 1 is the compact layout.
 #include "squeeze_internal.cuh"
 
 namespace sq {
@@ -30,16 +30,16 @@ struct BlockDev {
   uint8_t mask[kMaxRho * kMaxRho];  // micro-box membership (level-b pattern), row-major
 };
 
-// Block omega's position (in block units) and, for d = 0..8, the block at
-// offset (d % 3 - 1, d / 3 - 1): omega itself for d = 4, ~0 for a hole or
-// off the box.
+// For d = 0..8, the block at offset (d % 3 - 1, d / 3 - 1) from block omega
+// (in block units): omega itself for d = 4, ~0 for a hole or off the box.
+// The carry walk of nu from omega's own digits stops at the first level
+// without a carry.
 __device__ inline uint32_t neighbour_block(const FracDev &fb, const SmemTables &t, uint64_t omega,
                                           int d) {
   if (d == 4) return (uint32_t)omega;
   const uint32_t wy = fdiv(fb.divW, (uint32_t)omega), wx = (uint32_t)omega - wy * fb.W;
-  uint32_t X, Y, nx, ny;
-  lambda_alu(fb, t, wx, wy, X, Y);
-  if (!nu_alu(fb, t, (int32_t)X + d % 3 - 1, (int32_t)Y + d / 3 - 1, nx, ny)) return ~0u;
+  uint32_t nx, ny;
+  if (!neighbour_omega(fb, t, wx, wy, d % 3 - 1, d / 3 - 1, nx, ny)) return ~0u;
   return ny * fb.W + nx;
 }
 
