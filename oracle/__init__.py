@@ -10,6 +10,8 @@ membership of an NBB fractal (Sec. 3), lambda (Sec. 3.3), nu (Sec. 3.4), the
 bounding-box Game-of-Life step over fractal cells (Sec. 4), plus the SplitMix64
 initial-state generator and a light-cone sampler for levels too large for the
 box.  The readings of garbled passages are listed at the top of the C file.
+The three-dimensional extension (``oracle.nbb3d``, ``nbb3d_oracle.c``) lives
+in the same library.
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "squeeze_oracle.c")
+_SOURCES = [_SRC, os.path.join(_HERE, "nbb3d_oracle.c")]
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -34,11 +37,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP) if missing or stale."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+             or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(src) for src in _SOURCES))
     if force or stale:
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SOURCES + ["-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

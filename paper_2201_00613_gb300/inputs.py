@@ -66,6 +66,52 @@ SINGLE = Fractal("single_cell", 2, 1, ((0, 0),))
 
 MIX = (TRIANGLE, CARPET, VICSEK)
 
+
+@dataclasses.dataclass(frozen=True)
+class Fractal3:
+    """A three-dimensional NBB fractal: offsets tau in [0, s)^3 (the paper's
+    extension to three dimensions, abstract and Sec. 7)."""
+
+    name: str
+    s: int
+    k: int
+    offsets: tuple  # k triples (tau_x, tau_y, tau_z), each coordinate in [0, s)
+
+    def offsets_array(self) -> np.ndarray:
+        """Offsets as a (k, 3) uint8 array, row beta = (tau_x, tau_y, tau_z)."""
+        return np.asarray(self.offsets, dtype=np.uint8).reshape(self.k, 3)
+
+    def cells(self, r: int) -> int:
+        return self.k ** r
+
+    def side(self, r: int) -> int:
+        return self.s ** r
+
+
+# Menger sponge F^{20,3}: the 3x3x3 cube minus its centre and the six face
+# centres, raster order (z-major, then y, x fastest).
+MENGER = Fractal3("menger_sponge", 3, 20, tuple(
+    (x, y, z) for z in range(3) for y in range(3) for x in range(3)
+    if (x == 1) + (y == 1) + (z == 1) <= 1))
+
+# Sierpinski tetrahedron on the cube's corner (s = 2): the origin and its
+# three axis neighbours.
+TETRA = Fractal3("sierpinski_tetrahedron", 2, 4, ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)))
+
+# Cantor dust F^{8,3}: the eight corners of the 3x3x3 cube.
+CANTOR_DUST = Fractal3("cantor_dust", 3, 8, tuple(
+    (x, y, z) for z in (0, 2) for y in (0, 2) for x in (0, 2)))
+
+# s = 2 with all eight octants: no holes, the fractal is the whole cube.
+FULL_CUBE = Fractal3("full_cube_s2", 2, 8, tuple(
+    (x, y, z) for z in range(2) for y in range(2) for x in range(2)))
+
+# The Sierpinski triangle in the plane z = 0: a 3-D fractal with a flat slab.
+FLAT_TRIANGLE = Fractal3("flat_triangle", 2, 3, ((0, 0, 0), (1, 0, 0), (0, 1, 0)))
+
+# One cell per level.
+SINGLE3 = Fractal3("single_cell_3d", 2, 1, ((0, 0, 0),))
+
 # Level ranges of the batched mixed workload, per fractal type.
 MIX_LEVELS = {"sierpinski_triangle": (8, 14), "sierpinski_carpet": (4, 8), "vicsek": (5, 9)}
 
