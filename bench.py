@@ -339,12 +339,16 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- same-GPU bounding box at level 16 ----------------------------------
-    compare = maps = blocks = workloads = None
+    compare = maps = blocks = workloads = nbb3d = None
     if not args.no_compare:
         compare = bb_compare(sq, torch, dev, stream)
         maps = map_compare(sq, torch, dev, stream)
         blocks = block_compare(sq, torch, dev, stream)
         workloads = workload_compare(sq, torch, dev, stream)
+        try:
+            nbb3d = nbb3d_compare(sq, torch, dev, stream)
+        except Exception as e:   # reported in the line, never fatal to it
+            nbb3d = {"error": str(e)[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -373,6 +377,7 @@ def main():
             "map_compare": maps,
             "block_compare": blocks,
             "workload_compare": workloads,
+            "nbb3d_compare": nbb3d,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -495,6 +500,36 @@ def workload_compare(sq, torch, dev, stream):
         t = timed(lambda n: sq.squeeze_ising_sweep(h.h, spins, n, n, 2.269, stream), 10)
         out["ising_sweep_von_neumann_" + c.name] = h.cells * 10 / t
         out["status"] = sq.squeeze_device_status(h.h)
+    torch.cuda.empty_cache()
+    return out
+
+
+def nbb3d_compare(sq, torch, dev, stream, steps=4):
+    """Three-dimensional fractals: the per-cell step (26 neighbours, B5/S45) on
+    the Menger sponge at level 7 (1.28e9 cells) and the Sierpinski tetrahedron
+    at level 15 (1.07e9 cells); hbm_frac counts two bytes per cell-update
+    against the copy bandwidth."""
+    out = {"unit": "cell-updates/s", "steps": steps, "rule": "B5/S45, 26 neighbours"}
+    for f, r in ((I.MENGER, 7), (I.TETRA, 15)):
+        with sq.Handle3(f, r) as h:
+            a = torch.empty(h.cells, dtype=torch.uint8, device=dev)
+            b = torch.empty_like(a)
+            sq.squeeze_3d_init_bernoulli(h.h, a, 3, I.p_q24(0.3), stream)
+            sq.squeeze_3d_step(h.h, a, b, 2, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sq.squeeze_3d_step(h.h, a, b, steps, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            rate = h.cells * steps / t
+            out["%s_r%d" % (f.name, r)] = {"cells": h.cells, "ms_per_step": 1e3 * t / steps,
+                                           "cell_updates_per_s": rate,
+                                           "hbm_frac": 2 * rate / 1e9 / peaks()[0],
+                                           "status": sq.squeeze_3d_device_status(h.h)}
+            del a, b
     torch.cuda.empty_cache()
     return out
 

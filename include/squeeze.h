@@ -298,7 +298,7 @@ int squeeze_block_init(const squeeze_handle *h, uint32_t b, uint8_t *d_blocks, u
 
 /* squeeze_block_step -- n_steps rule steps in block layout (one thread per
  * micro-box cell; neighbours across a block border through the 8 adjacent
- * blocks, found with lambda and nu at block level).  Result in d_blocks0
+ * blocks, found by the carry walk of nu at block level).  Result in d_blocks0
  * when n_steps is even, d_blocks1 when odd; the buffers must differ. */
 int squeeze_block_step(const squeeze_handle *h, uint32_t b, uint8_t *d_blocks0,
                        uint8_t *d_blocks1, uint64_t n_steps, void *stream);
@@ -335,6 +335,85 @@ int squeeze_block_to_compact(const squeeze_handle *h, uint32_t b, const uint8_t 
 int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
                          uint32_t birth, uint32_t survive, const uint8_t *d_in, uint8_t *d_out,
                          int *h_status, void *stream);
+
+/* ---- three-dimensional NBB fractals ---------------------------------------
+ * The abstract and Sec. 7 name the extension of the compact maps to three
+ * dimensions without defining it; this library carries Secs. 3.1-3.4 and 4
+ * over to a third axis:
+ *   - replicas at distinct offsets tau(beta) = (tau_x, tau_y, tau_z) in
+ *     [0, s)^3; a point of the n^3 box (n = s^r) is a cell iff every base-s
+ *     digit triple of its coordinates is an offset;
+ *   - compact layout: level mu puts its replica id into base-k digit
+ *     floor((mu-1)/3) of w_x, w_y or w_z for (mu-1) mod 3 = 0, 1, 2, so
+ *     W_x = k^ceil(r/3), W_y = k^floor((r+1)/3), W_z = k^floor(r/3), stored
+ *     as omega = (w_z * W_y + w_y) * W_x + w_x; one byte per cell, alive iff
+ *     bit 0 is set, k^r bytes per state;
+ *   - step: every cell counts its alive fractal neighbours among the offsets
+ *     (dx, dy, dz) selected by a 27-bit mask (bit (dz+1)*9 + (dy+1)*3 +
+ *     (dx+1); all 26 by default), holes and points off the box dead, and a
+ *     27-bit birth/survive rule gives its next state (default B5/S45, Bays'
+ *     three-dimensional Life).
+ * Conventions (return codes, d_ pointers, streams, device status) are those
+ * of the two-dimensional entry points. */
+typedef struct squeeze_3d_handle squeeze_3d_handle;
+
+/* squeeze_3d_create -- describe a level-r 3-D NBB fractal.
+ *   s        2 <= s <= 8.
+ *   k        1 <= k <= min(s^3, 255).
+ *   offsets  host array of 3*k bytes: replica beta at (offsets[3*beta],
+ *            offsets[3*beta+1], offsets[3*beta+2]), each < s, all distinct.
+ *   r        level; requires s^r <= 2^30 and k^r <= 2^40.
+ * Errors: INVALID_ARG for any violated bound (checked before any device
+ * work); OOM / CUDA when the status word cannot be allocated. */
+int squeeze_3d_create(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
+                      squeeze_3d_handle **out);
+
+/* squeeze_3d_destroy -- synchronise the device and free the handle.  NULL is
+ * accepted. */
+int squeeze_3d_destroy(squeeze_3d_handle *h);
+
+/* squeeze_3d_info -- k^r cells, the compact extents W_x, W_y, W_z and the
+ * side n = s^r.  Any output pointer may be NULL. */
+int squeeze_3d_info(const squeeze_3d_handle *h, uint64_t *n_cells, uint64_t *wx, uint64_t *wy,
+                    uint64_t *wz, uint64_t *side);
+
+/* squeeze_3d_set_rule -- 27-bit birth/survive masks over the neighbour count
+ * 0..26.  Affects steps enqueued after the call. */
+int squeeze_3d_set_rule(squeeze_3d_handle *h, uint32_t birth, uint32_t survive);
+
+/* squeeze_3d_set_neighbourhood -- 27-bit offset mask (bit 13, the cell
+ * itself, must be clear). */
+int squeeze_3d_set_neighbourhood(squeeze_3d_handle *h, uint32_t mask);
+
+/* squeeze_3d_lambda -- compact -> expanded.  d_omega: count uint64 (8-byte
+ * aligned); d_xyz receives 3*count int32 (x, y, z), (-1, -1, -1) for an index
+ * >= k^r. */
+int squeeze_3d_lambda(const squeeze_3d_handle *h, const uint64_t *d_omega, int32_t *d_xyz,
+                      uint64_t count, void *stream);
+
+/* squeeze_3d_nu -- expanded -> compact with hole rejection.  d_xyz: 3*count
+ * int32 points, any values; d_omega receives the compact index, or
+ * UINT64_MAX for a hole or a point off the box. */
+int squeeze_3d_nu(const squeeze_3d_handle *h, const int32_t *d_xyz, uint64_t *d_omega,
+                  uint64_t count, void *stream);
+
+/* squeeze_3d_init_bernoulli -- d_state[omega] = 1 iff the top 24 bits of
+ * SplitMix64 output number omega of the stream seeded with `seed` are below
+ * p_q24 (<= 2^24), else 0. */
+int squeeze_3d_init_bernoulli(const squeeze_3d_handle *h, uint8_t *d_state, uint64_t seed,
+                              uint32_t p_q24, void *stream);
+
+/* squeeze_3d_step -- n_steps steps, one thread per compact cell: lambda's
+ * digits, each neighbour by the carry walk of nu from the cell's own digits,
+ * the rule into the other buffer.  Result in d_buf0 when n_steps is even,
+ * d_buf1 when odd; the buffers (k^r bytes each) must differ.  A neighbour
+ * index past the state (impossible for a valid handle) is skipped and
+ * latches DEVICE_BOUNDS. */
+int squeeze_3d_step(squeeze_3d_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
+                    void *stream);
+
+/* squeeze_3d_device_status -- as squeeze_device_status, for a 3-D handle. */
+int squeeze_3d_device_status(squeeze_3d_handle *h, int *status);
 
 /* ---- diagnostics ---------------------------------------------------------- */
 

@@ -5,4 +5,4 @@ The compute path is the CUDA library ``libsqueeze.so`` (C ABI in
 with the same entry-point names.  ``inputs`` holds the seeded synthetic inputs.
 """
 from ._lib import *  # noqa: F401,F403
-from ._lib import Handle, SqueezeError, exported_names, lib, library_path  # noqa: F401
+from ._lib import Handle, Handle3, SqueezeError, exported_names, lib, library_path  # noqa: F401

@@ -29,6 +29,8 @@ SQUEEZE_MAP_TC_I8 = 4
 
 SQUEEZE_MOORE = 0x1EF
 SQUEEZE_VON_NEUMANN = 0xAA
+SQUEEZE_3D_MOORE = ((1 << 27) - 1) & ~(1 << 13)
+SQUEEZE_3D_VON_NEUMANN = (1 << 4) | (1 << 10) | (1 << 12) | (1 << 14) | (1 << 16) | (1 << 22)
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +99,21 @@ _SIGS = {
     "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_create": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "squeeze_3d_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_uint64)] * 5, ctypes.c_int),
+    "squeeze_3d_set_rule": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_3d_set_neighbourhood": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_3d_lambda": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                           ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_nu": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                       ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_init_bernoulli": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                   ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                         ctypes.c_void_p], ctypes.c_int),
+    "squeeze_3d_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "squeeze_last_cuda_error": ([], ctypes.c_char_p),
@@ -329,6 +346,62 @@ def squeeze_step_noalloc(s: int, k: int, offsets, r: int, birth: int, survive: i
     return int(st.value) if wait_status else None
 
 
+def squeeze_3d_create(s: int, k: int, offsets, r: int):
+    """Create a handle for the level-r 3-D NBB fractal; offsets = k (x, y, z) triples."""
+    flat = bytes(int(v) for t in offsets for v in t)
+    if len(flat) != 3 * k:
+        raise ValueError("need k offset triples")
+    buf = ctypes.create_string_buffer(flat, len(flat))
+    out = ctypes.c_void_p()
+    _check(_load().squeeze_3d_create(s, k, buf, r, ctypes.byref(out)), "squeeze_3d_create")
+    return out.value
+
+
+def squeeze_3d_destroy(h):
+    _check(_load().squeeze_3d_destroy(h), "squeeze_3d_destroy")
+
+
+def squeeze_3d_info(h):
+    """(n_cells, W_x, W_y, W_z, side n)."""
+    v = [ctypes.c_uint64() for _ in range(5)]
+    _check(_load().squeeze_3d_info(h, *[ctypes.byref(x) for x in v]), "squeeze_3d_info")
+    return tuple(int(x.value) for x in v)
+
+
+def squeeze_3d_set_rule(h, birth: int, survive: int):
+    _check(_load().squeeze_3d_set_rule(h, birth, survive), "squeeze_3d_set_rule")
+
+
+def squeeze_3d_set_neighbourhood(h, mask: int):
+    _check(_load().squeeze_3d_set_neighbourhood(h, mask), "squeeze_3d_set_neighbourhood")
+
+
+def squeeze_3d_lambda(h, d_omega, d_xyz, count: int, stream=None):
+    _check(_load().squeeze_3d_lambda(h, _ptr(d_omega), _ptr(d_xyz), count, _stream(stream)),
+           "squeeze_3d_lambda")
+
+
+def squeeze_3d_nu(h, d_xyz, d_omega, count: int, stream=None):
+    _check(_load().squeeze_3d_nu(h, _ptr(d_xyz), _ptr(d_omega), count, _stream(stream)),
+           "squeeze_3d_nu")
+
+
+def squeeze_3d_init_bernoulli(h, d_state, seed: int, p_q24: int, stream=None):
+    _check(_load().squeeze_3d_init_bernoulli(h, _ptr(d_state), seed & (2**64 - 1), p_q24,
+                                             _stream(stream)), "squeeze_3d_init_bernoulli")
+
+
+def squeeze_3d_step(h, d_buf0, d_buf1, n_steps: int, stream=None):
+    _check(_load().squeeze_3d_step(h, _ptr(d_buf0), _ptr(d_buf1), n_steps, _stream(stream)),
+           "squeeze_3d_step")
+
+
+def squeeze_3d_device_status(h) -> int:
+    v = ctypes.c_int()
+    _check(_load().squeeze_3d_device_status(h, ctypes.byref(v)), "squeeze_3d_device_status")
+    return int(v.value)
+
+
 def squeeze_device_status(h) -> int:
     v = ctypes.c_int()
     _check(_load().squeeze_device_status(h, ctypes.byref(v)), "squeeze_device_status")
@@ -355,6 +428,33 @@ class Handle:
     def close(self):
         if self.h:
             squeeze_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Handle3:
+    """Owns one 3-D squeeze handle; closes it on ``close()`` or at context exit."""
+
+    def __init__(self, fractal, r: int):
+        self.fractal = fractal
+        self.r = r
+        self.h = squeeze_3d_create(fractal.s, fractal.k, fractal.offsets, r)
+        self.cells, self.wx, self.wy, self.wz, self.side = squeeze_3d_info(self.h)
+
+    def close(self):
+        if self.h:
+            squeeze_3d_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -56,3 +56,27 @@ def test_null_handle_is_rejected():
     with pytest.raises(sq.SqueezeError) as e:
         sq.squeeze_info(None)
     assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("s,k,offsets,r", [
+    (1, 1, [(0, 0, 0)], 3),                           # s < 2
+    (9, 1, [(0, 0, 0)], 3),                           # s > 8
+    (2, 9, [(0, 0, 0)] * 9, 3),                       # k > s^3
+    (2, 2, [(0, 0, 0), (0, 0, 2)], 3),                # offset outside [0, s)
+    (2, 2, [(1, 0, 1), (1, 0, 1)], 3),                # repeated offset
+    (2, 1, [(0, 0, 0)], 31),                          # s^r > 2^30
+    (3, 20, [(x, y, z) for z in range(3) for y in range(3) for x in range(3)
+             if (x == 1) + (y == 1) + (z == 1) <= 1], 10),   # k^r > 2^40
+])
+def test_3d_create_rejects_bad_descriptors_before_touching_the_device(s, k, offsets, r):
+    with pytest.raises(sq.SqueezeError) as e:
+        sq.squeeze_3d_create(s, k, offsets, r)
+    assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+
+
+def test_3d_null_handle_is_rejected():
+    for call in (lambda: sq.squeeze_3d_info(None), lambda: sq.squeeze_3d_set_rule(None, 0, 0),
+                 lambda: sq.squeeze_3d_set_neighbourhood(None, 1)):
+        with pytest.raises(sq.SqueezeError) as e:
+            call()
+        assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
