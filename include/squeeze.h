@@ -50,6 +50,7 @@ extern "C" {
 #define SQUEEZE_ERR_CUDA (-4)          /* a CUDA runtime call failed              */
 #define SQUEEZE_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait gave up     */
 #define SQUEEZE_ERR_DEVICE_BOUNDS (-6) /* a device-side bounds check fired        */
+#define SQUEEZE_ERR_IO (-7)            /* a file could not be read or written, or is damaged */
 
 /* ---- step kernels --------------------------------------------------------- */
 #define SQUEEZE_STEP_AUTO 0    /* tiled kernel when the level allows, else per-cell ALU */
@@ -335,6 +336,35 @@ int squeeze_block_to_compact(const squeeze_handle *h, uint32_t b, const uint8_t 
 int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
                          uint32_t birth, uint32_t survive, const uint8_t *d_in, uint8_t *d_out,
                          int *h_status, void *stream);
+
+/* ---- checkpoint / resume ---------------------------------------------------
+ * A run is resumed from (fractal, level, step count, compact state).  These
+ * two calls are host code only: the caller copies the state between device
+ * and host (the state is caller-owned, like every buffer).  The paper has no
+ * counterpart; this is an interface of this library only.  File layout,
+ * little-endian: a 64-byte header (magic "SQZSTATE", version 1, header size,
+ * s, k, r, dimensions = 2, step, state bytes k^r, FNV-1a 64-bit hash of the
+ * state, reserved 0), the 2k offset bytes zero-padded to a multiple of 8,
+ * then the k^r state bytes in compact order.  The rule and neighbourhood are
+ * not stored: they belong to the handle that resumes the run. */
+
+/* squeeze_checkpoint_write -- write h_state (k^r bytes) and `step` to `path`.
+ * The fractal is validated as in squeeze_create.  The file is written under
+ * a temporary name beside `path` and renamed into place, so readers never see
+ * a partial file.  Errors: INVALID_ARG; IO (create, write or rename failed;
+ * squeeze_last_cuda_error() holds the reason). */
+int squeeze_checkpoint_write(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
+                             uint64_t step, const uint8_t *h_state, const char *path);
+
+/* squeeze_checkpoint_read -- read a checkpoint of the given fractal and level
+ * into h_state (k^r bytes) and *step.  Errors: INVALID_ARG for a bad
+ * descriptor or a valid checkpoint of another fractal, offset table or
+ * level; IO for a missing or unreadable file, a file that is not a
+ * checkpoint, a truncated or over-long file, or a state whose hash does not
+ * match.  After an error h_state's contents are unspecified and *step is not
+ * written. */
+int squeeze_checkpoint_read(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
+                            uint64_t *step, uint8_t *h_state, const char *path);
 
 /* ---- three-dimensional NBB fractals ---------------------------------------
  * The abstract and Sec. 7 name the extension of the compact maps to three

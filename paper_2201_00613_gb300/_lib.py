@@ -20,6 +20,7 @@ SQUEEZE_ERR_OOM = -3
 SQUEEZE_ERR_CUDA = -4
 SQUEEZE_ERR_DEVICE_TIMEOUT = -5
 SQUEEZE_ERR_DEVICE_BOUNDS = -6
+SQUEEZE_ERR_IO = -7
 
 SQUEEZE_STEP_AUTO = 0
 SQUEEZE_STEP_TILED = 1
@@ -99,6 +100,12 @@ _SIGS = {
     "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
+    "squeeze_checkpoint_write": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p,
+                                  ctypes.c_char_p], ctypes.c_int),
+    "squeeze_checkpoint_read": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                 ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "squeeze_3d_create": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "squeeze_3d_destroy": ([ctypes.c_void_p], ctypes.c_int),
@@ -344,6 +351,29 @@ def squeeze_step_noalloc(s: int, k: int, offsets, r: int, birth: int, survive: i
                                         ctypes.byref(st) if wait_status else None,
                                         _stream(stream)), "squeeze_step_noalloc")
     return int(st.value) if wait_status else None
+
+
+def _offsets_buffer(offsets, k: int):
+    flat = bytes(int(v) for pair in offsets for v in pair)
+    if len(flat) != 2 * k:
+        raise ValueError("need k offset pairs")
+    return ctypes.create_string_buffer(flat, len(flat))
+
+
+def squeeze_checkpoint_write(s: int, k: int, offsets, r: int, step: int, h_state, path):
+    """Write a host state (k^r bytes, e.g. a numpy array) and its step count to `path`."""
+    _check(_load().squeeze_checkpoint_write(s, k, _offsets_buffer(offsets, k), r, step,
+                                            _ptr(h_state), os.fsencode(path)),
+           "squeeze_checkpoint_write")
+
+
+def squeeze_checkpoint_read(s: int, k: int, offsets, r: int, h_state, path) -> int:
+    """Read a checkpoint into a host buffer of k^r bytes; returns its step count."""
+    step = ctypes.c_uint64(0)
+    _check(_load().squeeze_checkpoint_read(s, k, _offsets_buffer(offsets, k), r,
+                                           ctypes.byref(step), _ptr(h_state), os.fsencode(path)),
+           "squeeze_checkpoint_read")
+    return int(step.value)
 
 
 def squeeze_3d_create(s: int, k: int, offsets, r: int):

@@ -84,6 +84,7 @@ const char *squeeze_status_string(int status) {
     case SQUEEZE_ERR_CUDA: return "CUDA runtime error";
     case SQUEEZE_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case SQUEEZE_ERR_DEVICE_BOUNDS: return "device-side bounds check failed";
+    case SQUEEZE_ERR_IO: return "file could not be read or written, or is damaged";
     default: return "unknown status";
   }
 }
