@@ -10,6 +10,9 @@ that no active request overshoots.  Requests that arrive while a round is on
 the GPU join at the next round boundary, so their work overlaps with that of
 the requests already running.  A finished request's state stays on the
 device; its latency is the time from arrival to the end of its last round.
+cancel() withdraws a request from any thread: at the next round boundary a
+queued request is dropped before admission and an active one gives up its
+slot and its buffers; a request that has already finished keeps its result.
 All computation runs in the CUDA library; this module only schedules.  The
 device side sits behind a small backend object (DeviceBackend), so the
 scheduling can be exercised without a GPU.
@@ -18,6 +21,7 @@ from __future__ import annotations
 
 import dataclasses
 import statistics
+import threading
 import time
 from collections import deque
 
@@ -97,6 +101,19 @@ class RequestLoop:
         self.rounds = 0
         self.batches_built = 0
         self.refused_for_memory = 0
+        self.cancelled = []          # (request id, True if it was active when withdrawn)
+        self._cancel = set()
+        self._cancel_lock = threading.Lock()
+
+    def cancel(self, rid) -> None:
+        """Withdraw request `rid` at the next round boundary (thread-safe)."""
+        with self._cancel_lock:
+            self._cancel.add(rid)
+
+    def _take_cancellations(self):
+        with self._cancel_lock:
+            ids, self._cancel = self._cancel, set()
+        return ids
 
     def _fits(self, inst) -> bool:
         need = 2 * inst.fractal.cells(inst.r) + (1 << 20)
@@ -133,6 +150,26 @@ class RequestLoop:
             now = time.perf_counter() - t0
             if max_seconds and now > max_seconds:
                 break
+            withdrawn = self._take_cancellations()
+            if withdrawn:
+                kept = deque()
+                for req in pending:
+                    if req.rid in withdrawn:
+                        self.cancelled.append((req.rid, False))
+                    else:
+                        kept.append(req)
+                pending = kept
+                dropped = [s for s in active if s.request.rid in withdrawn]
+                if dropped:
+                    if batch:           # the batch refers to the dropped buffers: end it first
+                        be.destroy(batch)
+                    batch, members = None, ()
+                    for s in dropped:
+                        self.cancelled.append((s.request.rid, True))
+                        s.cur = s.other = None
+                    active = [s for s in active if s.request.rid not in withdrawn]
+                if not pending and not active:
+                    break
             while pending and pending[0].arrival_s <= now and len(active) < self.max_slots:
                 if not self._fits(pending[0].instance):
                     self.refused_for_memory += 1
@@ -191,4 +228,5 @@ class RequestLoop:
             "rounds": self.rounds,
             "batches_built": self.batches_built,
             "refused_for_memory": self.refused_for_memory,
+            "cancelled": len(self.cancelled),
         }

@@ -109,3 +109,67 @@ def test_late_arrivals_join_and_finish():
     out = loop.run(reqs, max_seconds=30)
     assert out["requests"] == 3
     assert {s.request.rid: s.cur.steps for s in loop.finished} == {0: 30, 1: 3, 2: 1}
+
+
+class _CancellingBackend(FakeBackend):
+    """Withdraws the given requests when the loop starts a given round."""
+
+    def __init__(self, loop_ref, at_round, rids):
+        super().__init__()
+        self.loop_ref, self.at_round, self.rids = loop_ref, at_round, rids
+        self.runs = 0
+
+    def run(self, batch, k):
+        self.runs += 1
+        if self.runs == self.at_round:
+            for rid in self.rids:
+                self.loop_ref[0].cancel(rid)
+        super().run(batch, k)
+
+
+def test_cancelled_requests_leave_and_the_rest_finish():
+    reqs = I.request_stream(seed=9, count=40, rate_per_s=1e5, levels=LEVELS, steps=(20, 60))
+    holder = []
+    # cancel 3 requests after the second round: some are active by then, others still queued
+    targets = [0, 1, 39]
+    be = _CancellingBackend(holder, 2, targets)
+    loop = RequestLoop(max_slots=4, chunk=5, keep_results=True, backend=be)
+    holder.append(loop)
+    out = loop.run(reqs)
+    assert out["cancelled"] == 3 and out["requests"] == len(reqs) - 3
+    gone = dict(loop.cancelled)
+    assert sorted(gone) == sorted(targets)
+    assert gone[0] and gone[1] and not gone[39]     # 0 and 1 were running, 39 still queued
+    finished = {s.request.rid for s in loop.finished}
+    assert finished == set(range(len(reqs))) - set(targets)
+    for s in loop.finished:
+        assert s.cur.steps == s.request.n_steps
+    # results are kept (keep_results): exactly the finished requests still hold buffers
+    import gc
+    gc.collect()
+    assert be.live == sum(2 * s.request.instance.fractal.cells(s.request.instance.r)
+                          for s in loop.finished)
+
+
+def test_cancelling_everything_ends_the_loop_and_frees_the_buffers():
+    reqs = I.request_stream(seed=10, count=12, rate_per_s=1e5, levels=LEVELS, steps=(30, 50))
+    holder = []
+    be = _CancellingBackend(holder, 1, list(range(12)))
+    loop = RequestLoop(max_slots=3, chunk=4, backend=be)
+    holder.append(loop)
+    out = loop.run(reqs)
+    assert out["requests"] == 0 and out["cancelled"] == 12
+    assert [active for _, active in loop.cancelled].count(True) == 3
+    assert be.live == 0                     # no request holds a buffer any more
+
+
+def test_cancelling_a_finished_or_unknown_request_changes_nothing():
+    reqs = I.request_stream(seed=11, count=10, rate_per_s=1e5, levels=LEVELS, steps=(1, 3))
+    be = FakeBackend()
+    loop = RequestLoop(max_slots=10, chunk=8, keep_results=True, backend=be)
+    out = loop.run(reqs)
+    loop.cancel(0)
+    loop.cancel(12345)
+    out2 = loop.run([])
+    assert out["requests"] == 10 and out2["cancelled"] == 0
+    assert all(s.cur.steps == s.request.n_steps for s in loop.finished)
