@@ -9,7 +9,9 @@
  * hole (Sec. 3.4), and a Life-like rule writes the next state into a second
  * compact buffer (Sec. 4).  Comparators (bounding box, the lambda(omega)
  * approach, the block-level layout, tensor-core maps) and other workloads
- * (heat diffusion, Ising spins) share the same handle.
+ * (heat diffusion, Ising spins) share the same handle.  Three-dimensional
+ * fractals have a handle of their own (squeeze_3d_*); checkpoint files of a
+ * compact state are written and read by host-only calls.
  *
  * Conventions for every entry point:
  *   - Return value: SQUEEZE_OK (0) or a negative SQUEEZE_ERR_* code.  Nothing

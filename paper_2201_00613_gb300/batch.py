@@ -182,6 +182,8 @@ def autotune(instances, use_cache=True, log=None) -> dict:
     if use_cache:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
         cache[key] = result
-        with open(_CACHE, "w") as f:
+        tmp = "%s.tmp%d" % (_CACHE, os.getpid())
+        with open(tmp, "w") as f:        # replaced whole: readers never see a partial file
             json.dump(cache, f, indent=1)
+        os.replace(tmp, _CACHE)
     return result
