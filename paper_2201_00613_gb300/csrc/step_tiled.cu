@@ -132,29 +132,71 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_wait_at(uint32_t addr, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(m)), "r"(parity)
+      : "r"(addr), "r"(parity)
       : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+  return mbar_try_wait_at(smem_u32(m), parity);
 }
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for an mbarrier phase, giving up after ~2 s with DEVICE_TIMEOUT.
-__device__ __forceinline__ void mbar_wait(uint64_t *m, uint32_t parity, int *status) {
-  if (mbar_try_wait(m, parity)) return;
+// Abort record of the CTA: set by the first wait that gives up, with the
+// shared-memory address of the barrier and the phase it gave up on.
+struct AbortRecord {
+  uint32_t bar;
+  uint32_t parity;
+  uint32_t set;
+};
+__shared__ AbortRecord g_abort;
+
+// Wait for an mbarrier phase, giving up after ~2 s with DEVICE_TIMEOUT.  A
+// wait that gives up records it in g_abort; every later wait of the CTA that
+// does not complete at once returns as soon as it sees the record, and no
+// more loads are issued, so a copy that never lands costs the launch about
+// 2 s instead of 2 s per group.  Control flow is unchanged (every thread still
+// reaches every barrier); the results of an aborted launch are not valid,
+// which the status word says.
+__device__ __noinline__ void mbar_wait_slow(uint32_t addr, uint32_t parity, int *status) {
+  volatile AbortRecord *ab = &g_abort;
   uint64_t t0 = global_ns();
-  while (!mbar_try_wait(m, parity)) {
+  while (!mbar_try_wait_at(addr, parity)) {
+    if (ab->set) return;
     if (global_ns() - t0 > 2000000000ull) {
       flag(status, SQUEEZE_ERR_DEVICE_TIMEOUT);
+      ab->bar = addr;
+      ab->parity = parity;
+      ab->set = 1u;
       return;
+    }
+  }
+}
+__device__ __forceinline__ void mbar_wait(uint64_t *m, uint32_t parity, int *status) {
+  const uint32_t addr = smem_u32(m);
+  if (!mbar_try_wait_at(addr, parity)) mbar_wait_slow(addr, parity, status);
+}
+
+// True once a wait of this CTA has given up (read after a CTA barrier, so
+// every thread sees the same value).
+__device__ __forceinline__ bool cta_aborted() {
+  return reinterpret_cast<volatile AbortRecord *>(&g_abort)->set != 0u;
+}
+
+// At the end of an aborted launch the copy that timed out may still land in
+// shared memory: give it one more bounded wait before the CTA exits.
+__device__ __forceinline__ void settle_abort() {
+  if (threadIdx.x == 0 && cta_aborted()) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait_at(g_abort.bar, g_abort.parity) && global_ns() - t0 < 2000000000ull) {
     }
   }
 }
@@ -557,7 +599,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   const uint64_t total = p.total, W = p.W;
   const uint32_t valid = p.valid;
 
-  if (warp == 0 && g_first < g_end)
+  if (warp == 0 && g_first < g_end && !cta_aborted())
     issue_group_loads(p, group_at(p, TW, g_first), in, stage_base + (it & 1u) * stage_bytes,
                       &mbar[it & 1u], lane);
   // Adjacent tile of this lane's tile in direction j = warp, for the group at hand.
@@ -684,7 +726,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     // The only CTA barrier of the group: all words (rows and halo) are in
     // place, and every warp has finished the previous group.
     __syncthreads();
-    if (warp == 0 && g + g_stride < g_end)
+    if (warp == 0 && g + g_stride < g_end && !cta_aborted())
       issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
 
@@ -816,6 +858,7 @@ __device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLay
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    g_abort.set = 0u;
   }
 }
 
@@ -833,6 +876,7 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
   run_groups<kLife, kTW>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
   bulk_wait_all();
+  settle_abort();
 }
 
 // One step of many instances (each with its own fractal, level and
@@ -866,6 +910,7 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
     }
   }
   bulk_wait_all();
+  settle_abort();
 }
 
 // One thread per (direction, tile): the adjacent tile of every tile, computed
