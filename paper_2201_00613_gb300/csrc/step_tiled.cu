@@ -1019,6 +1019,14 @@ uint32_t rows_per_word(uint32_t TW, uint32_t TH) {
   return 1;
 }
 
+// Slot word index of local cell c of a TW-wide tile: its slot row times 32
+// plus its lane (rpw tile rows per slot row, or two slot rows per tile row
+// when wpr = 2).
+uint32_t tile_slot_of(uint32_t c, uint32_t TW, uint32_t rpw, uint32_t wpr) {
+  if (wpr == 2) return (c / TW * 2u + c % TW / 32u) * 32u + lane_of(c % TW % 32u);
+  return (c / TW / rpw) * 32u + lane_of((c / TW % rpw) * TW + c % TW);
+}
+
 // Local lambda of the level-L fractal: compact (lx, ly) -> expanded (X, Y).
 void local_lambda(const FracDev &f, uint32_t L, uint32_t lx, uint32_t ly, uint32_t &X,
                   uint32_t &Y) {
@@ -1179,10 +1187,7 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
     local_lambda(f, L, c % TW, c / TW, B.X[c], B.Y[c]);
     inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
-  auto slot_of = [&](uint32_t c) {
-    if (wpr == 2) return (c / TW * 2u + c % TW / 32u) * 32u + lane_of(c % TW % 32u);
-    return (c / TW / rpw) * 32u + lane_of((c / TW % rpw) * TW + c % TW);
-  };
+  auto slot_of = [&](uint32_t c) { return tile_slot_of(c, TW, rpw, wpr); };
   const uint32_t kNone = 0xFFFFFFFFu;
   uint32_t *refs = B.refs;
   for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;

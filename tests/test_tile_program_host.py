@@ -1,0 +1,136 @@
+"""The tiled step's host-built neighbour program, emulated on the CPU.
+
+The tiled kernel never evaluates lambda or nu per cell: the host builds, once
+per fractal and tile level, a program that gives every local cell of a tile
+(a level-L sub-replica) 8 references into a word array of the tile's own
+cells, halo cells of the adjacent tiles (by direction) and a zero word.  This
+test builds that program with the library's own host code
+(tests/tile_host.cu), runs one step with it in numpy over every tile of a
+level-r fractal (adjacent tiles found with the oracle's lambda and nu), and
+compares the result with the oracle's box step, for every tile width the
+kernel instantiates (3, 9, 25, 27, shared 8- and 16-wide slot words, 64-wide
+rows split in two) and several neighbourhoods.  No GPU is needed.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_00613_gb300 import build as B
+from paper_2201_00613_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+P = ctypes.c_void_p
+MAX = np.uint64(2 ** 64 - 1)
+
+DIAG2 = I.Fractal("diag2", 2, 2, ((0, 0), (1, 1)))
+VON_NEUMANN = 0xAA
+ONE_SIDED = sum(1 << ((dy + 1) * 3 + dx + 1) for dx, dy in [(1, 0), (1, 1), (0, -1), (-1, 1)])
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    nvcc = B._nvcc()
+    if not (os.path.isabs(nvcc) and os.path.exists(nvcc)) and shutil.which(nvcc) is None:
+        pytest.skip("nvcc not found")
+    out = str(tmp_path_factory.mktemp("tile_host") / "libtile_host.so")
+    cmd = [nvcc] + B.ARCH + ["-O1", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler",
+                             "-fPIC", "-shared", "-I", B.INCLUDE, "-I", B.CSRC,
+                             os.path.join(HERE, "tile_host.cu"), "-o", out, "-lcudart"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return ctypes.CDLL(out)
+
+
+def ptr(a):
+    return a.ctypes.data_as(P)
+
+
+def program(lib, f, r, L, nbhd):
+    off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
+    caps = np.zeros(3, dtype=np.uint64)
+    assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
+    cells, slots, halo = (int(v) for v in caps)
+    info = np.zeros(8, dtype=np.uint32)
+    slot = np.zeros(cells, dtype=np.uint32)
+    X = np.zeros(cells, dtype=np.uint32)
+    Y = np.zeros(cells, dtype=np.uint32)
+    refs16 = np.zeros(slots * 8, dtype=np.uint16)
+    halo_off = np.zeros(halo, dtype=np.uint32)
+    halo_dir = np.zeros(halo, dtype=np.uint8)
+    dir_list = np.zeros(9, dtype=np.uint8)
+    rc = lib.tile_program(f.s, f.k, ptr(off), r, L, nbhd, ptr(info), ptr(slot), ptr(X), ptr(Y),
+                          ptr(refs16), ptr(halo_off), ptr(halo_dir), ptr(dir_list))
+    assert rc == 0, rc
+    TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs = (int(v) for v in info)
+    return dict(TW=TW, TH=TH, rpw=rpw, wpr=wpr, cells=ncell, slots=nslot, nhalo=nhalo,
+                slot=slot[:ncell].astype(np.int64), X=X[:ncell].astype(np.int64),
+                Y=Y[:ncell].astype(np.int64), refs=(refs16[:nslot * 8] // 4).astype(np.int64),
+                halo_off=halo_off[:nhalo].astype(np.int64), halo_dir=halo_dir[:nhalo],
+                dir_list=dir_list[:ndirs])
+
+
+def emulate_step(f, r, L, prog, state, rule=oracle.B3S23):
+    """One step of every tile through the program's word array (numpy)."""
+    W, H = oracle.compact_shape(f, r)[::-1]
+    TW, TH, side = prog["TW"], prog["TH"], f.s ** L
+    ty, tx = np.mgrid[0:H // TH, 0:W // TW]
+    bases = (ty.ravel() * TH * W + tx.ravel() * TW).astype(np.int64)
+    # the level-L block of each tile: its origin in expanded space
+    origin = oracle.lam(f, r, bases.astype(np.uint64)) - [prog["X"][0], prog["Y"][0]]
+    adj = np.full((len(bases), len(prog["dir_list"])), -1, dtype=np.int64)
+    for j, d in enumerate(prog["dir_list"]):
+        bx, by = int(d) % 3 - 1, int(d) // 3 - 1
+        q = origin + [bx * side + prog["X"][0], by * side + prog["Y"][0]]
+        om = oracle.nu(f, r, q)
+        ok = om != MAX
+        adj[ok, j] = om[ok].astype(np.int64)        # cell 0 of a tile is its base
+    loff = (np.arange(prog["cells"]) // TW) * W + np.arange(prog["cells"]) % TW
+    words = np.zeros((len(bases), prog["slots"] + prog["nhalo"] + 1), dtype=np.int64)
+    own = state[bases[:, None] + loff[None, :]].astype(np.int64) & 1
+    words[:, prog["slot"]] = own
+    for i in range(prog["nhalo"]):
+        a = adj[:, prog["halo_dir"][i]]
+        ok = a >= 0
+        words[ok, prog["slots"] + i] = state[a[ok] + prog["halo_off"][i]] & 1
+    refs = prog["refs"].reshape(-1, 8)[prog["slot"]]          # (cells, 8)
+    count = words[:, refs].sum(axis=2)                        # (tiles, cells)
+    nxt = np.where(own == 1, (rule[1] >> count) & 1, (rule[0] >> count) & 1)
+    out = np.zeros_like(state)
+    out[bases[:, None] + loff[None, :]] = nxt
+    return out
+
+
+CASES = [
+    (I.TRIANGLE, 8, 2, oracle.MOORE), (I.TRIANGLE, 8, 3, oracle.MOORE),
+    (I.TRIANGLE, 8, 5, oracle.MOORE), (I.TRIANGLE, 9, 6, oracle.MOORE),
+    (I.TRIANGLE, 9, 6, VON_NEUMANN), (I.TRIANGLE, 9, 6, ONE_SIDED),
+    (I.TRIANGLE_PAPER, 8, 6, oracle.MOORE),
+    (I.CARPET, 5, 2, oracle.MOORE), (I.CARPET, 5, 3, oracle.MOORE), (I.CARPET, 5, 3, ONE_SIDED),
+    (I.VICSEK, 6, 3, oracle.MOORE), (I.VICSEK, 6, 4, oracle.MOORE),
+    (I.FULL2, 8, 3, oracle.MOORE), (I.FULL2, 8, 4, oracle.MOORE), (I.FULL2, 8, 5, oracle.MOORE),
+    (DIAG2, 10, 5, oracle.MOORE), (DIAG2, 10, 7, oracle.MOORE), (DIAG2, 10, 9, VON_NEUMANN),
+]
+
+
+@pytest.mark.parametrize("f,r,L,nbhd", CASES,
+                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CASES])
+def test_program_step_equals_the_oracle(lib, f, r, L, nbhd):
+    prog = program(lib, f, r, L, nbhd)
+    assert prog["cells"] == f.k ** L
+    state = I.bernoulli_bytes(100 + r + L, f.k ** r, 0.45)
+    m = oracle.member_grid(f, r)
+    want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
+        m, oracle.compact_to_box(f, r, state), 1, oracle.B3S23, nbhd))
+    assert np.array_equal(emulate_step(f, r, L, prog, state), want)
+
+
+def test_program_shapes_cover_every_kernel_width(lib):
+    seen = set()
+    for f, r, L, nbhd in CASES:
+        p = program(lib, f, r, L, nbhd)
+        seen.add((p["TW"], p["rpw"], p["wpr"]))
+    assert {(27, 1, 1), (25, 1, 1), (8, 4, 1), (16, 2, 1), (64, 1, 2)} <= seen

@@ -1,0 +1,97 @@
+// tile_host.cu -- test support: the host-built neighbour program of the tiled
+// step (step_tiled.cu), exported so that a CPU emulation of one step can run
+// on it and be compared with the oracle.  No CUDA calls are made.
+#include "step_tiled.cu"
+
+int sq_cuda_fail(cudaError_t) { return SQUEEZE_ERR_CUDA; }   // never reached: no CUDA calls here
+void sq_set_error_text(const char *) {}
+
+namespace {
+
+// The kernel-side descriptor of a level-r fractal (the fields the builder reads).
+bool fill(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t nbhd, FracDev &f) {
+  memset(&f, 0, sizeof(f));
+  f.s = s;
+  f.k = k;
+  f.r = r;
+  f.n = (uint32_t)ipow(s, r);
+  f.W = (uint32_t)ipow(k, (r + 1) / 2);
+  f.H = (uint32_t)ipow(k, r / 2);
+  f.cells = (uint64_t)f.W * f.H;
+  f.divk = make_fastdiv(k);
+  f.divs = make_fastdiv(s);
+  f.divW = make_fastdiv(f.W);
+  f.nbhd = nbhd;
+  memset(f.hnu, kHole, sizeof(f.hnu));
+  for (uint32_t b = 0; b < k; ++b) {
+    if (off[2 * b] >= s || off[2 * b + 1] >= s) return false;
+    f.taux[b] = off[2 * b];
+    f.tauy[b] = off[2 * b + 1];
+    f.hnu[off[2 * b + 1] * s + off[2 * b]] = (uint8_t)b;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Capacities of the program arrays: cells, slots, halo entries.
+int tile_sizes(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L, uint64_t *out) {
+  FracDev f;
+  if (!fill(s, k, off, r, kMoore, f)) return SQUEEZE_ERR_INVALID_ARG;
+  TileBuildSizes z;
+  sq_tile_build_sizes(f, L, z);
+  out[0] = z.cells;
+  out[1] = z.slots;
+  out[2] = z.halo;
+  return SQUEEZE_OK;
+}
+
+// The level-L program: info = (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs);
+// per local cell its slot and local expanded position; per slot 8 byte
+// offsets into the word array (slots, then halo words, then a zero word);
+// per halo word its offset from the adjacent tile's base and its direction
+// index into dir_list.
+int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L,
+                 uint32_t nbhd, uint32_t *info, uint32_t *slot, uint32_t *X, uint32_t *Y,
+                 uint16_t *refs16, uint32_t *halo_off, uint8_t *halo_dir, uint8_t *dir_list) {
+  FracDev f;
+  if (!fill(s, k, off, r, nbhd, f)) return SQUEEZE_ERR_INVALID_ARG;
+  TileBuildSizes z;
+  sq_tile_build_sizes(f, L, z);
+  std::vector<int32_t> inv(z.box);
+  std::vector<uint32_t> vX(z.cells), vY(z.cells), refs(z.slots * 8), order(z.halo), rank(z.halo);
+  std::vector<uint64_t> key(z.halo), sorted(z.halo);
+  TileBuild B;
+  B.inv = inv.data();
+  B.X = vX.data();
+  B.Y = vY.data();
+  B.refs = refs.data();
+  B.halo_key = key.data();
+  B.halo_sorted = sorted.data();
+  B.order = order.data();
+  B.rank = rank.data();
+  B.refs16 = refs16;
+  B.halo_off = halo_off;
+  B.halo_dir = halo_dir;
+  B.box_cap = z.box;
+  B.cells_cap = z.cells;
+  B.slots_cap = z.slots;
+  B.halo_cap = z.halo;
+  TileSpec sp;
+  const int rc = sq_tile_build(f, L, B, sp);
+  if (rc) return rc;
+  const uint32_t wpr = sp.TW == 64 ? 2u : 1u;
+  const uint32_t v[8] = {sp.TW, sp.TH, sp.rpw, wpr, sp.cells, sp.slots, sp.nhalo, sp.ndirs};
+  memcpy(info, v, sizeof(v));
+  for (uint32_t c = 0; c < sp.cells; ++c) {
+    slot[c] = tile_slot_of(c, sp.TW, sp.rpw, wpr);
+    X[c] = vX[c];
+    Y[c] = vY[c];
+  }
+  memcpy(dir_list, sp.dir_list, 9);
+  return SQUEEZE_OK;
+}
+
+}  // extern "C"
