@@ -85,7 +85,8 @@ __device__ __forceinline__ uint32_t rule_word(const Rule &rule, uint32_t self, c
 // Carry walk: the level-L block adjacent to tile (tx, ty) in direction
 // (dx, dy), as a tile (ntx, nty), or false for a hole / off the box.  Tile
 // coordinates fit 32 bits, so the digit updates use wrap-around arithmetic.
-__device__ bool adjacent_tile(const FracDev &f, uint32_t L, const uint8_t *taux,
+// Host-callable too, so that the walk can be checked on the CPU.
+__host__ __device__ bool adjacent_tile(const FracDev &f, uint32_t L, const uint8_t *taux,
                               const uint8_t *tauy, const uint8_t *hnu, uint32_t tx, uint32_t ty,
                               int dx, int dy, uint32_t &ntx, uint32_t &nty) {
   int cx = dx, cy = dy;

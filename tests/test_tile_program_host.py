@@ -6,10 +6,11 @@ per fractal and tile level, a program that gives every local cell of a tile
 cells, halo cells of the adjacent tiles (by direction) and a zero word.  This
 test builds that program with the library's own host code
 (tests/tile_host.cu), runs one step with it in numpy over every tile of a
-level-r fractal (adjacent tiles found with the oracle's lambda and nu), and
-compares the result with the oracle's box step, for every tile width the
-kernel instantiates (3, 9, 25, 27, shared 8- and 16-wide slot words, 64-wide
-rows split in two) and several neighbourhoods.  No GPU is needed.
+level-r fractal, and compares the result with the oracle's box step, for
+every tile width the kernel instantiates (3, 9, 25, 27, shared 8- and 16-wide
+slot words, 64-wide rows split in two) and several neighbourhoods.  The adjacent tiles come from
+the kernel's own carry walk (host-callable), which is also compared with the
+tiles the oracle's lambda and nu give.  No GPU is needed.
 """
 import ctypes
 import os
@@ -73,13 +74,16 @@ def program(lib, f, r, L, nbhd):
                 dir_list=dir_list[:ndirs])
 
 
-def emulate_step(f, r, L, prog, state, rule=oracle.B3S23):
-    """One step of every tile through the program's word array (numpy)."""
+def tile_bases(f, r, prog):
     W, H = oracle.compact_shape(f, r)[::-1]
-    TW, TH, side = prog["TW"], prog["TH"], f.s ** L
-    ty, tx = np.mgrid[0:H // TH, 0:W // TW]
-    bases = (ty.ravel() * TH * W + tx.ravel() * TW).astype(np.int64)
-    # the level-L block of each tile: its origin in expanded space
+    ty, tx = np.mgrid[0:H // prog["TH"], 0:W // prog["TW"]]
+    return (ty.ravel() * prog["TH"] * W + tx.ravel() * prog["TW"]).astype(np.int64)
+
+
+def oracle_adjacency(f, r, L, prog):
+    """Base of the tile adjacent to each tile in each program direction (-1:
+    none), from the oracle's lambda and nu of the tiles' first cells."""
+    bases, side = tile_bases(f, r, prog), f.s ** L
     origin = oracle.lam(f, r, bases.astype(np.uint64)) - [prog["X"][0], prog["Y"][0]]
     adj = np.full((len(bases), len(prog["dir_list"])), -1, dtype=np.int64)
     for j, d in enumerate(prog["dir_list"]):
@@ -88,6 +92,27 @@ def emulate_step(f, r, L, prog, state, rule=oracle.B3S23):
         om = oracle.nu(f, r, q)
         ok = om != MAX
         adj[ok, j] = om[ok].astype(np.int64)        # cell 0 of a tile is its base
+    return adj
+
+
+def library_adjacency(lib, f, r, L, prog):
+    """The same from the kernel's carry walk (tile indices turned into bases)."""
+    off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
+    bases = tile_bases(f, r, prog)
+    adj = np.full((len(bases), len(prog["dir_list"])), -1, dtype=np.int64)
+    for j, d in enumerate(prog["dir_list"]):
+        t = np.zeros(len(bases), dtype=np.uint32)
+        assert lib.tile_adjacency(f.s, f.k, ptr(off), r, L, int(d), ptr(t)) == 0
+        ok = t != np.uint32(2 ** 32 - 1)
+        adj[ok, j] = bases[t[ok].astype(np.int64)]
+    return adj
+
+
+def emulate_step(f, r, L, prog, state, adj, rule=oracle.B3S23):
+    """One step of every tile through the program's word array (numpy)."""
+    W = oracle.compact_shape(f, r)[1]
+    TW = prog["TW"]
+    bases = tile_bases(f, r, prog)
     loff = (np.arange(prog["cells"]) // TW) * W + np.arange(prog["cells"]) % TW
     words = np.zeros((len(bases), prog["slots"] + prog["nhalo"] + 1), dtype=np.int64)
     own = state[bases[:, None] + loff[None, :]].astype(np.int64) & 1
@@ -125,7 +150,9 @@ def test_program_step_equals_the_oracle(lib, f, r, L, nbhd):
     m = oracle.member_grid(f, r)
     want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
         m, oracle.compact_to_box(f, r, state), 1, oracle.B3S23, nbhd))
-    assert np.array_equal(emulate_step(f, r, L, prog, state), want)
+    adj = library_adjacency(lib, f, r, L, prog)
+    assert np.array_equal(adj, oracle_adjacency(f, r, L, prog))
+    assert np.array_equal(emulate_step(f, r, L, prog, state, adj), want)
 
 
 def test_program_shapes_cover_every_kernel_width(lib):

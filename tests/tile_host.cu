@@ -94,4 +94,24 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   return SQUEEZE_OK;
 }
 
+// The tile adjacent to every tile (tx, ty) of the level-r fractal in
+// direction d = (dy+1)*3 + (dx+1), by the kernel's carry walk:
+// out[ty * tiles_x + tx] = nty * tiles_x + ntx, or UINT32_MAX for none.
+int tile_adjacency(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L, uint32_t d,
+                   uint32_t *out) {
+  FracDev f;
+  if (!fill(s, k, off, r, kMoore, f)) return SQUEEZE_ERR_INVALID_ARG;
+  const uint32_t TW = (uint32_t)ipow(k, (L + 1) / 2), TH = (uint32_t)ipow(k, L / 2);
+  const uint32_t tiles_x = f.W / TW, tiles_y = f.H / TH;
+  for (uint32_t ty = 0; ty < tiles_y; ++ty)
+    for (uint32_t tx = 0; tx < tiles_x; ++tx) {
+      uint32_t ntx, nty, v = ~0u;
+      if (adjacent_tile(f, L, f.taux, f.tauy, f.hnu, tx, ty, (int)(d % 3) - 1, (int)(d / 3) - 1,
+                        ntx, nty))
+        v = nty * tiles_x + ntx;
+      out[(size_t)ty * tiles_x + tx] = v;
+    }
+  return SQUEEZE_OK;
+}
+
 }  // extern "C"
