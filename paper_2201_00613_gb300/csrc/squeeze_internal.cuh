@@ -86,8 +86,8 @@ __device__ inline void load_tables(SmemTables &t, const FracDev &f) {
 
 // lambda (Sec. 3.3): sum over levels mu = 1..r of tau(beta_mu) * s^(mu-1),
 // beta_mu the base-k digit ceil(mu/2)-1 of w_x (odd mu) or w_y (even mu).
-__device__ inline void lambda_alu(const FracDev &f, const SmemTables &t, uint32_t wx,
-                                  uint32_t wy, uint32_t &x, uint32_t &y) {
+__host__ __device__ inline void lambda_alu(const FracDev &f, const SmemTables &t, uint32_t wx,
+                                           uint32_t wy, uint32_t &x, uint32_t &y) {
   uint32_t X = 0, Y = 0, scale = 1;
   for (uint32_t mu = 1; mu <= f.r; ++mu) {
     uint32_t src = (mu & 1u) ? wx : wy;
@@ -105,8 +105,8 @@ __device__ inline void lambda_alu(const FracDev &f, const SmemTables &t, uint32_
 // nu (Sec. 3.4): per level the base-s digit pair theta_mu selects a replica id
 // through H_nu (a hole rejects the point); odd levels accumulate id *
 // k^floor((mu-1)/2) on w_x, even levels on w_y.
-__device__ inline bool nu_alu(const FracDev &f, const SmemTables &t, int32_t x, int32_t y,
-                              uint32_t &wx, uint32_t &wy) {
+__host__ __device__ inline bool nu_alu(const FracDev &f, const SmemTables &t, int32_t x, int32_t y,
+                                       uint32_t &wx, uint32_t &wy) {
   if (x < 0 || y < 0 || (uint32_t)x >= f.n || (uint32_t)y >= f.n) return false;
   uint32_t ux = (uint32_t)x, uy = (uint32_t)y;
   uint32_t nx = 0, ny = 0, wtx = 1, wty = 1;
@@ -138,9 +138,9 @@ __device__ inline bool nu_alu(const FracDev &f, const SmemTables &t, int32_t x, 
 // reads the cell's replica digit beta_mu, moves its offset tau(beta_mu) by the
 // carries, looks up the new replica through H_nu (a hole ends the walk) and
 // corrects that level's term of the compact index.
-__device__ inline bool neighbour_omega(const FracDev &f, const SmemTables &t, uint32_t wx,
-                                       uint32_t wy, int dx, int dy, uint32_t &nwx,
-                                       uint32_t &nwy) {
+__host__ __device__ inline bool neighbour_omega(const FracDev &f, const SmemTables &t, uint32_t wx,
+                                                uint32_t wy, int dx, int dy, uint32_t &nwx,
+                                                uint32_t &nwy) {
   uint32_t rx = wx, ry = wy;
   nwx = wx;
   nwy = wy;
