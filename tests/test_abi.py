@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI: the library builds, loads, and exports every
-entry point declared in include/squeeze.h.  No GPU is needed."""
+entry point declared in include/squeeze.h, and a plain C99 caller builds, links
+and runs against it.  No GPU is needed."""
 import os
 import re
 import subprocess
@@ -80,3 +81,47 @@ def test_3d_null_handle_is_rejected():
         with pytest.raises(sq.SqueezeError) as e:
             call()
         assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "squeeze.h"
+
+int main(int argc, char **argv) {
+  const uint8_t tri[6] = {0, 0, 1, 0, 0, 1};
+  const uint8_t bad[6] = {0, 0, 1, 0, 1, 0};           /* repeated offset */
+  uint8_t state[27], back[27];
+  uint64_t step = 0;
+  squeeze_handle *h = 0;
+  int i;
+  if (argc < 2) return 90;
+  if (strcmp(squeeze_status_string(SQUEEZE_ERR_IO), "ok") == 0) return 91;
+  if (squeeze_create(2, 3, bad, 3, &h) != SQUEEZE_ERR_INVALID_ARG || h) return 92;
+  if (squeeze_info(0, 0, 0, 0, 0) != SQUEEZE_ERR_INVALID_ARG) return 93;
+  for (i = 0; i < 27; ++i) state[i] = (uint8_t)(i % 2);
+  if (squeeze_checkpoint_write(2, 3, tri, 3, 42, state, argv[1]) != SQUEEZE_OK) return 94;
+  if (squeeze_checkpoint_read(2, 3, tri, 3, &step, back, argv[1]) != SQUEEZE_OK) return 95;
+  if (step != 42 || memcmp(state, back, 27) != 0) return 96;
+  if (squeeze_checkpoint_read(2, 3, tri, 4, &step, back, argv[1]) != SQUEEZE_ERR_INVALID_ARG)
+    return 97;
+  printf("c caller ok\n");
+  return 0;
+}
+"""
+
+
+def test_c_caller_compiles_links_and_runs_without_a_gpu(tmp_path):
+    """The header is plain C99; a C program linked against the library calls
+    entry points that need no GPU (status text, argument errors, checkpoints)."""
+    path = build.build()
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(path)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lsqueeze", "-Wl,-rpath," + libdir], check=True)
+    res = subprocess.run([str(exe), str(tmp_path / "c.ckpt")], capture_output=True, text=True)
+    assert res.returncode == 0, (res.returncode, res.stderr)
+    assert "c caller ok" in res.stdout
