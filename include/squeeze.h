@@ -418,14 +418,15 @@ int squeeze_3d_set_rule(squeeze_3d_handle *h, uint32_t birth, uint32_t survive);
 int squeeze_3d_set_neighbourhood(squeeze_3d_handle *h, uint32_t mask);
 
 /* squeeze_3d_lambda -- compact -> expanded.  d_omega: count uint64 (8-byte
- * aligned); d_xyz receives 3*count int32 (x, y, z), (-1, -1, -1) for an index
- * >= k^r. */
+ * aligned); d_xyz (4-byte aligned) receives 3*count int32 (x, y, z),
+ * (-1, -1, -1) for an index >= k^r.  A misaligned pointer is INVALID_ARG. */
 int squeeze_3d_lambda(const squeeze_3d_handle *h, const uint64_t *d_omega, int32_t *d_xyz,
                       uint64_t count, void *stream);
 
 /* squeeze_3d_nu -- expanded -> compact with hole rejection.  d_xyz: 3*count
- * int32 points, any values; d_omega receives the compact index, or
- * UINT64_MAX for a hole or a point off the box. */
+ * int32 points (4-byte aligned), any values; d_omega (8-byte aligned)
+ * receives the compact index, or UINT64_MAX for a hole or a point off the
+ * box.  A misaligned pointer is INVALID_ARG. */
 int squeeze_3d_nu(const squeeze_3d_handle *h, const int32_t *d_xyz, uint64_t *d_omega,
                   uint64_t count, void *stream);
 
