@@ -97,7 +97,8 @@ int squeeze_set_rule(squeeze_handle *h, uint32_t birth, uint32_t survive);
  *   d_omega  count linear compact indices (uint64).
  *   d_xy     receives 2*count int32: (x, y) per index; (-1, -1) for an index
  *            >= k^r.
- * Uses the integer ALU form. */
+ * Both arrays must be 8-byte aligned (else INVALID_ARG).  Uses the integer
+ * ALU form. */
 int squeeze_lambda(const squeeze_handle *h, const uint64_t *d_omega, int32_t *d_xy,
                    uint64_t count, void *stream);
 
@@ -106,7 +107,8 @@ int squeeze_lambda(const squeeze_handle *h, const uint64_t *d_omega, int32_t *d_
  * levels accumulated on x, which makes nu the inverse of lambda).
  *   d_xy     2*count int32 points (x, y); any value is allowed.
  *   d_omega  receives count uint64: the compact index, or UINT64_MAX for a
- *            hole or a point outside [0, s^r)^2. */
+ *            hole or a point outside [0, s^r)^2.
+ * Both arrays must be 8-byte aligned (else INVALID_ARG). */
 int squeeze_nu(const squeeze_handle *h, const int32_t *d_xy, uint64_t *d_omega,
                uint64_t count, void *stream);
 
