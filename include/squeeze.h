@@ -148,7 +148,12 @@ int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t s
  *   d_buf1   k^r bytes, scratch for the other parity.
  *   The result is in d_buf0 when n_steps is even and in d_buf1 when odd.
  *   kind     SQUEEZE_STEP_* / SQUEEZE_MAP_*.  TC_I8 -> UNSUPPORTED.
- * The two buffers must not overlap.  n_steps = 0 enqueues nothing. */
+ * The two buffers must not overlap.  n_steps = 0 enqueues nothing.  The tiled
+ * kernel needs both buffers 16-byte aligned (its bulk copies): TILED with a
+ * misaligned buffer is INVALID_ARG, and AUTO then takes the per-cell ALU
+ * kernel.  A level whose tiled program would not fit is UNSUPPORTED for
+ * TILED (AUTO falls back to the per-cell ALU kernel only when no tile level
+ * fits at all). */
 int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                  int kind, void *stream);
 
