@@ -1,11 +1,13 @@
 """Run the compact step on one level for profiler captures.
 
   python -m paper_2201_00613_gb300.profile_step --level 18 --steps 3 [--kind tiled|alu|tc]
-      [--fractal triangle|carpet|vicsek] [--maps N]
+      [--fractal triangle|carpet|vicsek|menger|tetrahedron] [--maps N]
 
-Initialises the seeded Bernoulli(0.5) triangle state at the given level and
-runs `steps` steps, one kernel launch per step.  Used with ncu on a case that
-is larger than L2 but small enough for a multi-pass capture.
+Initialises the seeded Bernoulli(0.5) state of the fractal at the given level
+and runs `steps` steps, one kernel launch per step (the three-dimensional
+fractals take the per-cell 3-D step; --kind and --maps apply to the planar
+ones).  Used with ncu on a case that is larger than L2 but small enough for a
+multi-pass capture.
 """
 import argparse
 import sys
@@ -17,6 +19,19 @@ from . import inputs as I
 
 KINDS = {"tiled": sq.SQUEEZE_STEP_TILED, "alu": sq.SQUEEZE_MAP_ALU, "tc": sq.SQUEEZE_MAP_TC_BF16}
 FRACTALS = {"triangle": I.TRIANGLE, "carpet": I.CARPET, "vicsek": I.VICSEK}
+FRACTALS_3D = {"menger": I.MENGER, "tetrahedron": I.TETRA}
+
+
+def run_3d(f, level, steps):
+    with sq.Handle3(f, level) as h:
+        s0 = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+        s1 = torch.empty_like(s0)
+        sq.squeeze_3d_init_bernoulli(h.h, s0, 3, I.p_q24(0.5))
+        sq.squeeze_3d_step(h.h, s0, s1, steps)
+        torch.cuda.synchronize()
+        st = sq.squeeze_3d_device_status(h.h)
+        print("3-D %s level %d cells %d steps %d status %d" % (f.name, level, h.cells, steps, st))
+        return 0 if st == 0 else 1
 
 
 def main(argv=None):
@@ -24,11 +39,13 @@ def main(argv=None):
     p.add_argument("--level", type=int, default=18)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--kind", default="tiled", choices=sorted(KINDS))
-    p.add_argument("--fractal", default="triangle", choices=sorted(FRACTALS))
+    p.add_argument("--fractal", default="triangle", choices=sorted(FRACTALS) + sorted(FRACTALS_3D))
     p.add_argument("--maps", type=int, default=0,
                    help="first run lambda then nu over this many seeded points (with --kind tc "
                         "on the tensor cores, else on the ALU)")
     a = p.parse_args(argv)
+    if a.fractal in FRACTALS_3D:
+        return run_3d(FRACTALS_3D[a.fractal], a.level, a.steps)
     f = FRACTALS[a.fractal]
     with sq.Handle(f, a.level) as h:
         if a.maps:
