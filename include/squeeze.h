@@ -353,8 +353,10 @@ int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_
  * counterpart; this is an interface of this library only.  File layout,
  * little-endian: a 64-byte header (magic "SQZSTATE", version 1, header size,
  * s, k, r, dimensions = 2, step, state bytes k^r, FNV-1a 64-bit hash of the
- * state, reserved 0), the 2k offset bytes zero-padded to a multiple of 8,
- * then the k^r state bytes in compact order.  The rule and neighbourhood are
+ * state, FNV-1a 64-bit hash of the header with this last word as 0 followed
+ * by the padded offsets), the 2k offset bytes zero-padded to a multiple of 8,
+ * then the k^r state bytes in compact order.  A single damaged byte anywhere
+ * in the file changes one of the two hashes.  The rule and neighbourhood are
  * not stored: they belong to the handle that resumes the run. */
 
 /* squeeze_checkpoint_write -- write h_state (k^r bytes) and `step` to `path`.
@@ -369,8 +371,8 @@ int squeeze_checkpoint_write(uint32_t s, uint32_t k, const uint8_t *offsets, uin
  * into h_state (k^r bytes) and *step.  Errors: INVALID_ARG for a bad
  * descriptor or a valid checkpoint of another fractal, offset table or
  * level; IO for a missing or unreadable file, a file that is not a
- * checkpoint, a truncated or over-long file, or a state whose hash does not
- * match.  After an error h_state's contents are unspecified and *step is not
+ * checkpoint, a truncated or over-long file, or a header or state whose hash
+ * does not match.  After an error h_state's contents are unspecified and *step is not
  * written. */
 int squeeze_checkpoint_read(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
                             uint64_t *step, uint8_t *h_state, const char *path);

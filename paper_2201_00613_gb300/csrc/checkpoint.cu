@@ -4,10 +4,13 @@
 // device and a host buffer.  A checkpoint file is, in little-endian order, a
 // 64-byte header (magic "SQZSTATE", format version, header size, s, k, r,
 // the number of dimensions (2), the step count, the state size k^r, the
-// FNV-1a 64-bit hash of the state and a reserved word), the 2k offset bytes
+// FNV-1a 64-bit hash of the state and the FNV-1a 64-bit hash of the header
+// (this word read as 0) followed by the padded offsets), the 2k offset bytes
 // padded with zeros to a multiple of 8, and the k^r state bytes in compact
-// order.  Files are written under a temporary name and renamed into place, so
-// a reader sees either the old file or the complete new one.
+// order.  FNV-1a changes its hash for any single changed byte, so one
+// damaged byte anywhere in the file is caught.  Files are written under a
+// temporary name and renamed into place, so a reader sees either the old file
+// or the complete new one.
 #include <errno.h>
 #include <stdio.h>
 #include <string.h>
@@ -28,19 +31,24 @@ struct Header {
   uint64_t step;
   uint64_t state_bytes;
   uint64_t checksum;        // FNV-1a 64 of the state bytes
-  uint64_t reserved;
+  uint64_t header_hash;     // FNV-1a 64 of this header (this word as 0) and the padded offsets
 };
 static_assert(sizeof(Header) == 64, "checkpoint header layout");
 
 // FNV-1a, 64-bit (Fowler, Noll, Vo): per byte, xor it in, then multiply by
 // the FNV prime 2^40 + 2^8 + 0xb3, starting from the offset basis.
-uint64_t fnv1a64(const uint8_t *p, uint64_t n) {
-  uint64_t h = 0xcbf29ce484222325ull;
+constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
+uint64_t fnv1a64(const uint8_t *p, uint64_t n, uint64_t h = kFnvBasis) {
   for (uint64_t i = 0; i < n; ++i) {
     h ^= p[i];
     h *= 0x100000001b3ull;
   }
   return h;
+}
+
+uint64_t header_hash_of(Header hd, const uint8_t *off, uint32_t off_bytes) {
+  hd.header_hash = 0;
+  return fnv1a64(off, off_bytes, fnv1a64(reinterpret_cast<const uint8_t *>(&hd), sizeof(hd)));
 }
 
 uint32_t padded_offsets(uint32_t k) { return (2 * k + 7) / 8 * 8; }
@@ -100,6 +108,7 @@ int squeeze_checkpoint_write(uint32_t s, uint32_t k, const uint8_t *offsets, uin
   uint8_t off[2 * 256 + 8];
   memset(off, 0, sizeof(off));
   memcpy(off, offsets, 2 * k);
+  hd.header_hash = header_hash_of(hd, off, padded_offsets(k));
 
   char tmp[4096];
   if (snprintf(tmp, sizeof(tmp), "%s.tmp%ld", path, (long)getpid()) >= (int)sizeof(tmp))
@@ -145,6 +154,11 @@ int squeeze_checkpoint_read(uint32_t s, uint32_t k, const uint8_t *offsets, uint
   if (!ok) {
     fclose(fp);
     return io_fail("not a checkpoint:", path);
+  }
+  if (header_hash_of(hd, off, padded_offsets(hd.k)) != hd.header_hash) {
+    fclose(fp);
+    errno = 0;
+    return io_fail("damaged checkpoint header:", path);
   }
   // a valid file of another fractal or level is the caller's mistake, not damage
   if (hd.s != s || hd.k != k || hd.r != r || memcmp(off, offsets, 2 * k) != 0 ||

@@ -1,9 +1,10 @@
 """Checkpoint and resume of a compact state (squeeze_checkpoint_write / _read).
 
 The file functions are host code, so everything but the last test runs without
-a GPU: the round trip, the header layout, the FNV-1a hash against published
-test vectors, rejection of another fractal or level (INVALID_ARG) and of a
-damaged, truncated, over-long or foreign file (IO), and atomic replacement.
+a GPU: the round trip, the header layout, the FNV-1a hashes (the state's
+against published test vectors), rejection of another fractal or level
+(INVALID_ARG) and of a damaged, truncated, over-long or foreign file (IO), any
+single damaged byte, and atomic replacement.
 The GPU test checks that a run stopped halfway, written out, read back and
 resumed ends bit for bit where the uninterrupted run ends.
 """
@@ -15,6 +16,14 @@ import pytest
 
 import paper_2201_00613_gb300 as sq
 from paper_2201_00613_gb300 import inputs as I
+
+
+def fnv1a64(data: bytes) -> int:
+    """FNV-1a, 64-bit (Fowler, Noll, Vo), written out for the test."""
+    h = 0xCBF29CE484222325
+    for b in data:
+        h = ((h ^ b) * 0x100000001B3) & (2 ** 64 - 1)
+    return h
 
 
 def write(f, r, step, state, path):
@@ -41,12 +50,14 @@ def test_round_trip_and_header_layout(tmp_path):
     step, back = read(f, r, path)
     assert step == 12345 and np.array_equal(back, state)
     raw = open(path, "rb").read()
-    magic, version, hbytes, s, k, rr, dims, st, nbytes, _, reserved = struct.unpack(
+    magic, version, hbytes, s, k, rr, dims, st, nbytes, shash, hhash = struct.unpack(
         "<8sIIIIIIQQQQ", raw[:64])
     assert (magic, version, hbytes, s, k, rr, dims) == (b"SQZSTATE", 1, 72, 2, 3, 7, 2)
-    assert (st, nbytes, reserved) == (12345, 3 ** 7, 0)
+    assert (st, nbytes) == (12345, 3 ** 7)
     assert raw[64:72] == bytes([0, 0, 1, 0, 0, 1, 0, 0])        # offsets, zero-padded
     assert len(raw) == 72 + 3 ** 7 and raw[72:] == state.tobytes()
+    assert shash == fnv1a64(state.tobytes())
+    assert hhash == fnv1a64(raw[:56] + bytes(8) + raw[64:72])   # header (this word as 0), offsets
     assert not [p for p in os.listdir(tmp_path) if ".tmp" in p]
 
 
@@ -74,7 +85,7 @@ def test_another_fractal_or_level_is_an_argument_error(tmp_path):
 
 
 @pytest.mark.parametrize("damage", ["flip", "truncate", "append", "magic", "version", "garbage",
-                                    "missing", "empty"])
+                                    "missing", "empty", "step", "offsets", "state_hash"])
 def test_damaged_files_are_io_errors(tmp_path, damage):
     f, r = I.CARPET, 3
     path = str(tmp_path / "c.ckpt")
@@ -94,12 +105,32 @@ def test_damaged_files_are_io_errors(tmp_path, damage):
         raw = bytearray(b"not a checkpoint at all")
     elif damage == "empty":
         raw = bytearray()
+    elif damage == "step":
+        raw[32] ^= 4                     # step count 7 -> 3
+    elif damage == "offsets":
+        raw[64] ^= 1
+    elif damage == "state_hash":
+        raw[48] ^= 0x80
     if damage == "missing":
         os.remove(path)
     else:
         open(path, "wb").write(bytes(raw))
     assert code_of(lambda: read(f, r, path)) == sq.SQUEEZE_ERR_IO
     assert sq.squeeze_last_cuda_error()          # the reason is recorded
+
+
+def test_any_single_damaged_byte_is_caught(tmp_path):
+    f, r = I.TRIANGLE, 4
+    path = str(tmp_path / "t.ckpt")
+    write(f, r, 99, I.bernoulli_bytes(6, f.k ** r, 0.5), path)
+    raw = open(path, "rb").read()
+    rng = np.random.default_rng(0)
+    for pos in sorted(set(rng.integers(0, len(raw), 200).tolist()) | {8, 12, 32, 48, 56, 64}):
+        bad = bytearray(raw)
+        bad[pos] ^= int(rng.integers(1, 256))
+        open(path, "wb").write(bytes(bad))
+        code = code_of(lambda: read(f, r, path))
+        assert code in (sq.SQUEEZE_ERR_IO, sq.SQUEEZE_ERR_INVALID_ARG), (pos, code)
 
 
 def test_writes_replace_atomically_and_failures_leave_nothing(tmp_path):
