@@ -82,7 +82,8 @@ def check_neighbours(lib, f, r, om):
 
 
 @pytest.mark.parametrize("f,r", [(I.TRIANGLE, 7), (I.TRIANGLE_PAPER, 6), (I.CARPET, 4),
-                                 (I.VICSEK, 5), (I.FULL2, 6), (I.SINGLE, 4), (DIAG2, 9), (BIG, 2)],
+                                 (I.VICSEK, 5), (I.FULL2, 6), (I.SINGLE, 4), (DIAG2, 9), (BIG, 2),
+                                 (I.TRIANGLE, 0), (I.CARPET, 1), (BIG, 1)],
                          ids=lambda v: getattr(v, "name", str(v)))
 def test_maps_and_walk_on_every_cell(lib, f, r):
     om = np.arange(f.k ** r + 3, dtype=np.uint64)
