@@ -138,6 +138,7 @@ CASES = [
     (I.VICSEK, 6, 3, oracle.MOORE), (I.VICSEK, 6, 4, oracle.MOORE),
     (I.FULL2, 8, 3, oracle.MOORE), (I.FULL2, 8, 4, oracle.MOORE), (I.FULL2, 8, 5, oracle.MOORE),
     (DIAG2, 10, 5, oracle.MOORE), (DIAG2, 10, 7, oracle.MOORE), (DIAG2, 10, 9, VON_NEUMANN),
+    (I.TRIANGLE, 6, 6, oracle.MOORE), (I.CARPET, 3, 3, oracle.MOORE),   # one tile: no neighbours
 ]
 
 
