@@ -12,11 +12,9 @@ bounding-box kernel on the full state at steps 1, 10, 100 and 1000; the CPU
 bounding-box oracle, run on the whole 65,536^2 box, equals the tiled step at
 every step from 1 to 10; a few cells match the oracle's light cone at T = 1000.
 
-Several minutes each (and a 13 GB host box at r = 16), so they run only when
-SQUEEZE_LONG=1 is set.
+Together about four minutes on a GB300 (the per-cell tensor-core step over
+3.5e9 cells dominates) and 13 GB of host memory for the r = 16 box.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -24,9 +22,7 @@ import oracle
 from paper_2201_00613_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SQUEEZE_LONG") != "1",
-                                 reason="long run: set SQUEEZE_LONG=1")]
+pytestmark = pytest.mark.gpu
 
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
