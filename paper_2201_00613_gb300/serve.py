@@ -10,6 +10,9 @@ that no active request overshoots.  Requests that arrive while a round is on
 the GPU join at the next round boundary, so their work overlaps with that of
 the requests already running.  A finished request's state stays on the
 device; its latency is the time from arrival to the end of its last round.
+A request that does not fit while nothing else of the loop is active can
+never be admitted (no memory of the loop's will be given back): it is
+rejected and recorded, and the loop goes on with the next one.
 cancel() withdraws a request from any thread: at the next round boundary a
 queued request is dropped before admission and an active one gives up its
 slot and its buffers; a request that has already finished keeps its result.
@@ -49,7 +52,12 @@ class DeviceBackend:
         self.device = torch.device(device)
 
     def free_bytes(self) -> int:
-        return self.torch.cuda.mem_get_info(self.device)[0]
+        # Blocks that torch's caching allocator holds but no tensor uses are
+        # free for the next request's buffers as well.
+        free = self.torch.cuda.mem_get_info(self.device)[0]
+        cached = (self.torch.cuda.memory_reserved(self.device)
+                  - self.torch.cuda.memory_allocated(self.device))
+        return free + max(0, cached)
 
     def handle(self, inst, level):
         h = self.sq.Handle(inst.fractal, inst.r)
@@ -71,7 +79,7 @@ class DeviceBackend:
 
     def batch(self, slots):
         batch = self.sq.squeeze_batch_create([(s.handle.h, s.cur, s.other) for s in slots])
-        self.sq.squeeze_batch_configure(batch, 288, 0, False)  # round lengths vary: no graphs
+        self.sq.squeeze_batch_configure(batch, 0, 0, False)  # round lengths vary: no graphs
         return batch
 
     def run(self, batch, k: int):
@@ -100,7 +108,10 @@ class RequestLoop:
         self.handles = {}   # (fractal name, r) -> handle, shared by the requests of that shape
         self.rounds = 0
         self.batches_built = 0
-        self.refused_for_memory = 0
+        self.refused_for_memory = 0  # requests that had to wait for memory (each counted once)
+        self.rejected = []           # requests that could not fit even with nothing else active
+        self.max_active = 0
+        self._waited = set()
         self.cancelled = []          # (request id, True if it was active when withdrawn)
         self._cancel = set()
         self._cancel_lock = threading.Lock()
@@ -171,10 +182,20 @@ class RequestLoop:
                 if not pending and not active:
                     break
             while pending and pending[0].arrival_s <= now and len(active) < self.max_slots:
-                if not self._fits(pending[0].instance):
+                head = pending[0]
+                if self._fits(head.instance):
+                    active.append(self._admit(pending.popleft(), now))
+                    continue
+                if not active:
+                    # Nothing of this loop is running, so no memory will be
+                    # given back: the request can never be admitted.
+                    self.rejected.append(pending.popleft().rid)
+                    continue
+                if head.rid not in self._waited:
+                    self._waited.add(head.rid)
                     self.refused_for_memory += 1
-                    break
-                active.append(self._admit(pending.popleft(), now))
+                break
+            self.max_active = max(self.max_active, len(active))
             if not active:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival_s - now)))
@@ -228,5 +249,7 @@ class RequestLoop:
             "rounds": self.rounds,
             "batches_built": self.batches_built,
             "refused_for_memory": self.refused_for_memory,
+            "rejected_for_memory": len(self.rejected),
+            "max_active": self.max_active,
             "cancelled": len(self.cancelled),
         }

@@ -43,11 +43,18 @@ def test_served_results_equal_solo_runs():
 
 
 def test_admission_respects_free_memory():
-    free, _ = torch.cuda.mem_get_info()
-    reqs = I.request_stream(seed=9, count=6, rate_per_s=1e6, levels=LEVELS, steps=(3, 5))
-    # a reserve just under the free memory admits one small request at a time at most
-    loop = RequestLoop(max_slots=8, chunk=2, reserve_bytes=max(0, free - (64 << 20)))
-    out = loop.run(reqs, max_seconds=60)
+    # Six requests of one shape arrive together; the reserve leaves room for
+    # one request's buffers (plus slack for the library's own tables) but not
+    # for two, so the others must wait for memory, one after the other.
+    f, r = I.TRIANGLE, 15
+    reqs = [I.Request(i, 0.0, I.Instance(f, r, 40 + i), 3 + i % 2) for i in range(6)]
+    need = 2 * f.cells(r) + (1 << 20)
+    loop = RequestLoop(max_slots=8, chunk=2, reserve_bytes=0, keep_results=True)
+    loop.reserve = loop.backend.free_bytes() - need - (16 << 20)
+    out = loop.run(reqs, max_seconds=120)
+    assert out["requests"] == len(reqs) and out["rejected_for_memory"] == 0
+    assert out["max_active"] == 1
+    assert out["refused_for_memory"] == len(reqs) - 1
+    for s in loop.finished[:2]:
+        assert torch.equal(s.cur, alone(s.request.instance, s.request.n_steps)), s.request.rid
     loop.close()
-    assert out["requests"] == len(reqs)
-    assert out["refused_for_memory"] >= 0

@@ -96,7 +96,24 @@ def test_admission_holds_the_memory_reserve():
     assert out["requests"] == len(reqs)
     assert be.max_live <= 3 * 2 * f.cells(r)
     assert max(be.batch_sizes) <= 3
-    assert out["refused_for_memory"] > 0
+    # each waiting request is counted once, however many rounds it waited
+    assert 0 < out["refused_for_memory"] <= len(reqs) - 3
+    assert out["rejected_for_memory"] == 0 and out["max_active"] == 3
+
+
+def test_a_request_that_can_never_fit_is_rejected_and_the_loop_ends():
+    f = I.TRIANGLE
+    small, big = I.Instance(f, 5, 1), I.Instance(f, 9, 2)
+    reqs = [I.Request(0, 0.0, small, 3), I.Request(1, 0.0, big, 3), I.Request(2, 0.0, small, 2)]
+    # room for a small request's buffers, never for the big one's (no max_seconds: the
+    # loop must end by itself)
+    be = FakeBackend(total_bytes=(1 << 20) + 2 * f.cells(5) + 10)
+    loop = RequestLoop(max_slots=4, chunk=4, reserve_bytes=0, backend=be)
+    out = loop.run(reqs)
+    assert loop.rejected == [1]
+    assert out["rejected_for_memory"] == 1 and out["requests"] == 2
+    assert sorted(s.request.rid for s in loop.finished) == [0, 2]
+    assert be.round_lengths == [3, 2] and be.live == 0
 
 
 def test_late_arrivals_join_and_finish():
