@@ -246,9 +246,12 @@ int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_
 
 /* ---- batched steps over many fractals -------------------------------------
  * A batch steps many independent instances (any mix of NBB fractals and
- * levels, each with its own handle, rule and buffer pair) together: one CA
- * step of all of them is a single launch of a persistent kernel whose CTAs
- * walk a cell-balanced schedule of (instance, group range) entries.  The
+ * levels, each with its own handle, rule and buffer pair) together.  The
+ * items are split by the tiled kernel's tile-row instantiation (tile rows of
+ * 27, 25, 64, ... cells); one CA step of all of them is one launch of a
+ * persistent kernel per instantiation, whose CTAs walk a balanced schedule
+ * of (instance, group range) entries (balanced by group slots, since a
+ * group costs about the same whether its 32 tiles are all present).  The
  * paper has no batched form; its step (Sec. 3.2, Sec. 4) is applied to each
  * instance unchanged, so every result equals the instance's own
  * squeeze_step with SQUEEZE_STEP_TILED. */
@@ -269,17 +272,21 @@ typedef struct {
 int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out);
 
 /* squeeze_batch_configure -- launch shape chosen by the autotuner: threads per
- * CTA (multiple of 32, 64..288), CTAs per SM (0 = as many as fit) and whether
- * squeeze_batch_run replays a captured CUDA graph (1) or launches directly. */
+ * CTA (0 = each instantiation's own choice, the one squeeze_step makes; else a
+ * multiple of 32 in 64..384 for every launch), CTAs per SM (0 = as many as
+ * fit) and whether squeeze_batch_run replays a captured CUDA graph (1) or
+ * launches directly.  The default is (0, 0, 1). */
 int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_per_sm,
                             int use_graph);
 
-/* squeeze_batch_info -- the resulting grid, CTA size and shared memory. */
+/* squeeze_batch_info -- the resulting launch shape: the CTAs of one step
+ * (summed over the instantiations' launches), the largest CTA size and the
+ * largest dynamic shared memory of a launch. */
 int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads,
                        uint32_t *smem_bytes);
 
 /* squeeze_batch_run -- n_steps steps of every instance on `stream`, one
- * launch per step; with graphs on, the n_steps launches are captured once
+ * launch per instantiation and step; with graphs on, the launches are captured once
  * (per distinct n_steps and starting buffer) and replayed.  The batch keeps
  * the step count across calls: every instance's state is in d_buf0 after an
  * even total number of steps since squeeze_batch_create and in d_buf1 after
@@ -339,9 +346,15 @@ int squeeze_block_to_compact(const squeeze_handle *h, uint32_t b, const uint8_t 
  * (the Sierpinski triangle above r = 16, for instance) is rejected with
  * UNSUPPORTED and a message in squeeze_last_cuda_error().  The first call on
  * a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.  Every
- * call rewrites the array and clears its status word, so calls that overlap
- * on the GPU (different streams, or threads without ordering) race on it. */
+ * device current); make that first call before any stream capture.  Under
+ * the CUDA runtime's lazy module loading (the default since CUDA 12.2) that
+ * first call is also what loads the code and the array onto the device, so
+ * it takes the array's 4 MiB and the kernels' code memory then, and can fail
+ * with a CUDA error when the device is full: an application that will own
+ * all device memory makes one call (on a small fractal) at start-up, before
+ * it reserves its budget.  Later calls take no device memory.  Every call
+ * rewrites the array and clears its status word, so calls that overlap on
+ * the GPU (different streams, or threads without ordering) race on it. */
 int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r,
                          uint32_t birth, uint32_t survive, const uint8_t *d_in, uint8_t *d_out,
                          int *h_status, void *stream);

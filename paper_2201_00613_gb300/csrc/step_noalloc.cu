@@ -11,7 +11,10 @@
 // callers cannot use squeeze_step().  This entry point runs the same tiled
 // kernel with all of its scratch (neighbour program, halo tables, per-tile
 // adjacency table, status word) placed in one file-scope device array of
-// fixed size, which every GPU that loads the library holds until exit.
+// fixed size, which every GPU that loads the library holds until exit.  With
+// the runtime's lazy module loading, the array (and this library's kernel
+// code) reaches a device on the first call there, when cudaGetSymbolAddress
+// below loads the module: that call takes device memory, later ones do not.
 //
 // Host-side construction of the neighbour program uses fixed-size static host
 // buffers as well, so no heap memory is requested either.

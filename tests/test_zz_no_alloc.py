@@ -60,6 +60,24 @@ def test_noalloc_other_rule_matches():
         assert torch.equal(y, z)
 
 
+def test_noalloc_calls_after_the_first_take_no_device_memory():
+    # The first call on a device loads the library's code and the static
+    # array there (lazy module loading); later calls must not change the
+    # device's free memory.
+    f, r = I.VICSEK, 6
+    n = f.k ** r
+    x = torch.from_numpy(I.bernoulli_bytes(7, n, 0.5)).cuda()
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    assert sq.squeeze_step_noalloc(f.s, f.k, f.offsets, r, B3, S23, x, y) == sq.SQUEEZE_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert sq.squeeze_step_noalloc(f.s, f.k, f.offsets, r, B3, S23, y, z) == sq.SQUEEZE_OK
+    assert sq.squeeze_step_noalloc(f.s, f.k, f.offsets, r, B3, S23, z, y) == sq.SQUEEZE_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_rejects_levels_beyond_its_scratch():
     f, r = I.TRIANGLE, 17
     n = f.k ** r
