@@ -12,6 +12,7 @@
 // temporary name and renamed into place, so a reader sees either the old file
 // or the complete new one.
 #include <errno.h>
+#include <fcntl.h>
 #include <stdio.h>
 #include <string.h>
 #include <unistd.h>
@@ -119,6 +120,9 @@ int squeeze_checkpoint_write(uint32_t s, uint32_t k, const uint8_t *offsets, uin
   bool ok = write_all(fp, &hd, sizeof(hd)) && write_all(fp, off, padded_offsets(k)) &&
             write_all(fp, h_state, f.cells);
   ok = (fflush(fp) == 0) && ok;
+  // The data reach the disk before the rename makes them the checkpoint, so
+  // a crash cannot leave `path` naming a truncated file.
+  ok = (fsync(fileno(fp)) == 0) && ok;
   ok = (fclose(fp) == 0) && ok;
   if (!ok) {
     const int e = errno;
@@ -131,6 +135,18 @@ int squeeze_checkpoint_write(uint32_t s, uint32_t k, const uint8_t *offsets, uin
     remove(tmp);
     errno = e;
     return io_fail("cannot rename to", path);
+  }
+  // Make the rename itself durable: sync the directory that holds the entry.
+  char dir[4096];
+  snprintf(dir, sizeof(dir), "%s", path);
+  char *slash = strrchr(dir, '/');
+  if (!slash) snprintf(dir, sizeof(dir), ".");
+  else if (slash == dir) dir[1] = 0;
+  else *slash = 0;
+  const int dfd = open(dir, O_RDONLY | O_DIRECTORY);
+  if (dfd >= 0) {
+    fsync(dfd);   // best effort: some file systems refuse fsync on a directory
+    close(dfd);
   }
   return SQUEEZE_OK;
 }
