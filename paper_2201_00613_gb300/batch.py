@@ -5,8 +5,9 @@ instance (allocated with torch), seeds every instance's Bernoulli start on
 the device, and steps all of them together through one batch object: one
 persistent launch per CA step, the steps captured in a CUDA graph.
 
-`autotune` picks the tile level per fractal type, the CTA size and the CTAs
-per SM for a given mix by timing candidate batches, and caches the choice in
+`autotune` picks the tile level per fractal type, the CTA size (0: each tile
+instantiation's own) and the CTAs per SM for a given mix by timing candidate
+batches, and caches the choice in
 ``_build/autotune.json`` keyed by the mix, the device name and its SM count.
 """
 from __future__ import annotations
@@ -27,7 +28,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 class MixedBatch:
     """Instances (fractal, r, seed, p) stepped together on one device."""
 
-    def __init__(self, instances, device="cuda", levels=None, threads=288, ctas_per_sm=0,
+    def __init__(self, instances, device="cuda", levels=None, threads=0, ctas_per_sm=0,
                  use_graph=True, init=True):
         self.instances = list(instances)
         self.device = torch.device(device)
@@ -52,7 +53,7 @@ class MixedBatch:
         try:
             self.batch = sq.squeeze_batch_create(
                 [(h.h, a, b) for h, a, b in zip(self.handles, self.buf0, self.buf1)])
-            if threads != 288 or ctas_per_sm or not use_graph:
+            if threads or ctas_per_sm or not use_graph:
                 sq.squeeze_batch_configure(self.batch, threads, ctas_per_sm, use_graph)
         except Exception:
             self.close()
@@ -151,9 +152,9 @@ def autotune(instances, use_cache=True, log=None) -> dict:
         types.setdefault(inst.fractal.name, (inst.fractal, 0))
         f, r = types[inst.fractal.name]
         types[inst.fractal.name] = (f, max(r, inst.r))
-    best = {"levels": {}, "threads": 288, "ctas_per_sm": 0}
+    best = {"levels": {}, "threads": 0, "ctas_per_sm": 0}
     t0 = time.time()
-    best_t = time_config(instances, None, 288, 0)
+    best_t = time_config(instances, None, 0, 0)
     trials = [(dict(best), best_t)]
     for name, (f, max_r) in types.items():
         for L in _level_candidates(f, max_r):
@@ -165,9 +166,9 @@ def autotune(instances, use_cache=True, log=None) -> dict:
             if t < best_t:
                 best_t, best = t, {"levels": levels, "threads": best["threads"],
                                    "ctas_per_sm": best["ctas_per_sm"]}
-    for threads in (192, 256, 288):
+    for threads in (0, 192, 256, 288):    # 0: each instantiation's own CTA size
         for ctas in (0, 2, 3):
-            if (threads, ctas) == (288, 0):   # the shape the level search already timed
+            if (threads, ctas) == (0, 0):   # the shape the level search already timed
                 continue
             t = time_config(instances, best["levels"], threads, ctas)
             trials.append(({"levels": best["levels"], "threads": threads, "ctas_per_sm": ctas}, t))

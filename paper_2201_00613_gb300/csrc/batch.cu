@@ -1,11 +1,17 @@
 // batch.cu -- many fractal instances stepped together.
 //
 // A batch is a fixed list of (handle, buffer pair) items, possibly of
-// different NBB fractals and levels.  One CA step of all items is ONE launch
-// of the persistent batched tiled kernel: its CTAs walk a host-built schedule
-// of (instance, group range) entries, split so that every CTA gets about the
-// same number of cells.  n_steps steps are captured once into a CUDA graph
-// (one launch per step, buffers ping-ponging) and replayed on later calls.
+// different NBB fractals and levels.  The items are split by the tiled
+// kernel's tile-row instantiation (the triangle's 27-wide rows, the Vicsek
+// cross's 25-wide ones, the carpet's 64-wide ones, ...): one CA step of all
+// items is one launch of the persistent batched kernel per instantiation, so
+// every launch runs one specialised code path with its own CTA size and
+// shared memory.  Each launch's CTAs walk a host-built schedule of (instance,
+// group range) entries, cut so that every CTA gets about the same number of
+// group slots (a group costs about the same whether its 32 tile lanes are
+// full or not).  n_steps steps are captured once into a CUDA graph (the
+// launches of one step, then the next step's, buffers ping-ponging) and
+// replayed on later calls.
 #include <stdio.h>
 #include <string.h>
 
@@ -17,18 +23,25 @@
 
 using namespace sq;
 
+// The items of one tile-row instantiation and their launch.
+struct BatchPlan {
+  int kind;                 // 27, 25, 8, 16, 64 or 0 (see sq_tile_kind)
+  bool life;                // every item of the plan runs B3/S23
+  TileLayout lay;           // the maxima of the items' shared-memory needs
+  int threads, grid;
+  BatchWork *d_work;
+  uint32_t *d_sched;
+};
+
 struct squeeze_batch {
   std::vector<squeeze_batch_item> items;
-  TileLayout lay;
-  bool life;
-  int threads, grid, ctas_per_sm;
+  std::vector<BatchPlan> plans;
+  int threads, ctas_per_sm;   // 0: each plan's own CTA size / the occupancy limit
   bool use_graph;
   uint32_t parity;          // 0: states are in buffer 0, 1: in buffer 1
   int device;
   TiledDev *d_devs;
   uint8_t **d_buf0, **d_buf1;
-  BatchWork *d_work;
-  uint32_t *d_sched;
   cudaStream_t capture;     // stream the graphs are captured on
   std::map<uint64_t, cudaGraphExec_t> graphs;  // (n_steps, parity) -> executable graph
 };
@@ -42,22 +55,24 @@ void release_graphs(squeeze_batch *b) {
 
 void release(squeeze_batch *b) {
   release_graphs(b);
+  for (BatchPlan &p : b->plans) {
+    cudaFree(p.d_work);
+    cudaFree(p.d_sched);
+  }
+  b->plans.clear();
   cudaFree(b->d_devs);
   cudaFree(b->d_buf0);
   cudaFree(b->d_buf1);
-  cudaFree(b->d_work);
-  cudaFree(b->d_sched);
   if (b->capture) cudaStreamDestroy(b->capture);
   b->d_devs = nullptr;
   b->d_buf0 = b->d_buf1 = nullptr;
-  b->d_work = nullptr;
-  b->d_sched = nullptr;
   b->capture = nullptr;
 }
 
-// Contiguous group ranges per CTA with about total_cells / grid cells each:
-// group g of instance i starts at cell cum[i] + g * cells_i / groups_i and
-// belongs to the CTA whose cell range holds that start.
+// Contiguous group ranges per CTA with about total / grid units of weight
+// each (cells[i] is instance i's weight, spread evenly over its groups):
+// group g of instance i starts at cum[i] + g * cells_i / groups_i and belongs
+// to the CTA whose range holds that start.
 void build_schedule(const std::vector<uint64_t> &cells, const std::vector<uint64_t> &groups,
                     int grid, std::vector<BatchWork> &work, std::vector<uint32_t> &start) {
   uint64_t total = 0;
@@ -92,63 +107,99 @@ int setup(squeeze_batch *b) {
   release(b);
   const uint32_t count = (uint32_t)b->items.size();
   std::vector<TiledDev> devs(count);
+  std::vector<TileSpec> specs(count);
   std::vector<uint8_t *> buf0(count), buf1(count);
-  std::vector<uint64_t> cells(count), groups(count);
-  b->life = true;
-  bool first = true;
   for (uint32_t i = 0; i < count; ++i) {
     squeeze_handle *h = b->items[i].h;
     int rc = sq_tiled_prepare(h);
     if (rc) return rc;
-    TileSpec sp;
-    rc = sq_tiled_describe(h, &devs[i], &sp);
+    rc = sq_tiled_describe(h, &devs[i], &specs[i]);
     if (rc) return rc;
-    TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
-    b->lay = first ? l : sq_tile_layout_max(b->lay, l);
-    first = false;
-    b->life = b->life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
     buf0[i] = b->items[i].d_buf0;
     buf1[i] = b->items[i].d_buf1;
-    cells[i] = h->f.cells;
-    groups[i] = sp.groups;
   }
-  if (b->lay.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
-  int occ = sq_batch_occupancy(b->life, b->threads, b->lay.smem);
-  if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
-  int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
   int sms = 0;
   SQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-  uint64_t total_groups = 0;
-  for (uint64_t g : groups) total_groups += g;
-  uint64_t grid = (uint64_t)per_sm * sms;
-  b->grid = (int)(grid < total_groups ? grid : total_groups);
-  std::vector<BatchWork> work;
-  std::vector<uint32_t> start;
-  build_schedule(cells, groups, b->grid, work, start);
+  // One plan per instantiation, in order of first appearance.
+  std::vector<int> kinds;
+  for (uint32_t i = 0; i < count; ++i) {
+    const int kind = sq_tile_kind(specs[i]);
+    bool seen = false;
+    for (int k : kinds) seen = seen || k == kind;
+    if (!seen) kinds.push_back(kind);
+  }
+  std::vector<std::vector<BatchWork>> works;
+  std::vector<std::vector<uint32_t>> starts;
+  for (int kind : kinds) {
+    BatchPlan p{};
+    p.kind = kind;
+    p.life = true;
+    bool first = true;
+    int own_threads = 0;
+    std::vector<uint32_t> idx;
+    std::vector<uint64_t> weight, groups;
+    for (uint32_t i = 0; i < count; ++i) {
+      if (sq_tile_kind(specs[i]) != kind) continue;
+      const TileSpec &sp = specs[i];
+      const squeeze_handle *h = b->items[i].h;
+      TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
+      p.lay = first ? l : sq_tile_layout_max(p.lay, l);
+      first = false;
+      p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
+      own_threads = sp.threads > own_threads ? sp.threads : own_threads;
+      idx.push_back(i);
+      // a group costs about the same whatever its fill: weigh it by its slots
+      weight.push_back(sp.groups * 32ull * sp.TW * sp.TH);
+      groups.push_back(sp.groups);
+    }
+    if (p.lay.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
+    p.threads = b->threads ? b->threads : own_threads;
+    const int occ = sq_batch_occupancy(p.life, kind, p.threads, p.lay.smem);
+    if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
+    const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
+    uint64_t total_groups = 0;
+    for (uint64_t g : groups) total_groups += g;
+    const uint64_t grid = (uint64_t)per_sm * sms;
+    p.grid = (int)(grid < total_groups ? grid : total_groups);
+    std::vector<BatchWork> work;
+    std::vector<uint32_t> start;
+    build_schedule(weight, groups, p.grid, work, start);
+    for (BatchWork &w : work) w.instance = idx[w.instance];
+    b->plans.push_back(p);
+    works.push_back(work);
+    starts.push_back(start);
+  }
 
   SQ_CUDA(cudaMalloc(&b->d_devs, sizeof(TiledDev) * count));
   SQ_CUDA(cudaMalloc(&b->d_buf0, sizeof(uint8_t *) * count));
   SQ_CUDA(cudaMalloc(&b->d_buf1, sizeof(uint8_t *) * count));
-  SQ_CUDA(cudaMalloc(&b->d_work, sizeof(BatchWork) * (work.size() ? work.size() : 1)));
-  SQ_CUDA(cudaMalloc(&b->d_sched, sizeof(uint32_t) * start.size()));
   SQ_CUDA(cudaMemcpy(b->d_devs, devs.data(), sizeof(TiledDev) * count, cudaMemcpyHostToDevice));
   SQ_CUDA(cudaMemcpy(b->d_buf0, buf0.data(), sizeof(uint8_t *) * count, cudaMemcpyHostToDevice));
   SQ_CUDA(cudaMemcpy(b->d_buf1, buf1.data(), sizeof(uint8_t *) * count, cudaMemcpyHostToDevice));
-  if (work.size())
-    SQ_CUDA(cudaMemcpy(b->d_work, work.data(), sizeof(BatchWork) * work.size(),
+  for (size_t k = 0; k < b->plans.size(); ++k) {
+    BatchPlan &p = b->plans[k];
+    const std::vector<BatchWork> &work = works[k];
+    const std::vector<uint32_t> &start = starts[k];
+    SQ_CUDA(cudaMalloc(&p.d_work, sizeof(BatchWork) * (work.size() ? work.size() : 1)));
+    SQ_CUDA(cudaMalloc(&p.d_sched, sizeof(uint32_t) * start.size()));
+    if (work.size())
+      SQ_CUDA(cudaMemcpy(p.d_work, work.data(), sizeof(BatchWork) * work.size(),
+                         cudaMemcpyHostToDevice));
+    SQ_CUDA(cudaMemcpy(p.d_sched, start.data(), sizeof(uint32_t) * start.size(),
                        cudaMemcpyHostToDevice));
-  SQ_CUDA(cudaMemcpy(b->d_sched, start.data(), sizeof(uint32_t) * start.size(),
-                     cudaMemcpyHostToDevice));
+  }
   SQ_CUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
   return SQUEEZE_OK;
 }
 
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
   for (uint64_t t = 0; t < n_steps; ++t) {
-    int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, b->d_work, b->d_sched, b->lay,
-                             b->grid, b->threads, b->life, (uint32_t)((b->parity + t) & 1u),
-                             st);
-    if (rc) return rc;
+    const uint32_t parity = (uint32_t)((b->parity + t) & 1u);
+    for (const BatchPlan &p : b->plans) {
+      int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
+                               p.grid, p.threads, p.life, p.kind, parity, st);
+      if (rc) return rc;
+    }
   }
   return SQUEEZE_OK;
 }
@@ -171,7 +222,7 @@ int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeez
   squeeze_batch *b = new (std::nothrow) squeeze_batch();
   if (!b) return SQUEEZE_ERR_OOM;
   b->items.assign(items, items + count);
-  b->threads = 288;
+  b->threads = 0;
   b->ctas_per_sm = 0;
   b->use_graph = true;
   b->parity = 0;
@@ -188,7 +239,8 @@ int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeez
 
 int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_per_sm,
                             int use_graph) {
-  if (!b || threads % 32 || threads < 64 || threads > 288) return SQUEEZE_ERR_INVALID_ARG;
+  if (!b || threads % 32 || (threads && threads < 64) || threads > 384)
+    return SQUEEZE_ERR_INVALID_ARG;
   SQ_CUDA(cudaDeviceSynchronize());
   b->threads = (int)threads;
   b->ctas_per_sm = (int)ctas_per_sm;
@@ -199,9 +251,15 @@ int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_pe
 int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads,
                        uint32_t *smem_bytes) {
   if (!b) return SQUEEZE_ERR_INVALID_ARG;
-  if (grid) *grid = (uint32_t)b->grid;
-  if (threads) *threads = (uint32_t)b->threads;
-  if (smem_bytes) *smem_bytes = b->lay.smem;
+  uint32_t g = 0, t = 0, m = 0;
+  for (const BatchPlan &p : b->plans) {
+    g += (uint32_t)p.grid;
+    t = (uint32_t)p.threads > t ? (uint32_t)p.threads : t;
+    m = p.lay.smem > m ? p.lay.smem : m;
+  }
+  if (grid) *grid = g;
+  if (threads) *threads = t;
+  if (smem_bytes) *smem_bytes = m;
   return SQUEEZE_OK;
 }
 

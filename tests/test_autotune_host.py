@@ -30,7 +30,7 @@ def test_coordinate_search_and_cache(tmp_path, monkeypatch):
     assert "vicsek" not in res["levels"]          # no candidate beat the default there
     assert (res["threads"], res["ctas_per_sm"]) == (256, 3)
     assert res["seconds_per_step"] == 10.0 - 2.0 - 1.5 - 0.5 - 0.25
-    assert res["trials"] == len(calls) == 1 + 9 + 8
+    assert res["trials"] == len(calls) == 1 + 9 + 11
     cached = json.load(open(tmp_path / "autotune.json"))
     assert list(cached.values())[0]["threads"] == 256
     n = len(calls)
