@@ -11,7 +11,8 @@
 namespace sq {
 namespace {
 
-constexpr int kBBRows = 32;     // rows per thread strip
+constexpr int kBBRows = 64;      // rows per thread strip
+constexpr int kBBAhead = 4;      // rows whose loads are in flight ahead of the row computed
 constexpr int kBBThreads = 256;  // 16-byte chunks per block along a row
 
 __global__ void bb_init_kernel(FracDev f, uint8_t *__restrict__ grid, uint64_t seed,
@@ -65,7 +66,12 @@ __device__ __forceinline__ uint32_t bytes_eq(uint32_t cnt, uint32_t c) {
   return (~(x + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
 }
 
+// Next alive bits (0x01 per byte) of 4 cells with neighbour counts cnt and
+// alive bits `alive`.  kLife: B3/S23 is "count | alive == 3" (a count of 3,
+// or 2 with the cell alive); otherwise the masks are evaluated count by count.
+template <bool kLife>
 __device__ __forceinline__ uint32_t swar_rule(Rule rule, uint32_t cnt, uint32_t alive) {
+  if (kLife) return bytes_eq(cnt | alive, 3u);
   uint32_t next = 0;
   uint32_t any = rule.birth | rule.survive;
 #pragma unroll
@@ -97,56 +103,83 @@ __device__ __forceinline__ void make_row(const uint4 &v, uint32_t left, uint32_t
   }
 }
 
-// Load one 16-byte chunk of row y (zeros off the box) and its two edge bytes.
-__device__ __forceinline__ void load_row(const uint8_t *__restrict__ in, uint32_t n, int64_t y,
-                                         uint32_t chunk, uint32_t nchunks, Row16 &o) {
-  uint4 v = make_uint4(0, 0, 0, 0);
-  bool in_box = y >= 0 && y < (int64_t)n;
-  bool live = chunk < nchunks;
+// One row's 16-byte chunk as loaded (zeros off the box) and, for the warp's
+// edge lanes, the byte just outside the warp's 512 bytes on that side.
+struct RowLoad {
+  uint4 v;
+  uint32_t edge;
+};
+
+__device__ __forceinline__ RowLoad load_row(const uint8_t *__restrict__ in, uint32_t n, int64_t y,
+                                            uint32_t chunk, uint32_t nchunks) {
+  RowLoad o;
+  o.v = make_uint4(0, 0, 0, 0);
+  o.edge = 0;
+  const bool in_box = y >= 0 && y < (int64_t)n;
   const uint8_t *row = in + (uint64_t)(in_box ? y : 0) * n;
-  if (in_box && live) v = __ldg(reinterpret_cast<const uint4 *>(row) + chunk);
-  unsigned lane = threadIdx.x & 31u;
-  uint32_t left = __shfl_up_sync(0xFFFFFFFFu, v.w >> 24, 1);
-  uint32_t right = __shfl_down_sync(0xFFFFFFFFu, v.x, 1) & 0xFFu;
-  if (lane == 0) left = (in_box && live && chunk > 0) ? row[chunk * 16 - 1] : 0u;
-  if (lane == 31) right = (in_box && chunk + 1 < nchunks) ? row[chunk * 16 + 16] : 0u;
-  make_row(v, left, right, o);
+  if (in_box && chunk < nchunks) o.v = __ldg(reinterpret_cast<const uint4 *>(row) + chunk);
+  const unsigned lane = threadIdx.x & 31u;
+  if (in_box && lane == 0 && chunk > 0 && chunk < nchunks) o.edge = __ldg(row + chunk * 16 - 1);
+  if (in_box && lane == 31 && chunk + 1 < nchunks) o.edge = __ldg(row + chunk * 16 + 16);
+  return o;
+}
+
+// Horizontal sums of a loaded row: the bytes left and right of the chunk come
+// from the neighbouring lanes (the warp's edge lanes loaded theirs).
+__device__ __forceinline__ void row_sums(const RowLoad &l, Row16 &o) {
+  const unsigned lane = threadIdx.x & 31u;
+  uint32_t left = __shfl_up_sync(0xFFFFFFFFu, l.v.w >> 24, 1);
+  uint32_t right = __shfl_down_sync(0xFFFFFFFFu, l.v.x, 1) & 0xFFu;
+  if (lane == 0) left = l.edge;
+  if (lane == 31) right = l.edge;
+  make_row(l.v, left, right, o);
 }
 
 // SWAR step; requires n % 16 == 0.  Block: kBBThreads consecutive chunks of a
-// row; grid.y: strips of kBBRows rows.
+// row; grid.y: strips of kBBRows rows.  The loads of the next kBBAhead rows
+// are in flight while a row is computed (the rows are kept in a register
+// queue indexed at compile time), so each thread keeps several 16-byte loads
+// outstanding; every row is read (kBBRows + 2) / kBBRows times (3 % more than once).
+template <bool kLife>
 __global__ void __launch_bounds__(kBBThreads) bb_step_swar(uint32_t n, Rule rule,
                                                            const uint8_t *__restrict__ in,
                                                            uint8_t *__restrict__ out) {
-  uint32_t nchunks = n / 16;
-  uint32_t chunk = blockIdx.x * kBBThreads + threadIdx.x;
-  int64_t y0 = (int64_t)blockIdx.y * kBBRows;
-  Row16 up, cur, dn;
-  load_row(in, n, y0 - 1, chunk, nchunks, up);
-  load_row(in, n, y0, chunk, nchunks, cur);
-  uint4 vcur = make_uint4(0, 0, 0, 0);
-  if (chunk < nchunks && y0 < n) vcur = __ldg(reinterpret_cast<const uint4 *>(in + (uint64_t)y0 * n) + chunk);
-  for (int i = 0; i < kBBRows; ++i) {
-    int64_t y = y0 + i;
-    if (y >= n) break;  // uniform across the block
-    load_row(in, n, y + 1, chunk, nchunks, dn);
-    uint4 vnext = make_uint4(0, 0, 0, 0);
-    if (chunk < nchunks && y + 1 < n)
-      vnext = __ldg(reinterpret_cast<const uint4 *>(in + (uint64_t)(y + 1) * n) + chunk);
-    if (chunk < nchunks) {
-      uint32_t w[4] = {vcur.x, vcur.y, vcur.z, vcur.w};
-      uint32_t o[4];
+  const uint32_t nchunks = n / 16;
+  const uint32_t chunk = blockIdx.x * kBBThreads + threadIdx.x;
+  const int64_t y0 = (int64_t)blockIdx.y * kBBRows;
+  Row16 up, cur;
+  row_sums(load_row(in, n, y0 - 1, chunk, nchunks), up);
+  const RowLoad l0 = load_row(in, n, y0, chunk, nchunks);
+  row_sums(l0, cur);
+  uint4 vcur = l0.v;
+  RowLoad q[kBBAhead];   // q[k] holds row y + 1 + k at the top of step k of a round
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t cnt = up.h[j] + dn.h[j] + cur.h[j] - cur.a[j];
-        uint32_t next = swar_rule(rule, cnt, cur.a[j]);
-        o[j] = (w[j] & 0x02020202u) | (next & (w[j] >> 1) & 0x01010101u);
+  for (int k = 0; k < kBBAhead; ++k) q[k] = load_row(in, n, y0 + 1 + k, chunk, nchunks);
+  for (int i0 = 0; i0 < kBBRows; i0 += kBBAhead) {
+#pragma unroll
+    for (int k = 0; k < kBBAhead; ++k) {
+      const int64_t y = y0 + i0 + k;
+      if (y >= n) break;  // uniform across the block
+      Row16 dn;
+      row_sums(q[k], dn);
+      const uint4 vnext = q[k].v;
+      // (rows past the strip's last neighbour row are not needed: not loaded)
+      if (i0 + k + 1 + kBBAhead <= kBBRows) q[k] = load_row(in, n, y + 1 + kBBAhead, chunk, nchunks);
+      if (chunk < nchunks) {
+        const uint32_t w[4] = {vcur.x, vcur.y, vcur.z, vcur.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t cnt = up.h[j] + dn.h[j] + cur.h[j] - cur.a[j];
+          const uint32_t next = swar_rule<kLife>(rule, cnt, cur.a[j]);
+          o[j] = (w[j] & 0x02020202u) | (next & (w[j] >> 1) & 0x01010101u);
+        }
+        reinterpret_cast<uint4 *>(out + (uint64_t)y * n)[chunk] = make_uint4(o[0], o[1], o[2], o[3]);
       }
-      reinterpret_cast<uint4 *>(out + (uint64_t)y * n)[chunk] = make_uint4(o[0], o[1], o[2], o[3]);
+      up = cur;
+      cur = dn;
+      vcur = vnext;
     }
-    up = cur;
-    cur = dn;
-    vcur = vnext;
   }
 }
 
@@ -218,7 +251,9 @@ int sq_launch_bb_step(const squeeze_handle *h, const uint8_t *in, uint8_t *out, 
       ((uintptr_t)out % 16 == 0)) {
     uint32_t nchunks = n / 16;
     dim3 grid((nchunks + kBBThreads - 1) / kBBThreads, (n + kBBRows - 1) / kBBRows);
-    bb_step_swar<<<grid, kBBThreads, 0, st>>>(n, h->rule, in, out);
+    const bool life = h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
+    if (life) bb_step_swar<true><<<grid, kBBThreads, 0, st>>>(n, h->rule, in, out);
+    else bb_step_swar<false><<<grid, kBBThreads, 0, st>>>(n, h->rule, in, out);
   } else {
     uint64_t total = (uint64_t)n * n;
     bb_step_simple<<<grid_for(total, 256), 256, 0, st>>>(n, h->rule, h->f.nbhd, in, out);
