@@ -53,6 +53,11 @@ extern "C" {
 #define SQUEEZE_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait gave up     */
 #define SQUEEZE_ERR_DEVICE_BOUNDS (-6) /* a device-side bounds check fired        */
 #define SQUEEZE_ERR_IO (-7)            /* a file could not be read or written, or is damaged */
+#define SQUEEZE_ERR_DEVICE_UNSAFE (-8) /* a timed-out bulk copy never landed: later launches on
+                                          this context may see it land in their shared memory */
+
+/* ---- fault injection (tests of the error paths) --------------------------- */
+#define SQUEEZE_FAULT_WITHHOLD_LOADS 1u  /* tiled kernel issues no bulk loads: its waits run out */
 
 /* ---- step kernels --------------------------------------------------------- */
 #define SQUEEZE_STEP_AUTO 0    /* tiled kernel when the level allows, else per-cell ALU */
@@ -153,9 +158,23 @@ int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t s
  * misaligned buffer is INVALID_ARG, and AUTO then takes the per-cell ALU
  * kernel.  A level whose tiled program would not fit is UNSUPPORTED for
  * TILED (AUTO falls back to the per-cell ALU kernel only when no tile level
- * fits at all). */
+ * fits at all).  squeeze_last_step_info() tells which kernel AUTO chose.
+ * The tiled kernel advances two steps per launch where its program allows
+ * (the state of the intermediate step stays in shared memory), so d_buf1
+ * holds no particular step afterwards; the result is the same bit for bit. */
 int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                  int kind, void *stream);
+
+/* squeeze_last_step_info -- what the handle's last accepted squeeze_step
+ * call ran: *kind = SQUEEZE_STEP_TILED, SQUEEZE_MAP_ALU or SQUEEZE_MAP_TC_BF16
+ * (0 before the first step), so that a caller of AUTO can see a fall-back to
+ * the per-cell ALU kernel (misaligned buffers; about 300x slower than the
+ * tiled kernel); *launches = kernel launches it enqueued; *two_step = how
+ * many of them advanced two steps (the tiled kernel runs n steps as two-step
+ * launches where it can: n = 100 is 50 launches).  Any pointer may be NULL.
+ * INVALID_ARG for a null handle. */
+int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
+                           uint64_t *two_step);
 
 /* squeeze_step_host -- the same run from and to HOST memory: copies h_in
  * (k^r bytes, ideally pinned) into d_buf0, runs n_steps, copies the result to
@@ -473,9 +492,32 @@ int squeeze_3d_device_status(squeeze_3d_handle *h, int *status);
 /* ---- diagnostics ---------------------------------------------------------- */
 
 /* squeeze_device_status -- synchronise the device, then read and clear the
- * handle's device status word: *status = SQUEEZE_OK, DEVICE_BOUNDS or
- * DEVICE_TIMEOUT.  Returns CUDA if the synchronisation itself failed. */
+ * handle's device status word: *status = SQUEEZE_OK, DEVICE_BOUNDS,
+ * DEVICE_TIMEOUT or DEVICE_UNSAFE.  DEVICE_TIMEOUT: a wait of the tiled
+ * kernel on its bulk copies gave up; that CTA stopped loading, the launch's
+ * output is not valid, and the copy it waited for was accounted for before
+ * the kernel ended, so later launches are safe.  DEVICE_UNSAFE: the copy a
+ * CTA gave up on had still not landed after a second wait of the same limit;
+ * it may still write into shared memory that a later launch owns, so the
+ * context should be discarded.  Returns CUDA if the synchronisation itself
+ * failed. */
 int squeeze_device_status(squeeze_handle *h, int *status);
+
+/* squeeze_set_wait_limit -- how long a device-side wait of this handle's
+ * tiled and batched steps spins before it gives up with DEVICE_TIMEOUT:
+ * ns in [1000, 10^10] nanoseconds of %globaltimer, or 0 for the default of
+ * 2 s.  INVALID_ARG otherwise.  A batch reads the limit of each item's handle
+ * when it is created. */
+int squeeze_set_wait_limit(squeeze_handle *h, uint64_t ns);
+
+/* squeeze_set_fault_injection -- test hook for the device error paths:
+ * flags = 0 (off) or SQUEEZE_FAULT_WITHHOLD_LOADS, under which the tiled step
+ * issues none of its bulk loads, so that its first wait runs out after the
+ * wait limit, every CTA abandons its work, and the launch ends with
+ * DEVICE_TIMEOUT in the status word (nothing is left in flight: no copy was
+ * issued).  The output buffer then holds garbage in place of the step's
+ * result.  INVALID_ARG for unknown flags. */
+int squeeze_set_fault_injection(squeeze_handle *h, uint32_t flags);
 
 /* squeeze_status_string -- static text for a status code. */
 const char *squeeze_status_string(int status);

@@ -21,6 +21,9 @@ SQUEEZE_ERR_CUDA = -4
 SQUEEZE_ERR_DEVICE_TIMEOUT = -5
 SQUEEZE_ERR_DEVICE_BOUNDS = -6
 SQUEEZE_ERR_IO = -7
+SQUEEZE_ERR_DEVICE_UNSAFE = -8
+
+SQUEEZE_FAULT_WITHHOLD_LOADS = 1
 
 SQUEEZE_STEP_AUTO = 0
 SQUEEZE_STEP_TILED = 1
@@ -122,6 +125,11 @@ _SIGS = {
                          ctypes.c_void_p], ctypes.c_int),
     "squeeze_3d_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "squeeze_set_wait_limit": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "squeeze_set_fault_injection": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_last_step_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+                               ctypes.c_int),
     "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "squeeze_last_cuda_error": ([], ctypes.c_char_p),
 }
@@ -436,6 +444,22 @@ def squeeze_device_status(h) -> int:
     v = ctypes.c_int()
     _check(_load().squeeze_device_status(h, ctypes.byref(v)), "squeeze_device_status")
     return int(v.value)
+
+
+def squeeze_set_wait_limit(h, ns: int) -> None:
+    _check(_load().squeeze_set_wait_limit(h, ns), "squeeze_set_wait_limit")
+
+
+def squeeze_set_fault_injection(h, flags: int) -> None:
+    _check(_load().squeeze_set_fault_injection(h, flags), "squeeze_set_fault_injection")
+
+
+def squeeze_last_step_info(h) -> tuple:
+    """(kind, launches, two-step launches) of the handle's last squeeze_step."""
+    kind, launches, two = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_load().squeeze_last_step_info(h, ctypes.byref(kind), ctypes.byref(launches),
+                                          ctypes.byref(two)), "squeeze_last_step_info")
+    return int(kind.value), int(launches.value), int(two.value)
 
 
 def squeeze_status_string(code: int) -> str:

@@ -85,6 +85,8 @@ const char *squeeze_status_string(int status) {
     case SQUEEZE_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case SQUEEZE_ERR_DEVICE_BOUNDS: return "device-side bounds check failed";
     case SQUEEZE_ERR_IO: return "file could not be read or written, or is damaged";
+    case SQUEEZE_ERR_DEVICE_UNSAFE:
+      return "a timed-out bulk copy never landed; later launches on this context are unsafe";
     default: return "unknown status";
   }
 }
@@ -226,11 +228,26 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     int rc = sq_tiled_prepare(h);
     if (rc) return rc;
   }
+  h->last_kind = kind;
+  // The tiled kernel runs two steps per launch where its program allows:
+  // n = 2p + s steps as p two-step launches and s one-step ones, except that
+  // the launch count must have the parity of n (every launch swaps the
+  // buffers, and the result belongs in d_buf[n & 1]), so an odd p gives one
+  // of its two-step launches up for two one-step launches.
+  uint64_t doubles = 0, singles = n_steps;
+  if (kind == SQUEEZE_STEP_TILED && sq_tiled_two_step(h)) {
+    doubles = n_steps / 2;
+    singles = n_steps % 2;
+    if (doubles & 1u) {
+      doubles -= 1;
+      singles += 2;
+    }
+  }
   uint8_t *a = d_buf0, *b = d_buf1;
-  for (uint64_t t = 0; t < n_steps; ++t) {
+  for (uint64_t t = 0; t < doubles + singles; ++t) {
     int rc;
     switch (kind) {
-      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, st); break;
+      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, t < doubles ? 2u : 1u, st); break;
       case SQUEEZE_MAP_TC_BF16: rc = sq_launch_step_tc(h, a, b, st); break;
       default: rc = sq_launch_step_alu(h, a, b, st); break;
     }
@@ -239,6 +256,8 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     a = b;
     b = tmp;
   }
+  h->last_launches = doubles + singles;
+  h->last_two_step = doubles;
   return SQUEEZE_OK;
 }
 
@@ -318,6 +337,28 @@ int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_
                           void *stream) {
   if (check_handle(h) || !d_grid || !d_state) return SQUEEZE_ERR_INVALID_ARG;
   return sq_launch_bb_gather(h, d_grid, d_state, (cudaStream_t)stream);
+}
+
+int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
+                           uint64_t *two_step_launches) {
+  if (check_handle(h)) return SQUEEZE_ERR_INVALID_ARG;
+  if (kind) *kind = h->last_kind;
+  if (launches) *launches = h->last_launches;
+  if (two_step_launches) *two_step_launches = h->last_two_step;
+  return SQUEEZE_OK;
+}
+
+int squeeze_set_wait_limit(squeeze_handle *h, uint64_t ns) {
+  if (check_handle(h) || (ns && (ns < 1000ull || ns > 10000000000ull)))
+    return SQUEEZE_ERR_INVALID_ARG;
+  h->wait_ns = ns;
+  return SQUEEZE_OK;
+}
+
+int squeeze_set_fault_injection(squeeze_handle *h, uint32_t flags) {
+  if (check_handle(h) || (flags & ~SQUEEZE_FAULT_WITHHOLD_LOADS)) return SQUEEZE_ERR_INVALID_ARG;
+  h->fault = flags;
+  return SQUEEZE_OK;
 }
 
 int squeeze_device_status(squeeze_handle *h, int *status) {

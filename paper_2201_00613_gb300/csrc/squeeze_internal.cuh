@@ -211,13 +211,21 @@ struct TiledDev {
   const uint8_t *halo_dir;   // nhalo direction indices
   const uint32_t *adj;       // ndirs x tiles adjacent tile indices (~0: none)
   int *status;
+  uint32_t nhalo1;           // first-ring halo words (the rest, if any, are the second ring)
+  uint32_t halo2_start[10];  // second-ring words of direction j: [halo2_start[j], halo2_start[j+1])
+  uint64_t wait_ns;          // a bulk-copy wait gives up after this many ns
+  uint32_t fault;            // SQUEEZE_FAULT_* (test hook), normally 0
+  uint32_t pad_;
 };
+
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 
 // Shared-memory layout of one launch of the tiled kernel (uniform over the
 // instances of a batched launch: the maxima of their needs).
 struct TileLayout {
   uint32_t win_bytes;        // one word buffer (two are used)
   uint32_t hoff_bytes;       // halo offsets
+  uint32_t hdir_bytes;       // halo direction indices (one byte per halo word)
   uint32_t rowa_bytes;       // per-row alignment offsets (two sets)
   uint32_t carry_bytes;      // per-row 16-byte chunk handed to the next group
   uint32_t stage_bytes;      // one staging buffer (two are used)
@@ -228,13 +236,17 @@ struct TileLayout {
 // tables live.
 struct TileSpec {
   uint32_t L, TW, TH, rpw, cells, slots, nhalo, ndirs, dir_mask;
+  uint32_t nhalo1;     // halo words the one-step program reads (the first ring)
+  uint32_t two_step;   // 1: the program also runs two steps per launch (second ring built)
   uint8_t dir_list[9];
-  uint32_t halo_start[10];
+  uint32_t halo_start[10];   // first-ring words of direction j: [halo_start[j], halo_start[j+1])
+  uint32_t halo2_start[10];  // second-ring words of direction j (indices >= nhalo1)
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
   size_t smem;
-  int grid, threads;   // grid of the B3/S23 instantiation
+  int grid, threads;   // grid of the B3/S23 instantiation (one step per launch)
   int grid_rule;       // grid of the generic-rule instantiation
+  int grid2, grid2_rule;   // the same for the two-step instantiations
 };
 
 // Capacities needed to build the program of one tile level.
@@ -254,6 +266,10 @@ struct TileBuild {
   uint32_t *halo_off;
   uint8_t *halo_dir;
   uint64_t box_cap, cells_cap, slots_cap, halo_cap;
+  // 1: also build the second halo ring and the first ring's references, so
+  // that the program runs two steps per launch (refs and refs16 then need
+  // (slots + halo_cap) * 8 entries).
+  uint32_t two_step;
 };
 
 // One entry of a batched launch's schedule: CTA c processes entries
@@ -285,6 +301,11 @@ struct squeeze_handle {
   int device;                // CUDA device the tables live on
   uint32_t tiled_level;      // 0 = not chosen yet
   TiledProgram *tiled;       // lazily built neighbour program of the tiled kernel
+  uint64_t wait_ns;          // device wait limit of the tiled kernels (0: default)
+  uint32_t fault;            // fault-injection flags (tests only)
+  int last_kind;             // kind the last squeeze_step ran (0 before the first)
+  uint64_t last_launches;    // kernel launches of that call
+  uint64_t last_two_step;    // of which two steps per launch
 };
 
 // Error plumbing and descriptor validation (handle.cu).
@@ -307,8 +328,11 @@ int sq_launch_init(const squeeze_handle *h, uint8_t *state, uint64_t seed, uint3
 int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                        cudaStream_t st);
 int sq_tiled_prepare(squeeze_handle *h);
+// One launch of the handle's tiled program: steps = 1, or 2 when the
+// program was built for two steps per launch (sq_tiled_two_step).
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
-                         cudaStream_t st);
+                         uint32_t steps, cudaStream_t st);
+bool sq_tiled_two_step(const squeeze_handle *h);
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
 int sq_tiled_default_level_for(const sq::FracDev &f);
@@ -323,15 +347,19 @@ sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint3
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
 int sq_tile_build_adjacency(const sq::FracDev &f, const sq::TiledDev &d, uint32_t *adj,
                             cudaStream_t st);
+// One launch of the tiled kernel: steps = 1, or 2 (program built with two_step).
 int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t *in,
-                   uint8_t *out, cudaStream_t st);
+                   uint8_t *out, uint32_t steps, cudaStream_t st);
 // The handle's prepared tiled program (sq_tiled_prepare first).
 int sq_tiled_describe(const squeeze_handle *h, sq::TiledDev *d, sq::TileSpec *sp);
+// Tile-row instantiation of a program: 8 or 16 (rows sharing a slot word),
+// 27, 25 or 64 (their own instantiations), 0 (width taken at run time).
+int sq_tile_kind(const sq::TileSpec &sp);
 // CTAs per SM of the batched kernel instance for this shape (0 if it cannot run).
-int sq_batch_occupancy(bool life, int threads, uint32_t smem);
+int sq_batch_occupancy(bool life, int kind, int threads, uint32_t smem);
 int sq_batch_launch(const sq::TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const sq::BatchWork *d_work, const uint32_t *d_sched,
-                    const sq::TileLayout &lay, int grid, int threads, bool life,
+                    const sq::TileLayout &lay, int grid, int threads, bool life, int kind,
                     uint32_t parity, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);

@@ -137,7 +137,7 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
   Rule rule{birth, survive};
   TiledDev d = sq_tiled_dev(f, rule, sp, d_refs, d_hoff, d_hdir, d_adj, d_status);
   rc = sq_tile_build_adjacency(f, d, d_adj, st);
-  if (rc == SQUEEZE_OK) rc = sq_tile_launch(d, sp, d_in, d_out, st);
+  if (rc == SQUEEZE_OK) rc = sq_tile_launch(d, sp, d_in, d_out, 1, st);
   if (rc) return rc;
   if (h_status) {
     SQ_CUDA(cudaStreamSynchronize(st));

@@ -152,38 +152,47 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 // Abort record of the CTA: set by the first wait that gives up, with the
-// shared-memory address of the barrier and the phase it gave up on.
+// shared-memory address of the barrier and the phase it gave up on, the wait
+// limit, the status word to report to, and whether any copy was issued at
+// all (not under the load-withholding test hook).
 struct AbortRecord {
   uint32_t bar;
   uint32_t parity;
   uint32_t set;
+  uint32_t nocopy;
+  uint64_t limit;
+  int *status;
 };
 __shared__ AbortRecord g_abort;
 
-// Wait for an mbarrier phase, giving up after ~2 s with DEVICE_TIMEOUT.  A
-// wait that gives up records it in g_abort; every later wait of the CTA that
-// does not complete at once returns as soon as it sees the record, and no
-// more loads are issued, so a copy that never lands costs the launch about
-// 2 s instead of 2 s per group.  Control flow is unchanged (every thread still
-// reaches every barrier); the results of an aborted launch are not valid,
-// which the status word says.
-__device__ __noinline__ void mbar_wait_slow(uint32_t addr, uint32_t parity, int *status) {
+// Wait for an mbarrier phase, giving up after `limit` ns (2 s unless the
+// handle sets another) with DEVICE_TIMEOUT.  A wait that gives up records it
+// in g_abort; every later wait of the CTA that does not complete at once
+// returns as soon as it sees the record, and no more loads are issued, so a
+// copy that never lands costs the launch one limit instead of one per group.
+// Control flow is unchanged (every thread still reaches every barrier); the
+// results of an aborted launch are not valid, which the status word says.
+__device__ __noinline__ void mbar_wait_slow(uint32_t addr, uint32_t parity, int *status,
+                                            uint64_t limit, uint32_t fault) {
   volatile AbortRecord *ab = &g_abort;
   uint64_t t0 = global_ns();
   while (!mbar_try_wait_at(addr, parity)) {
     if (ab->set) return;
-    if (global_ns() - t0 > 2000000000ull) {
+    if (global_ns() - t0 > limit) {
       flag(status, SQUEEZE_ERR_DEVICE_TIMEOUT);
       ab->bar = addr;
       ab->parity = parity;
+      ab->limit = limit;
+      ab->status = status;
+      ab->nocopy = (fault & SQUEEZE_FAULT_WITHHOLD_LOADS) ? 1u : 0u;
       ab->set = 1u;
       return;
     }
   }
 }
-__device__ __forceinline__ void mbar_wait(uint64_t *m, uint32_t parity, int *status) {
+__device__ __forceinline__ void mbar_wait(uint64_t *m, uint32_t parity, const TiledDev &p) {
   const uint32_t addr = smem_u32(m);
-  if (!mbar_try_wait_at(addr, parity)) mbar_wait_slow(addr, parity, status);
+  if (!mbar_try_wait_at(addr, parity)) mbar_wait_slow(addr, parity, p.status, p.wait_ns, p.fault);
 }
 
 // True once a wait of this CTA has given up (read after a CTA barrier, so
@@ -193,12 +202,17 @@ __device__ __forceinline__ bool cta_aborted() {
 }
 
 // At the end of an aborted launch the copy that timed out may still land in
-// shared memory: give it one more bounded wait before the CTA exits.
+// shared memory: give it one more bounded wait before the CTA exits.  If it
+// still has not landed, it may land in a later CTA's shared memory: the
+// status becomes DEVICE_UNSAFE.  (Under the load-withholding hook nothing was
+// issued, so there is nothing to wait for.)
 __device__ __forceinline__ void settle_abort() {
-  if (threadIdx.x == 0 && cta_aborted()) {
+  if (threadIdx.x == 0 && cta_aborted() && !g_abort.nocopy) {
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait_at(g_abort.bar, g_abort.parity) && global_ns() - t0 < 2000000000ull) {
-    }
+    bool landed = mbar_try_wait_at(g_abort.bar, g_abort.parity);
+    while (!landed && global_ns() - t0 < g_abort.limit)
+      landed = mbar_try_wait_at(g_abort.bar, g_abort.parity);
+    if (!landed) atomicExch(g_abort.status, SQUEEZE_ERR_DEVICE_UNSAFE);
   }
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
@@ -356,8 +370,7 @@ __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint
       const uint32_t word = __ballot_sync(0xFFFFFFFFu, alive);
       if (lane == 0) words[h] = word;
     }
-    return;
-  }
+  } else {
   for (uint32_t h = h0; h < h1; h += kBatch) {
     uint32_t v[kBatch];
 #pragma unroll
@@ -376,6 +389,7 @@ __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint
         if (lane == 0) words[h + i] = word;
       }
     }
+  }
   }
 }
 
@@ -507,11 +521,13 @@ __device__ __forceinline__ void unpack_row(uint32_t *stage32w, uint8_t *stage, u
 }
 
 // Shared-memory carve-up of the tiled kernel (offsets in bytes; every region
-// starts at a multiple of 16): two word buffers, halo offsets, 2 mbarriers,
-// two sets of row offsets, the row-end carry chunks, two staging buffers.
+// starts at a multiple of 16): two word buffers, halo offsets, halo
+// directions, 2 mbarriers, two sets of row offsets, the row-end carry chunks,
+// two staging buffers.
 struct SmemPtrs {
   unsigned char *win0;
   uint32_t *hoff;
+  uint8_t *hdir;
   uint64_t *mbar;
   uint8_t *rowa;
   uint8_t *carry;
@@ -525,6 +541,8 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
   off += 2 * (size_t)lay.win_bytes;
   q.hoff = reinterpret_cast<uint32_t *>(smem + off);
   off += lay.hoff_bytes;
+  q.hdir = smem + off;
+  off += lay.hdir_bytes;
   q.mbar = reinterpret_cast<uint64_t *>(smem + off);
   off += 16;
   q.rowa = smem + off;
@@ -533,6 +551,22 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
   off += lay.carry_bytes;
   q.stage0 = smem + off;
   return q;
+}
+
+// The rule applied to word c of a word array: its 8 neighbour words by the
+// program's byte offsets (one 16-byte table load), the word itself as "alive".
+template <bool kLife>
+__device__ __forceinline__ uint32_t rule_at(const TiledDev &p, const unsigned char *wbase,
+                                            uint32_t c) {
+  const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(p.refs) + c);
+  const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
+  uint32_t n[8];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    n[2 * d] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4410));
+    n[2 * d + 1] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4432));
+  }
+  return rule_word<kLife>(p.rule, reinterpret_cast<const uint32_t *>(wbase)[c], n);
 }
 
 // One pass of the tiled step over groups g_first, g_first + g_stride, ...
@@ -554,7 +588,17 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
 // i % 2, the bulk loads of group i + 1 land in the other one.  `it` counts
 // the groups this CTA has processed (it selects buffers and mbarrier phases)
 // and carries over from one call to the next.
-template <bool kLife, int kTW>
+//
+// kT = 2 (two steps per launch): the packed words of a group go to word
+// buffer X (buffer 0), together with both halo rings and the per-direction
+// masks of which adjacent tiles exist; after the barrier a first rule pass
+// writes step 1 of every slot and of the first halo ring to buffer Y (a
+// first-ring cell of a missing tile stays dead), and after a second barrier
+// the usual rule pass computes step 2 from Y and writes it back.  X is free
+// again once every warp has passed the second barrier, and Y once every warp
+// has passed the next group's first barrier, so the two buffers need no
+// double-buffering by group.
+template <bool kLife, int kTW, int kT>
 __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &lay,
                                            const uint8_t *__restrict__ in,
                                            uint8_t *__restrict__ out, uint64_t g_first,
@@ -579,6 +623,7 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   const SmemPtrs q = carve(smem, lay);
   const size_t win_bytes = lay.win_bytes, stage_bytes = lay.stage_bytes;
   uint32_t *hoff = q.hoff;
+  uint8_t *hdir = q.hdir;
   uint64_t *mbar = q.mbar;
   uint8_t *rowa = q.rowa;
   uint8_t *carry = q.carry;
@@ -591,7 +636,12 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     return kWPR * (u0 + ((uint32_t)k / kWPR) * nw) + (uint32_t)k % kWPR;
   };
   __syncthreads();  // the previous call (another instance) is done with every buffer
+  // A CTA that gave up on an earlier instance of a batch loads nothing more:
+  // this instance's output is not valid either, so its status says so.
+  if (tid == 0 && cta_aborted()) flag(p.status, SQUEEZE_ERR_DEVICE_TIMEOUT);
   for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
+  if constexpr (kT == 2)
+    for (uint32_t i = tid; i < p.nhalo1; i += nthreads) hdir[i] = p.halo_dir[i];
   if (tid == 0) {
     reinterpret_cast<uint32_t *>(smem)[slots + nhalo] = 0u;  // "no neighbour" words
     reinterpret_cast<uint32_t *>(smem + win_bytes)[slots + nhalo] = 0u;
@@ -600,7 +650,8 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   const uint64_t total = p.total, W = p.W;
   const uint32_t valid = p.valid;
 
-  if (warp == 0 && g_first < g_end && !cta_aborted())
+  const bool withhold = (p.fault & SQUEEZE_FAULT_WITHHOLD_LOADS) != 0u;  // test hook
+  if (warp == 0 && g_first < g_end && !cta_aborted() && !withhold)
     issue_group_loads(p, group_at(p, TW, g_first), in, stage_base + (it & 1u) * stage_bytes,
                       &mbar[it & 1u], lane);
   // Adjacent tile of this lane's tile in direction j = warp, for the group at hand.
@@ -610,8 +661,11 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 
   for (uint64_t g = g_first; g < g_end; g += g_stride, ++it) {
     const uint32_t b = it & 1u;
-    unsigned char *wbase = smem + b * win_bytes;
+    // Word buffer of the packed input: by group parity for one step per
+    // launch; buffer 0 (X) for two.
+    unsigned char *wbase = smem + (kT == 2 ? 0u : b) * win_bytes;
     uint32_t *win = reinterpret_cast<uint32_t *>(wbase);
+    uint32_t *emask = win + slots + nhalo + 1;   // kT = 2: which adjacent tiles exist, per direction
     uint8_t *stage = stage_base + b * stage_bytes;
     const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
     uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
@@ -651,12 +705,26 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         }
       }
       if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
+      if constexpr (kT == 2) {
+        gather_halo<kHaloBatch>(p, TW, t_cur, p.halo2_start[warp], p.halo2_start[warp + 1], hoff,
+                                win + slots, in, lane);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, t_cur != ~0u);
+        if (lane == 0) emask[warp] = m;
+      }
     }
-    for (uint32_t j = warp + nw; j < p.ndirs; j += nw)
-      gather_halo<kHaloBatch>(p, TW, adjacent_of(p, G, j, lane), p.halo_start[j], p.halo_start[j + 1], hoff,
-                  win + slots, in, lane);
+    for (uint32_t j = warp + nw; j < p.ndirs; j += nw) {
+      const uint32_t t = adjacent_of(p, G, j, lane);
+      gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff, win + slots,
+                              in, lane);
+      if constexpr (kT == 2) {
+        gather_halo<kHaloBatch>(p, TW, t, p.halo2_start[j], p.halo2_start[j + 1], hoff,
+                                win + slots, in, lane);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, t != ~0u);
+        if (lane == 0) emask[j] = m;
+      }
+    }
 
-    mbar_wait(&mbar[b], (it >> 1) & 1u, p.status);
+    mbar_wait(&mbar[b], (it >> 1) & 1u, p);
     // Bytes past the last 16-byte boundary of the buffer (only rows that end
     // within 16 bytes of it) were not part of a bulk copy: load them here.
     if (G.row0 + (uint64_t)(p.TH - 1) * W + seg + 16 > total) {
@@ -727,30 +795,35 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     // The only CTA barrier of the group: all words (rows and halo) are in
     // place, and every warp has finished the previous group.
     __syncthreads();
-    if (warp == 0 && g + g_stride < g_end && !cta_aborted())
+    if (warp == 0 && g + g_stride < g_end && !cta_aborted() && !withhold)
       issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
+
+    // kT = 2: step 1 of the own slot rows and of the first halo ring, X -> Y.
+    const unsigned char *rbase = wbase;   // the words the final rule pass reads
+    if constexpr (kT == 2) {
+      uint32_t *yw = reinterpret_cast<uint32_t *>(smem + win_bytes);
+      for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
+        uint32_t nx[kR];
+#pragma unroll
+        for (int k = 0; k < kR; ++k)
+          nx[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, wbase, vrow(u0, k) * 32u + lane) : 0u;
+#pragma unroll
+        for (int k = 0; k < kR; ++k)
+          if (vrow(u0, k) < VR) yw[vrow(u0, k) * 32u + lane] = nx[k];
+      }
+      for (uint32_t i = warp * 32u + lane; i < p.nhalo1; i += nw * 32u)
+        yw[slots + i] = rule_at<kLife>(p, wbase, slots + i) & emask[hdir[i]];
+      __syncthreads();   // step 1 complete; every warp is done reading X
+      rbase = smem + win_bytes;
+    }
 
     // Rule, inverse transpose and write-back of the own rows.
     for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
       uint32_t y[kR];
 #pragma unroll
-      for (int k = 0; k < kR; ++k) {
-        const uint32_t c = vrow(u0, k) * 32u + lane;
-        uint32_t next = 0;
-        if (vrow(u0, k) < VR) {
-          const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(p.refs) + c);
-          const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
-          uint32_t n[8];
-#pragma unroll
-          for (int d = 0; d < 4; ++d) {
-            n[2 * d] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4410));
-            n[2 * d + 1] = *reinterpret_cast<const uint32_t *>(wbase + __byte_perm(rw[d], 0, 0x4432));
-          }
-          next = rule_word<kLife>(p.rule, win[c], n);
-        }
-        y[k] = next;
-      }
+      for (int k = 0; k < kR; ++k)
+        y[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, rbase, vrow(u0, k) * 32u + lane) : 0u;
       transpose32_n<kR>(y, keep, rot);
       // Row offsets first: a shared load after the unpack's stores would wait for them.
       uint32_t arow[kR];
@@ -863,9 +936,9 @@ __device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLay
   }
 }
 
-// One step of one instance; CTA c of the persistent grid takes the
+// kT steps (1 or 2) of one instance; CTA c of the persistent grid takes the
 // contiguous run of groups [c G / grid, (c + 1) G / grid).
-template <bool kLife, int kTW>
+template <bool kLife, int kTW, int kT>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, TileLayout lay, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -875,40 +948,39 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   uint32_t it = 0;
   const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
   const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
-  run_groups<kLife, kTW>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
+  run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
   bulk_wait_all();
   settle_abort();
 }
 
 // One step of many instances (each with its own fractal, level and
-// buffers) in a single persistent launch.  parity selects the step's input:
-// buffer 0 on even steps, buffer 1 on odd ones.  Each schedule entry runs the
-// instantiation for its instance's tile-row width.
-template <bool kLife>
+// buffers) that share one tile-row instantiation, in a single persistent
+// launch.  parity selects the step's input: buffer 0 on even steps, buffer 1
+// on odd ones.  CTA c walks its schedule entries, each a contiguous run of
+// groups of one instance; the instance's description is copied to shared
+// memory for the run (its fields are read throughout the group loop).
+template <bool kLife, int kTW>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
     const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
     uint8_t *const *__restrict__ buf1, const BatchWork *__restrict__ work,
     const uint32_t *__restrict__ sched_start, TileLayout lay, uint32_t parity) {
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(16) TiledDev s_dev;
+  static_assert(sizeof(TiledDev) % 4 == 0, "TiledDev is copied as words");
   uint32_t keep[5], rot[5];
   make_transpose(threadIdx.x & 31u, keep, rot);
   init_barriers(smem, lay);
   uint32_t it = 0;
   for (uint32_t e = sched_start[blockIdx.x]; e < sched_start[blockIdx.x + 1]; ++e) {
     const BatchWork w = work[e];
-    const TiledDev &d = devs[w.instance];
+    __syncthreads();  // every thread is done with the previous entry's description
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(devs + w.instance);
+    for (uint32_t i = threadIdx.x; i < sizeof(TiledDev) / 4; i += blockDim.x)
+      reinterpret_cast<uint32_t *>(&s_dev)[i] = __ldg(src + i);
+    __syncthreads();  // s_dev complete: run_groups reads its sizes before its own first barrier
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
-    const uint32_t kind =
-        d.rpw == 4 ? 8u : (d.rpw == 2 ? 16u : (d.TW == 27 || d.TW == 25 || d.TW == 64 ? d.TW : 0u));
-    switch (kind) {
-      case 27: run_groups<kLife, 27>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-      case 25: run_groups<kLife, 25>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-      case 8: run_groups<kLife, 8>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-      case 16: run_groups<kLife, 16>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-      case 64: run_groups<kLife, 64>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-      default: run_groups<kLife, 0>(d, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it); break;
-    }
+    run_groups<kLife, kTW, 1>(s_dev, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it);
   }
   bulk_wait_all();
   settle_abort();
@@ -941,28 +1013,34 @@ __global__ void build_adjacency_kernel(FracDev f, TiledDev p, uint32_t *__restri
 
 // ---- host side: the level-L neighbour program ------------------------------
 
-const void *batch_kernel_for(bool life) {
-  return life ? (const void *)step_batch_kernel<true> : (const void *)step_batch_kernel<false>;
+// The batched kernel of one tile-row instantiation (see tiled_kernel_for).
+const void *batch_kernel_for(bool life, int kind) {
+  switch (kind) {
+    case 27: return life ? (const void *)step_batch_kernel<true, 27> : (const void *)step_batch_kernel<false, 27>;
+    case 25: return life ? (const void *)step_batch_kernel<true, 25> : (const void *)step_batch_kernel<false, 25>;
+    case 8: return life ? (const void *)step_batch_kernel<true, 8> : (const void *)step_batch_kernel<false, 8>;
+    case 16: return life ? (const void *)step_batch_kernel<true, 16> : (const void *)step_batch_kernel<false, 16>;
+    case 64: return life ? (const void *)step_batch_kernel<true, 64> : (const void *)step_batch_kernel<false, 64>;
+    default: return life ? (const void *)step_batch_kernel<true, 0> : (const void *)step_batch_kernel<false, 0>;
+  }
 }
 
 // The instantiation for a program: rows shared by slot words (rpw 4 or 2) and
 // rows of two slot words (width 64) have their own, as have the common widths
-// 27 (triangle) and 25 (Vicsek).
-const void *tiled_kernel_for(bool life, uint32_t TW, uint32_t rpw) {
-  if (life) {
-    if (rpw == 4) return (const void *)step_tiled_kernel<true, 8>;
-    if (rpw == 2) return (const void *)step_tiled_kernel<true, 16>;
-    if (TW == 64) return (const void *)step_tiled_kernel<true, 64>;
-    if (TW == 27) return (const void *)step_tiled_kernel<true, 27>;
-    if (TW == 25) return (const void *)step_tiled_kernel<true, 25>;
-    return (const void *)step_tiled_kernel<true, 0>;
-  }
-  if (rpw == 4) return (const void *)step_tiled_kernel<false, 8>;
-  if (rpw == 2) return (const void *)step_tiled_kernel<false, 16>;
-  if (TW == 64) return (const void *)step_tiled_kernel<false, 64>;
-  if (TW == 27) return (const void *)step_tiled_kernel<false, 27>;
-  if (TW == 25) return (const void *)step_tiled_kernel<false, 25>;
-  return (const void *)step_tiled_kernel<false, 0>;
+// 27 (triangle) and 25 (Vicsek); steps per launch 1 or 2.
+template <bool kLife, int kT>
+const void *tiled_kernel_of(uint32_t TW, uint32_t rpw) {
+  if (rpw == 4) return (const void *)step_tiled_kernel<kLife, 8, kT>;
+  if (rpw == 2) return (const void *)step_tiled_kernel<kLife, 16, kT>;
+  if (TW == 64) return (const void *)step_tiled_kernel<kLife, 64, kT>;
+  if (TW == 27) return (const void *)step_tiled_kernel<kLife, 27, kT>;
+  if (TW == 25) return (const void *)step_tiled_kernel<kLife, 25, kT>;
+  return (const void *)step_tiled_kernel<kLife, 0, kT>;
+}
+
+const void *tiled_kernel_for(bool life, uint32_t TW, uint32_t rpw, uint32_t steps) {
+  if (steps == 2) return life ? tiled_kernel_of<true, 2>(TW, rpw) : tiled_kernel_of<false, 2>(TW, rpw);
+  return life ? tiled_kernel_of<true, 1>(TW, rpw) : tiled_kernel_of<false, 1>(TW, rpw);
 }
 
 
@@ -977,14 +1055,21 @@ uint64_t ipow(uint64_t b, uint32_t e) {
 
 using namespace sq;
 
+static uint32_t layout_total(const TileLayout &l) {
+  return 2 * l.win_bytes + l.hoff_bytes + l.hdir_bytes + 16 + l.rowa_bytes + l.carry_bytes +
+         2 * l.stage_bytes;
+}
+
+// Word buffer: slots, halo words, the zero word and 9 per-direction masks.
 TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
   TileLayout l;
-  l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1) * 4 + 15) & ~(size_t)15);
+  l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1 + 9) * 4 + 15) & ~(size_t)15);
   l.hoff_bytes = (uint32_t)(((size_t)nhalo * 4 + 15) & ~(size_t)15);
+  l.hdir_bytes = (uint32_t)(((size_t)nhalo + 15) & ~(size_t)15);
   l.rowa_bytes = (uint32_t)(((size_t)2 * TH + 15) & ~(size_t)15);
   l.carry_bytes = 16u * TH;
   l.stage_bytes = (uint32_t)((size_t)TH * pitch + 64);  // + slack for whole-word reads
-  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + l.carry_bytes + 2 * l.stage_bytes;
+  l.smem = layout_total(l);
   return l;
 }
 
@@ -992,10 +1077,11 @@ TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
   TileLayout l;
   l.win_bytes = a.win_bytes > b.win_bytes ? a.win_bytes : b.win_bytes;
   l.hoff_bytes = a.hoff_bytes > b.hoff_bytes ? a.hoff_bytes : b.hoff_bytes;
+  l.hdir_bytes = a.hdir_bytes > b.hdir_bytes ? a.hdir_bytes : b.hdir_bytes;
   l.rowa_bytes = a.rowa_bytes > b.rowa_bytes ? a.rowa_bytes : b.rowa_bytes;
   l.carry_bytes = a.carry_bytes > b.carry_bytes ? a.carry_bytes : b.carry_bytes;
   l.stage_bytes = a.stage_bytes > b.stage_bytes ? a.stage_bytes : b.stage_bytes;
-  l.smem = 2 * l.win_bytes + l.hoff_bytes + 16 + l.rowa_bytes + l.carry_bytes + 2 * l.stage_bytes;
+  l.smem = layout_total(l);
   return l;
 }
 
@@ -1085,6 +1171,10 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   d.halo_dir = halo_dir;
   d.adj = adj;
   d.status = status;
+  d.wait_ns = kDefaultWaitNs;
+  d.fault = 0;
+  d.nhalo1 = sp.nhalo1;
+  for (int i = 0; i < 10; ++i) d.halo2_start[i] = sp.halo2_start[i];
   return d;
 }
 
@@ -1114,33 +1204,24 @@ bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level) {
 // stays within kTiledSmemCap (so that several CTAs share an SM).
 int sq_tiled_default_level(const squeeze_handle *h) { return sq_tiled_default_level_for(h->f); }
 
-// Number of distinct halo references (direction, cell of the adjacent block)
-// of the level-L program.
+// Number of distinct halo words of the level-L program as the handle builds
+// it (both rings: the second is needed to run two steps per launch).
 uint32_t count_halo(const FracDev &f, uint32_t L) {
-  uint32_t TW = (uint32_t)ipow(f.k, (L + 1) / 2), TH = (uint32_t)ipow(f.k, L / 2);
-  uint32_t cells = TW * TH, side = (uint32_t)ipow(f.s, L);
-  std::vector<int32_t> inv((size_t)side * side, -1);
-  std::vector<uint32_t> X(cells), Y(cells);
-  for (uint32_t c = 0; c < cells; ++c) {
-    local_lambda(f, L, c % TW, c / TW, X[c], Y[c]);
-    inv[(size_t)Y[c] * side + X[c]] = (int32_t)c;
-  }
-  std::vector<uint8_t> seen((size_t)9 * cells, 0);
-  uint32_t n = 0;
-  for (uint32_t c = 0; c < cells; ++c)
-    for (int d = 0; d < 9; ++d) {
-      int64_t qx = (int64_t)X[c] + d % 3 - 1, qy = (int64_t)Y[c] + d / 3 - 1;
-      int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
-      if (bx == 0 && by == 0) continue;
-      int32_t t = inv[(size_t)(qy - (int64_t)by * side) * side + (qx - (int64_t)bx * side)];
-      if (t < 0) continue;
-      uint8_t &m = seen[(size_t)((by + 1) * 3 + (bx + 1)) * cells + t];
-      if (!m) {
-        m = 1;
-        ++n;
-      }
-    }
-  return n;
+  TileBuildSizes z;
+  sq_tile_build_sizes(f, L, z);
+  std::vector<int32_t> inv(z.box);
+  std::vector<uint32_t> X(z.cells), Y(z.cells), refs((z.slots + z.halo) * 8), order(z.halo),
+      rank(z.halo);
+  std::vector<uint64_t> keys(z.halo), sorted(z.halo);
+  std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
+  std::vector<uint32_t> halo_off(z.halo);
+  std::vector<uint8_t> halo_dir(z.halo);
+  TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
+                 order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
+                 z.box, z.cells, z.slots, z.halo, 1u};
+  TileSpec sp;
+  if (sq_tile_build(f, L, B, sp) != SQUEEZE_OK) return 0xFFFFu;   // too large to build
+  return sp.nhalo;
 }
 
 size_t sq_tiled_smem_cap() { return kTiledSmemCap; }
@@ -1167,7 +1248,18 @@ void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
 
 // Host construction of the level-L neighbour program (see the file comment):
 // local lambda and its inverse over the level-L box, 8 references per slot
-// (local slot, halo slot or the zero word), halo slots sorted by direction.
+// (local slot, halo word or the zero word), halo words sorted by direction.
+//
+// With B.two_step the program also serves launches that run two steps: the
+// first ring of halo cells (the cells of adjacent blocks that are neighbours
+// of the tile's cells) gets references of its own, to the tile's slots, the
+// first ring and a second ring (their neighbours outside the tile and the
+// first ring), so that a launch can advance the tile and the first ring by
+// one step in shared memory and then the tile by a second step.  Halo words
+// are numbered first ring first ([0, nhalo1), sorted by direction), then the
+// second ring ([nhalo1, nhalo), sorted by direction); one-step launches read
+// the first ring only.  Word array: slots | first ring | second ring | zero
+// word | 9 words of per-direction "adjacent tile exists" masks.
 int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp) {
   if (L == 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
   uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
@@ -1189,56 +1281,80 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
     inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
   auto slot_of = [&](uint32_t c) { return tile_slot_of(c, TW, rpw, wpr); };
-  const uint32_t kNone = 0xFFFFFFFFu;
+  const uint32_t kNone = 0xFFFFFFFFu, kFull = 0xFFFFFFFEu;
   uint32_t *refs = B.refs;
-  for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;
   uint32_t nhalo = 0;
-  for (uint32_t c = 0; c < cells; ++c) {
+  // Reference to the point (qx, qy) of the expanded plane, relative to the
+  // tile's own level-L box: a local slot, slots + a halo index (a halo cell is
+  // registered on first sight), kNone for a hole, or kFull when the halo list
+  // is full.  Points up to two cells outside the box lie in the 8 adjacent
+  // boxes, since a box is at least 2 cells wide.
+  auto ref_of = [&](int64_t qx, int64_t qy) -> uint32_t {
+    const int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
+    const int64_t lxp = qx - (int64_t)bx * side, lyp = qy - (int64_t)by * side;
+    const int32_t target = inv[(size_t)lyp * side + lxp];
+    if (target < 0) return kNone;
+    if (bx == 0 && by == 0) return slot_of((uint32_t)target);
+    // (direction << 32) | local cell in the adjacent block
+    const uint64_t key = ((uint64_t)((by + 1) * 3 + (bx + 1)) << 32) | (uint32_t)target;
+    uint32_t i = 0;
+    while (i < nhalo && B.halo_key[i] != key) ++i;
+    if (i == nhalo) {
+      if (nhalo == B.halo_cap) return kFull;
+      B.halo_key[nhalo++] = key;
+    }
+    return slots + i;
+  };
+  // The 8 references of the cell at (px, py); an offset outside the
+  // neighbourhood refers to the zero word, like a hole.
+  auto fill_refs = [&](int64_t px, int64_t py, uint32_t *row) -> bool {
     int k8 = 0;
-    uint32_t sc = slot_of(c);
     for (int d = 0; d < 9; ++d) {
       if (d == 4) continue;
-      int64_t qx = (int64_t)B.X[c] + d % 3 - 1, qy = (int64_t)B.Y[c] + d / 3 - 1;
-      int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
-      int64_t lxp = qx - (int64_t)bx * side, lyp = qy - (int64_t)by * side;
-      // an offset outside the neighbourhood refers to the zero word, like a hole
-      int32_t target = ((f.nbhd >> d) & 1u) ? inv[(size_t)lyp * side + lxp] : -1;
       uint32_t ref = kNone;
-      if (target >= 0) {
-        if (bx == 0 && by == 0) {
-          ref = slot_of((uint32_t)target);
-        } else {
-          // (direction << 32) | local cell in the adjacent block
-          uint64_t key = ((uint64_t)((by + 1) * 3 + (bx + 1)) << 32) | (uint32_t)target;
-          uint32_t i = 0;
-          while (i < nhalo && B.halo_key[i] != key) ++i;
-          if (i == nhalo) {
-            if (nhalo == B.halo_cap) return SQUEEZE_ERR_UNSUPPORTED;
-            B.halo_key[nhalo++] = key;
-          }
-          ref = slots + i;
-        }
-      }
-      refs[(size_t)sc * 8 + k8++] = ref;
+      if ((f.nbhd >> d) & 1u) ref = ref_of(px + d % 3 - 1, py + d / 3 - 1);
+      if (ref == kFull) return false;
+      row[k8++] = ref;
+    }
+    return true;
+  };
+  for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;   // slots without a cell
+  for (uint32_t c = 0; c < cells; ++c)
+    if (!fill_refs(B.X[c], B.Y[c], refs + (size_t)slot_of(c) * 8)) return SQUEEZE_ERR_UNSUPPORTED;
+  const uint32_t n1 = nhalo;
+  if (B.two_step) {
+    // References of the first ring (its neighbours may add the second ring).
+    for (uint32_t i = 0; i < n1; ++i) {
+      const uint64_t key = B.halo_key[i];
+      const uint32_t d = (uint32_t)(key >> 32), t = (uint32_t)key;
+      const int64_t px = (int64_t)B.X[t] + ((int)(d % 3) - 1) * (int64_t)side;
+      const int64_t py = (int64_t)B.Y[t] + ((int)(d / 3) - 1) * (int64_t)side;
+      if (!fill_refs(px, py, refs + (size_t)(slots + i) * 8)) return SQUEEZE_ERR_UNSUPPORTED;
     }
   }
-  // Sort the halo slots by direction (then local cell) and renumber them.
+  // Sort each ring by direction (then local cell) and renumber: the first
+  // ring takes [0, n1), the second [n1, nhalo).
   for (uint32_t i = 0; i < nhalo; ++i) B.order[i] = i;
-  std::sort(B.order, B.order + nhalo,
-            [&](uint32_t x, uint32_t y) { return B.halo_key[x] < B.halo_key[y]; });
+  auto by_key = [&](uint32_t x, uint32_t y) { return B.halo_key[x] < B.halo_key[y]; };
+  std::sort(B.order, B.order + n1, by_key);
+  std::sort(B.order + n1, B.order + nhalo, by_key);
   for (uint32_t i = 0; i < nhalo; ++i) B.rank[B.order[i]] = i;
-  for (size_t i = 0; i < (size_t)slots * 8; ++i)
-    if (refs[i] != kNone && refs[i] >= slots) refs[i] = slots + B.rank[refs[i] - slots];
-  // keys in sorted order
   uint64_t *sorted = B.halo_sorted;
   for (uint32_t i = 0; i < nhalo; ++i) sorted[B.rank[i]] = B.halo_key[i];
-  // References are byte offsets into the word array, 8 per slot (16 bytes).
-  if (((uint64_t)slots + nhalo + 1) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
+  // References are byte offsets into the word array, 8 per slot (16 bytes);
+  // rows of the first ring follow the slots' rows in their sorted order.
+  const uint32_t zero = slots + nhalo;
+  if (((uint64_t)zero + 1 + 9) * 4 > 0xFFFFu) return SQUEEZE_ERR_UNSUPPORTED;
+  auto enc = [&](uint32_t r) -> uint16_t {
+    if (r == kNone) return (uint16_t)(4u * zero);
+    return (uint16_t)(4u * (r < slots ? r : slots + B.rank[r - slots]));
+  };
   for (uint32_t c = 0; c < slots; ++c)
-    for (uint32_t d = 0; d < 8; ++d) {
-      uint32_t r = refs[(size_t)c * 8 + d];
-      B.refs16[(size_t)c * 8 + d] = (uint16_t)(4u * (r == kNone ? slots + nhalo : r));
-    }
+    for (uint32_t d = 0; d < 8; ++d) B.refs16[(size_t)c * 8 + d] = enc(refs[(size_t)c * 8 + d]);
+  if (B.two_step)
+    for (uint32_t i = 0; i < n1; ++i)
+      for (uint32_t d = 0; d < 8; ++d)
+        B.refs16[(size_t)(slots + B.rank[i]) * 8 + d] = enc(refs[(size_t)(slots + i) * 8 + d]);
   uint32_t dir_mask = 0;
   for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(sorted[i] >> 32);
   memset(&sp, 0, sizeof(sp));
@@ -1248,14 +1364,17 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
       dir_index[d] = (uint8_t)sp.ndirs;
       sp.dir_list[sp.ndirs++] = (uint8_t)d;
     }
+  for (uint32_t j = 0; j < 10; ++j) sp.halo2_start[j] = n1;
   for (uint32_t i = 0; i < nhalo; ++i) {
     uint32_t d = (uint32_t)(sorted[i] >> 32), lc = (uint32_t)sorted[i];
     B.halo_dir[i] = dir_index[d];
     B.halo_off[i] = (lc / TW) * f.W + lc % TW;
-    sp.halo_start[dir_index[d] + 1] = i + 1;
+    (i < n1 ? sp.halo_start : sp.halo2_start)[dir_index[d] + 1] = i + 1;
   }
-  for (uint32_t j = 1; j <= 9; ++j)
+  for (uint32_t j = 1; j <= 9; ++j) {
     if (sp.halo_start[j] < sp.halo_start[j - 1]) sp.halo_start[j] = sp.halo_start[j - 1];
+    if (sp.halo2_start[j] < sp.halo2_start[j - 1]) sp.halo2_start[j] = sp.halo2_start[j - 1];
+  }
   sp.L = L;
   sp.TW = TW;
   sp.TH = TH;
@@ -1263,6 +1382,8 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.cells = cells;
   sp.slots = slots;
   sp.nhalo = nhalo;
+  sp.nhalo1 = n1;
+  sp.two_step = B.two_step ? 1u : 0u;
   sp.dir_mask = dir_mask;
   sp.tiles_x = f.W / TW;
   sp.tiles_y = f.H / TH;
@@ -1294,16 +1415,20 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return sq_cuda_fail(e);
-  for (int life = 0; life < 2; ++life) {
-    const void *fn = tiled_kernel_for(life != 0, sp.TW, sp.rpw);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
-    int n = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
-    if (e != cudaSuccess) return sq_cuda_fail(e);
-    if (n < 1) return SQUEEZE_ERR_UNSUPPORTED;
-    uint64_t grid = (uint64_t)n * sms;
-    (life ? sp.grid : sp.grid_rule) = (int)(grid < sp.groups ? grid : sp.groups);
-  }
+  for (uint32_t steps = 1; steps <= (sp.two_step ? 2u : 1u); ++steps)
+    for (int life = 0; life < 2; ++life) {
+      const void *fn = tiled_kernel_for(life != 0, sp.TW, sp.rpw, steps);
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
+      int n = 0;
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);
+      if (e != cudaSuccess) return sq_cuda_fail(e);
+      if (n < 1) return SQUEEZE_ERR_UNSUPPORTED;
+      const uint64_t grid = (uint64_t)n * sms;
+      const int g = (int)(grid < sp.groups ? grid : sp.groups);
+      if (steps == 1) (life ? sp.grid : sp.grid_rule) = g;
+      else (life ? sp.grid2 : sp.grid2_rule) = g;
+    }
   return SQUEEZE_OK;
 }
 
@@ -1316,13 +1441,15 @@ int sq_tile_build_adjacency(const FracDev &f, const TiledDev &d, uint32_t *adj, 
 }
 
 int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uint8_t *out,
-                   cudaStream_t st) {
+                   uint32_t steps, cudaStream_t st) {
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
+  if (steps != 1 && !(steps == 2 && sp.two_step)) return SQUEEZE_ERR_INVALID_ARG;
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
   TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
   void *args[] = {&dd, &lay, &in, &out};
-  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw), dim3(life ? sp.grid : sp.grid_rule),
+  const int grid = steps == 2 ? (life ? sp.grid2 : sp.grid2_rule) : (life ? sp.grid : sp.grid_rule);
+  SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw, steps), dim3(grid),
                            dim3(sp.threads), args, sp.smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
@@ -1338,14 +1465,15 @@ int sq_tiled_prepare(squeeze_handle *h) {
   sq_tile_build_sizes(f, L, z);
   if (z.box > (1ull << 28)) return SQUEEZE_ERR_UNSUPPORTED;
   std::vector<int32_t> inv(z.box);
-  std::vector<uint32_t> X(z.cells), Y(z.cells), refs(z.slots * 8), order(z.halo), rank(z.halo);
+  std::vector<uint32_t> X(z.cells), Y(z.cells), refs((z.slots + z.halo) * 8), order(z.halo),
+      rank(z.halo);
   std::vector<uint64_t> keys(z.halo), sorted(z.halo);
-  std::vector<uint16_t> refs16(z.slots * 8);
+  std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
   std::vector<uint32_t> halo_off(z.halo);
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
-                 z.box, z.cells, z.slots, z.halo};
+                 z.box, z.cells, z.slots, z.halo, 1u};
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
   int rc = sq_tile_build(f, L, B, p->spec);
@@ -1356,11 +1484,12 @@ int sq_tiled_prepare(squeeze_handle *h) {
   }
   const TileSpec &sp = p->spec;
   uint32_t nhalo = sp.nhalo;
-  cudaError_t e = cudaMalloc(&p->d_refs, (size_t)sp.slots * 16);
+  const size_t ref_bytes = (size_t)(sp.slots + sp.nhalo1) * 16;   // slots, then the first ring
+  cudaError_t e = cudaMalloc(&p->d_refs, ref_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
   if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_refs, refs16.data(), (size_t)sp.slots * 16, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->d_refs, refs16.data(), ref_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
     e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
@@ -1388,25 +1517,38 @@ int sq_tiled_prepare(squeeze_handle *h) {
 }
 
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
-                         cudaStream_t st) {
+                         uint32_t steps, cudaStream_t st) {
   const TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
-  return sq_tile_launch(d, p->spec, in, out, st);
+  if (h->wait_ns) d.wait_ns = h->wait_ns;
+  d.fault = h->fault;
+  return sq_tile_launch(d, p->spec, in, out, steps, st);
 }
+
+bool sq_tiled_two_step(const squeeze_handle *h) { return h->tiled && h->tiled->spec.two_step; }
 
 int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
   const TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   *d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
                     h->d_status);
+  if (h->wait_ns) d->wait_ns = h->wait_ns;
+  d->fault = h->fault;
   *sp = p->spec;
   return SQUEEZE_OK;
 }
 
-int sq_batch_occupancy(bool life, int threads, uint32_t smem) {
-  const void *fn = batch_kernel_for(life);
+int sq_tile_kind(const TileSpec &sp) {
+  if (sp.rpw == 4) return 8;
+  if (sp.rpw == 2) return 16;
+  if (sp.TW == 27 || sp.TW == 25 || sp.TW == 64) return (int)sp.TW;
+  return 0;
+}
+
+int sq_batch_occupancy(bool life, int kind, int threads, uint32_t smem) {
+  const void *fn = batch_kernel_for(life, kind);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -1417,10 +1559,11 @@ int sq_batch_occupancy(bool life, int threads, uint32_t smem) {
 
 int sq_batch_launch(const TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const BatchWork *d_work, const uint32_t *d_sched, const TileLayout &lay,
-                    int grid, int threads, bool life, uint32_t parity, cudaStream_t st) {
+                    int grid, int threads, bool life, int kind, uint32_t parity, cudaStream_t st) {
   TileLayout l = lay;
   void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity};
-  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life), dim3(grid), dim3(threads), args, l.smem, st));
+  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, kind), dim3(grid), dim3(threads), args, l.smem,
+                           st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }

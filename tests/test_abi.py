@@ -57,6 +57,13 @@ def test_null_handle_is_rejected():
     with pytest.raises(sq.SqueezeError) as e:
         sq.squeeze_info(None)
     assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+    for call in (lambda: sq.squeeze_set_wait_limit(None, 0),
+                 lambda: sq.squeeze_set_fault_injection(None, 0),
+                 lambda: sq.squeeze_last_step_info(None)):
+        with pytest.raises(sq.SqueezeError) as e:
+            call()
+        assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
+    assert "unsafe" in sq.squeeze_status_string(sq.SQUEEZE_ERR_DEVICE_UNSAFE)
 
 
 @pytest.mark.parametrize("s,k,offsets,r", [

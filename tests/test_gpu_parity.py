@@ -248,7 +248,14 @@ def test_misaligned_buffers():
             sq.squeeze_step(h.h, a, b, 1, sq.SQUEEZE_STEP_TILED)
         assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
         sq.squeeze_step(h.h, a, b, 1, sq.SQUEEZE_STEP_AUTO)  # falls back to the ALU kernel
+        assert sq.squeeze_last_step_info(h.h)[0] == sq.SQUEEZE_MAP_ALU   # ... observably
         assert np.array_equal(b.cpu().numpy(), oracle.run_compact(f, r, c0, 1))
+        x = torch.empty(h.cells, dtype=torch.uint8, device=DEV)
+        y = torch.empty_like(x)
+        x.copy_(to_dev(c0))
+        sq.squeeze_step(h.h, x, y, 1, sq.SQUEEZE_STEP_AUTO)   # aligned: the tiled kernel
+        assert sq.squeeze_last_step_info(h.h)[0] == sq.SQUEEZE_STEP_TILED
+        assert torch.equal(y, b)
 
 
 def test_tile_level_limits():
@@ -420,3 +427,45 @@ def test_r20_tiled_against_light_cone_and_alu():
         got = a[torch.from_numpy(om.astype(np.int64)).to(DEV)].cpu().numpy()
         assert np.array_equal(got, want)
         assert_status_ok(h)
+
+
+TWO_STEP_RULES = [(1 << 3, (1 << 2) | (1 << 3)),                    # B3/S23
+                  ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),       # HighLife
+                  ((1 << 0) | (1 << 3), (1 << 2) | (1 << 3))]       # B03/S23: births at 0
+
+
+@pytest.mark.parametrize("f,r", [(I.TRIANGLE, 9), (I.TRIANGLE_PAPER, 8), (I.CARPET, 5),
+                                 (I.VICSEK, 6), (I.FULL2, 7), (I.TRIANGLE, 4)],
+                         ids=["triangle9", "triangle_paper8", "carpet5", "vicsek6", "full2-7",
+                              "triangle4"])
+@pytest.mark.parametrize("steps", [4, 7, 12])
+def test_two_step_launches_match_the_oracle(f, r, steps):
+    """The tiled kernel runs pairs of steps in one launch (step 1 of the tile and
+    of its first halo ring in shared memory); every rule, including one with
+    births at zero neighbours (which a missing adjacent tile must not feed),
+    must give the oracle's states."""
+    with sq.Handle(f, r) as h:
+        c0 = I.bernoulli_bytes(31 + steps, h.cells, 0.4)
+        box0 = oracle.compact_to_box(f, r, c0)
+        m = oracle.member_grid(f, r)
+        for rule in TWO_STEP_RULES:
+            sq.squeeze_set_rule(h.h, *rule)
+            got = run_steps(h, c0, steps, sq.SQUEEZE_STEP_TILED)
+            kind, launches, two = sq.squeeze_last_step_info(h.h)
+            assert kind == sq.SQUEEZE_STEP_TILED and two >= 1
+            assert launches % 2 == steps % 2 and 2 * two + (launches - two) == steps
+            want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(m, box0, steps, rule,
+                                                                   oracle.MOORE))
+            assert np.array_equal(got, want), rule
+        assert sq.squeeze_device_status(h.h) == sq.SQUEEZE_OK
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 6, 10])
+def test_launch_plan_puts_the_result_in_the_right_buffer(steps):
+    f, r = I.TRIANGLE, 10
+    with sq.Handle(f, r) as h:
+        c0 = I.bernoulli_bytes(5, h.cells, 0.5)
+        got = run_steps(h, c0, steps, sq.SQUEEZE_STEP_TILED)
+        _, launches, two = sq.squeeze_last_step_info(h.h)
+        assert launches % 2 == steps % 2 and 2 * two + (launches - two) == steps
+        assert np.array_equal(got, oracle.run_compact(f, r, c0, steps))

@@ -50,26 +50,27 @@ def ptr(a):
     return a.ctypes.data_as(P)
 
 
-def program(lib, f, r, L, nbhd):
+def program(lib, f, r, L, nbhd, two_step=0):
     off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
     caps = np.zeros(3, dtype=np.uint64)
     assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
     cells, slots, halo = (int(v) for v in caps)
-    info = np.zeros(8, dtype=np.uint32)
+    info = np.zeros(9, dtype=np.uint32)
     slot = np.zeros(cells, dtype=np.uint32)
     X = np.zeros(cells, dtype=np.uint32)
     Y = np.zeros(cells, dtype=np.uint32)
-    refs16 = np.zeros(slots * 8, dtype=np.uint16)
+    refs16 = np.zeros((slots + halo) * 8, dtype=np.uint16)
     halo_off = np.zeros(halo, dtype=np.uint32)
     halo_dir = np.zeros(halo, dtype=np.uint8)
     dir_list = np.zeros(9, dtype=np.uint8)
-    rc = lib.tile_program(f.s, f.k, ptr(off), r, L, nbhd, ptr(info), ptr(slot), ptr(X), ptr(Y),
-                          ptr(refs16), ptr(halo_off), ptr(halo_dir), ptr(dir_list))
+    rc = lib.tile_program(f.s, f.k, ptr(off), r, L, nbhd, two_step, ptr(info), ptr(slot), ptr(X),
+                          ptr(Y), ptr(refs16), ptr(halo_off), ptr(halo_dir), ptr(dir_list))
     assert rc == 0, rc
-    TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs = (int(v) for v in info)
+    TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs, nhalo1 = (int(v) for v in info)
+    nrows = nslot + (nhalo1 if two_step else 0)
     return dict(TW=TW, TH=TH, rpw=rpw, wpr=wpr, cells=ncell, slots=nslot, nhalo=nhalo,
-                slot=slot[:ncell].astype(np.int64), X=X[:ncell].astype(np.int64),
-                Y=Y[:ncell].astype(np.int64), refs=(refs16[:nslot * 8] // 4).astype(np.int64),
+                nhalo1=nhalo1, slot=slot[:ncell].astype(np.int64), X=X[:ncell].astype(np.int64),
+                Y=Y[:ncell].astype(np.int64), refs=(refs16[:nrows * 8] // 4).astype(np.int64),
                 halo_off=halo_off[:nhalo].astype(np.int64), halo_dir=halo_dir[:nhalo],
                 dir_list=dir_list[:ndirs])
 
@@ -129,6 +130,41 @@ def emulate_step(f, r, L, prog, state, adj, rule=oracle.B3S23):
     return out
 
 
+def emulate_two_steps(f, r, L, prog, state, adj, rule=oracle.B3S23, mask=True):
+    """Two steps of every tile through the two-step program, as one launch
+    runs them: the tile's words and both halo rings from the state, step 1
+    of the slots and of the first ring (a first-ring cell of a missing tile
+    stays dead), then step 2 of the tile from those."""
+    W = oracle.compact_shape(f, r)[1]
+    TW, slots, n1 = prog["TW"], prog["slots"], prog["nhalo1"]
+    bases = tile_bases(f, r, prog)
+    loff = (np.arange(prog["cells"]) // TW) * W + np.arange(prog["cells"]) % TW
+    nw = slots + prog["nhalo"] + 1
+    x = np.zeros((len(bases), nw), dtype=np.int64)
+    x[:, prog["slot"]] = state[bases[:, None] + loff[None, :]].astype(np.int64) & 1
+    exists = np.zeros((len(bases), prog["nhalo"]), dtype=np.int64)
+    for i in range(prog["nhalo"]):
+        a = adj[:, prog["halo_dir"][i]]
+        ok = a >= 0
+        x[ok, slots + i] = state[a[ok] + prog["halo_off"][i]] & 1
+        exists[:, i] = ok
+    refs = prog["refs"].reshape(-1, 8)                        # rows: slots, then the first ring
+
+    def rule_rows(words, rows):
+        count = words[:, refs[rows]].sum(axis=2)
+        own = words[:, rows]
+        return np.where(own == 1, (rule[1] >> count) & 1, (rule[0] >> count) & 1)
+
+    y = np.zeros_like(x)
+    y[:, prog["slot"]] = rule_rows(x, prog["slot"])
+    ring = np.arange(slots, slots + n1)
+    y[:, ring] = rule_rows(x, ring) & (exists[:, :n1] if mask else 1)
+    nxt = rule_rows(y, prog["slot"])
+    out = np.zeros_like(state)
+    out[bases[:, None] + loff[None, :]] = nxt
+    return out
+
+
 CASES = [
     (I.TRIANGLE, 8, 2, oracle.MOORE), (I.TRIANGLE, 8, 3, oracle.MOORE),
     (I.TRIANGLE, 8, 5, oracle.MOORE), (I.TRIANGLE, 9, 6, oracle.MOORE),
@@ -162,3 +198,42 @@ def test_program_shapes_cover_every_kernel_width(lib):
         p = program(lib, f, r, L, nbhd)
         seen.add((p["TW"], p["rpw"], p["wpr"]))
     assert {(27, 1, 1), (25, 1, 1), (8, 4, 1), (16, 2, 1), (64, 1, 2)} <= seen
+
+
+TWO_STEP_RULES = [oracle.B3S23, ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),   # Life, HighLife
+                  ((1 << 0) | (1 << 3), (1 << 2) | (1 << 3))]                 # B03/S23: birth at 0
+
+
+@pytest.mark.parametrize("f,r,L,nbhd", CASES,
+                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CASES])
+def test_two_step_program_equals_two_oracle_steps(lib, f, r, L, nbhd):
+    prog = program(lib, f, r, L, nbhd, two_step=1)
+    one = program(lib, f, r, L, nbhd)
+    # the first ring, its order and the slots' references are the one-step program's
+    assert prog["nhalo1"] == one["nhalo"] and prog["nhalo"] >= prog["nhalo1"]
+    assert np.array_equal(prog["halo_off"][:prog["nhalo1"]], one["halo_off"])
+    zero1, zero2 = one["slots"] + one["nhalo"], prog["slots"] + prog["nhalo"]
+    r1 = one["refs"].copy()
+    r1[r1 == zero1] = zero2
+    assert np.array_equal(prog["refs"][:prog["slots"] * 8], r1)
+    state = I.bernoulli_bytes(200 + r + L, f.k ** r, 0.45)
+    m = oracle.member_grid(f, r)
+    adj = library_adjacency(lib, f, r, L, prog)
+    for rule in TWO_STEP_RULES:
+        want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
+            m, oracle.compact_to_box(f, r, state), 2, rule, nbhd))
+        assert np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule), want), rule
+
+
+def test_two_step_emulation_catches_a_dropped_existence_mask(lib):
+    # Without the mask a first-ring cell of a missing tile can be born (rule
+    # B03 births at 0 neighbours) and feed step 2: the result must then differ.
+    f, r, L = I.TRIANGLE, 8, 3
+    prog = program(lib, f, r, L, oracle.MOORE, two_step=1)
+    adj = library_adjacency(lib, f, r, L, prog)
+    state = I.bernoulli_bytes(7, f.k ** r, 0.45)
+    rule = TWO_STEP_RULES[2]
+    want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
+        oracle.member_grid(f, r), oracle.compact_to_box(f, r, state), 2, rule, oracle.MOORE))
+    assert np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule), want)
+    assert not np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule, mask=False), want)

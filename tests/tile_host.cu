@@ -48,20 +48,23 @@ int tile_sizes(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t 
   return SQUEEZE_OK;
 }
 
-// The level-L program: info = (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs);
-// per local cell its slot and local expanded position; per slot 8 byte
-// offsets into the word array (slots, then halo words, then a zero word);
-// per halo word its offset from the adjacent tile's base and its direction
-// index into dir_list.
+// The level-L program: info = (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs,
+// nhalo1); per local cell its slot and local expanded position; per slot (and,
+// for a two-step program, per first-ring halo word after them) 8 byte offsets
+// into the word array (slots, then halo words, then a zero word); per halo
+// word its offset from the adjacent tile's base and its direction index into
+// dir_list.  refs16 needs (slots + halo) * 8 entries.
 int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L,
-                 uint32_t nbhd, uint32_t *info, uint32_t *slot, uint32_t *X, uint32_t *Y,
-                 uint16_t *refs16, uint32_t *halo_off, uint8_t *halo_dir, uint8_t *dir_list) {
+                 uint32_t nbhd, uint32_t two_step, uint32_t *info, uint32_t *slot, uint32_t *X,
+                 uint32_t *Y, uint16_t *refs16, uint32_t *halo_off, uint8_t *halo_dir,
+                 uint8_t *dir_list) {
   FracDev f;
   if (!fill(s, k, off, r, nbhd, f)) return SQUEEZE_ERR_INVALID_ARG;
   TileBuildSizes z;
   sq_tile_build_sizes(f, L, z);
   std::vector<int32_t> inv(z.box);
-  std::vector<uint32_t> vX(z.cells), vY(z.cells), refs(z.slots * 8), order(z.halo), rank(z.halo);
+  std::vector<uint32_t> vX(z.cells), vY(z.cells), refs((z.slots + z.halo) * 8), order(z.halo),
+      rank(z.halo);
   std::vector<uint64_t> key(z.halo), sorted(z.halo);
   TileBuild B;
   B.inv = inv.data();
@@ -79,11 +82,13 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   B.cells_cap = z.cells;
   B.slots_cap = z.slots;
   B.halo_cap = z.halo;
+  B.two_step = two_step;
   TileSpec sp;
   const int rc = sq_tile_build(f, L, B, sp);
   if (rc) return rc;
   const uint32_t wpr = sp.TW == 64 ? 2u : 1u;
-  const uint32_t v[8] = {sp.TW, sp.TH, sp.rpw, wpr, sp.cells, sp.slots, sp.nhalo, sp.ndirs};
+  const uint32_t v[9] = {sp.TW, sp.TH, sp.rpw, wpr, sp.cells, sp.slots, sp.nhalo, sp.ndirs,
+                         sp.nhalo1};
   memcpy(info, v, sizeof(v));
   for (uint32_t c = 0; c < sp.cells; ++c) {
     slot[c] = tile_slot_of(c, sp.TW, sp.rpw, wpr);
