@@ -1,9 +1,10 @@
 """Benchmark: compact-fractal B3/S23 steps on the Sierpinski triangle, level 20.
 
 One bench step = one run of the workload: 100 synchronous B3/S23 steps over
-the 3,486,784,401-cell compact state (Bernoulli(0.5), seed 3).  Each CA step
-is one launch of the bit-sliced tile kernel.  The state (2 x 3.49 GB) is far
-larger than L2, so no flush is needed between steps.
+the 3,486,784,401-cell compact state (Bernoulli(0.5), seed 3), as 50 launches
+of the bit-sliced tile kernel that each advance two steps (the intermediate
+step stays in shared memory).  The state (2 x 3.49 GB) is far larger than
+L2, so no flush is needed between launches.
 
 Printed (rank 0, one JSON line): value = fractal cell-updates/s over all
 ranks; the roofline of the step kernel against the measured HBM copy
@@ -11,10 +12,14 @@ bandwidth; the end-to-end rate through the C ABI from and to pinned host
 memory; the same-GPU bounding-box comparison at level 16; the integer-ALU
 maps and per-cell step against their tensor-core (tcgen05) forms at level 20;
 the block-level layouts at level 16; the von Neumann tiled step and fp32 heat
-diffusion; the CPU oracle on a bounded sample; SM clocks sampled during the
-timed region.
+diffusion; the 256-instance batched mix (autotuned, 50 steps under a CUDA
+graph) and the 10,000-request loop (Poisson arrivals at 80 % of the batched
+mix's measured throughput, p50/p99 latency); the CPU oracle on a bounded
+sample, on the level-10 workload and on the level-16 box; SM clocks sampled
+during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl squeeze|reference]
+                  [--requests N] [--no-serve] [--no-compare] [--no-cpu]
 """
 from __future__ import annotations
 
@@ -50,6 +55,9 @@ def parse():
     p.add_argument("--impl", default="squeeze", choices=["squeeze", "reference"])
     p.add_argument("--no-compare", action="store_true", help="skip the level-16 BB comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-serve", action="store_true",
+                   help="skip the batched mix and the request loop")
+    p.add_argument("--requests", type=int, default=10000, help="requests of the request loop")
     return p.parse_args()
 
 
@@ -186,6 +194,38 @@ def oracle_r10_timing():
     return out
 
 
+_R16_TIMER = """
+import json, sys, time
+sys.path.insert(0, %r)
+import oracle
+from paper_2201_00613_gb300 import inputs as I
+w = I.TRIANGLE_R16
+steps = int(sys.argv[1])
+m = oracle.member_grid(w.fractal, w.r)
+box = oracle.box_init(w.fractal, w.r, w.seed, I.p_q24(w.p))
+t0 = time.perf_counter()
+oracle.box_run(m, box, steps)
+dt = time.perf_counter() - t0
+print(json.dumps({"cells_per_s": w.fractal.cells(w.r) * steps / dt, "steps": steps,
+                  "seconds": dt, "threads": oracle.threads()}))
+"""
+
+
+def oracle_r16_timing():
+    """The oracle on the level-16 workload's whole 65,536^2 box (13 GB of host
+    memory): 10 steps on all cores, 2 steps on one core (separate processes)."""
+    out = {}
+    for name, env, steps in (("all_cores", {}, 10), ("one_core", {"OMP_NUM_THREADS": "1"}, 2)):
+        res = subprocess.run([sys.executable, "-c", _R16_TIMER % ROOT, str(steps)],
+                             capture_output=True, text=True, env=dict(os.environ, **env),
+                             timeout=900)
+        if res.returncode == 0 and res.stdout.strip():
+            out[name] = json.loads(res.stdout.strip().splitlines()[-1])
+        else:
+            out[name] = {"error": (res.stderr or res.stdout)[-300:]}
+    return out
+
+
 def cpu_oracle_baseline(seconds_hint=True):
     """The oracle as it stands, on all host cores, on a bounded sample of the
     workload: the level-CPU_SAMPLE_LEVEL top-left sub-replica of the level-20
@@ -312,11 +352,15 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1))
     clocks = clk.summary()
     status = sq.squeeze_device_status(h.h)
-    launches = args.steps * w.n_steps
+    _, launches_per_step, two_step = sq.squeeze_last_step_info(h.h)
+    launches = args.steps * launches_per_step
+    steps_per_launch = w.n_steps / launches_per_step
     ms_per_step = ms / args.steps
     value = job_value(cells, w.n_steps, args.steps, ms, world)
     launch_s = ms / 1e3 / launches
-    algo_bytes = 2 * cells  # own state read once + new state written once
+    # Algorithmic bytes: 2 per cell-update (own state read once, new state
+    # written once) times the cell-updates of one launch.
+    algo_bytes = 2 * cells * steps_per_launch
     peak, peak_kind = peaks()
     achieved = algo_bytes / launch_s / 1e9
     traffic = traffic_per_launch()
@@ -350,11 +394,18 @@ def main():
         except Exception as e:   # reported in the line, never fatal to it
             nbb3d = {"error": str(e)[:300]}
 
+    mix = loop = None
+    if not args.no_serve:
+        mix = batch_mix_leg(sq, torch, dev, peaks()[0])
+        if args.requests > 0 and world == 1:
+            loop = request_loop_leg(args.requests, mix["cell_updates_per_s"], mix["shape"]["levels"])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_baseline()
         cpu["cpu_model"] = _cpu_model()
         cpu["sierpinski_triangle_r10_100_steps"] = oracle_r10_timing()
+        cpu["sierpinski_triangle_r16_box"] = oracle_r16_timing()
 
     if rank == 0:
         line = {
@@ -366,6 +417,9 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
+                         "steps_per_launch": steps_per_launch,
+                         "state_bytes_moved_per_launch": 2 * cells,
+                         "dram_gbs": (traffic if traffic else 2 * cells) / launch_s / 1e9,
                          "avg_launch_ms": launch_s * 1e3},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": cells,
                     "d2h_bytes_per_step": cells, "api": "squeeze_step_host",
@@ -378,11 +432,64 @@ def main():
             "block_compare": blocks,
             "workload_compare": workloads,
             "nbb3d_compare": nbb3d,
+            "batch_mix": mix,
+            "request_loop": loop,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_mix_leg(sq, torch, dev, peak_gbs, steps=50):
+    """The 256-instance mixed batch (triangle r 8-14, carpet r 4-8, Vicsek r
+    5-9, Bernoulli(0.5), seed 5): autotuned tile levels and launch shape, then
+    `steps` steps in one captured CUDA graph (one launch per tile-row
+    instantiation and step), timed with CUDA events after a warm replay.  Two
+    bytes per cell-update against the copy bandwidth (the 0.9 GB of states
+    exceed L2)."""
+    from paper_2201_00613_gb300.batch import MixedBatch, autotune
+    mix = I.batch_mix(5, 256)
+    t0 = time.perf_counter()
+    shape = autotune(mix)
+    tune_s = time.perf_counter() - t0
+    with MixedBatch(mix, levels=shape["levels"], threads=shape["threads"],
+                    ctas_per_sm=shape["ctas_per_sm"]) as mb:
+        mb.run(steps)   # capture + warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mb.run(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        rate = mb.cells * steps / sec
+        status = max((abs(sq.squeeze_device_status(h.h)) for h in mb.handles), default=0)
+        launches = sq.squeeze_batch_info(mb.batch)
+        return {"workload": "batched mix, 256 instances, seed 5", "instances": len(mix),
+                "cells": mb.cells, "steps": steps, "seconds": sec, "cell_updates_per_s": rate,
+                "hbm_frac": 2 * rate / 1e9 / peak_gbs, "state_bytes": 2 * mb.cells,
+                "shape": {k: shape[k] for k in ("levels", "threads", "ctas_per_sm")},
+                "ctas_per_step": launches[0], "tuning_seconds": tune_s, "status": -status}
+
+
+def request_loop_leg(n, capacity, levels):
+    """`n` requests (seed 6): type uniform over the mix, level uniform up to
+    triangle 18 / carpet 9 / Vicsek 12, steps uniform 10-500, Poisson arrivals
+    at a rate that offers 80 % of the batched mix's measured throughput;
+    continuous batching with admission by free HBM (64 slots, rounds of at
+    most 25 steps)."""
+    from paper_2201_00613_gb300.serve import RequestLoop
+    proto = I.request_stream(seed=6, count=2000, rate_per_s=1.0)
+    mean_work = statistics.mean(r.instance.fractal.cells(r.instance.r) * r.n_steps for r in proto)
+    rate = 0.8 * capacity / mean_work
+    reqs = I.request_stream(seed=6, count=n, rate_per_s=rate)
+    loop = RequestLoop(max_slots=64, chunk=25, levels=levels)
+    out = loop.run(reqs)
+    loop.close()
+    out.update({"offered_rate_per_s": rate, "offered_load": "80 % of the batched mix",
+                "mean_work_cell_updates": mean_work})
+    return out
 
 
 def bb_compare(sq, torch, dev, stream, steps=20):
@@ -446,13 +553,20 @@ def bb_compare(sq, torch, dev, stream, steps=20):
     l1.record(stream)
     torch.cuda.synchronize()
     lam = h.cells * steps / (l0.elapsed_time(l1) / 1e3)
+    peak = peaks()[0]
+    compact_frac = 2 * compact / 1e9 / peak     # one step per launch: 2 bytes per cell-update
+    bb_frac = bb_gbs / peak
     out = {"workload": w.name, "r": w.r, "steps": steps,
            "compact_cell_updates_per_s": compact,
-           "compact_l2": "flushed before every step",
+           "compact_l2": "one step per launch, L2 flushed before every launch",
+           "compact_hbm_frac": compact_frac,
            "compact_resident_cell_updates_per_s": resident,
-           "bb_cell_updates_per_s": bb, "bb_box_gbs": bb_gbs,
+           "compact_resident": "200 steps in one call (two steps per launch, state in L2)",
+           "bb_cell_updates_per_s": bb, "bb_box_gbs": bb_gbs, "bb_hbm_frac": bb_frac,
            "lambda_approach_cell_updates_per_s": lam,
            "speedup_compact_over_bb": compact / bb,
+           "speedup_compact_resident_over_bb": resident / bb,
+           "speedup_compact_over_bb_at_equal_hbm_frac": compact / bb * bb_frac / compact_frac,
            "speedup_compact_over_lambda_approach": compact / lam,
            "memory_bytes": {"compact": 2 * h.cells, "bb": 2 * h.side * h.side}}
     h.close()

@@ -2,12 +2,15 @@
 
   python -m paper_2201_00613_gb300.profile_step --level 18 --steps 3 [--kind tiled|alu|tc]
       [--fractal triangle|carpet|vicsek|menger|tetrahedron] [--maps N]
+  python -m paper_2201_00613_gb300.profile_step --batch-mix --steps 12
 
 Initialises the seeded Bernoulli(0.5) state of the fractal at the given level
 and runs `steps` steps, one kernel launch per step (the three-dimensional
 fractals take the per-cell 3-D step; --kind and --maps apply to the planar
-ones).  Used with ncu on a case that is larger than L2 but small enough for a
-multi-pass capture.
+ones).  --batch-mix steps the 256-instance mixed batch (default launch
+shape, no tuning) `steps` times through its CUDA graph instead.  Used with
+ncu on a case that is larger than L2 but small enough for a multi-pass
+capture.
 """
 import argparse
 import sys
@@ -34,6 +37,18 @@ def run_3d(f, level, steps):
         return 0 if st == 0 else 1
 
 
+def run_batch_mix(steps):
+    from .batch import MixedBatch
+    with MixedBatch(I.batch_mix(5, 256)) as mb:
+        mb.run(steps)
+        torch.cuda.synchronize()
+        st = [sq.squeeze_device_status(h.h) for h in mb.handles]
+        grid, threads, smem = sq.squeeze_batch_info(mb.batch)
+        print("batched mix: %d instances, %d cells, %d steps, %d CTAs per step, status %d"
+              % (len(mb.handles), mb.cells, steps, grid, min(st)))
+        return 0 if not any(st) else 1
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--level", type=int, default=18)
@@ -43,7 +58,11 @@ def main(argv=None):
     p.add_argument("--maps", type=int, default=0,
                    help="first run lambda then nu over this many seeded points (with --kind tc "
                         "on the tensor cores, else on the ALU)")
+    p.add_argument("--batch-mix", action="store_true",
+                   help="step the 256-instance mixed batch instead of one fractal")
     a = p.parse_args(argv)
+    if a.batch_mix:
+        return run_batch_mix(a.steps)
     if a.fractal in FRACTALS_3D:
         return run_3d(FRACTALS_3D[a.fractal], a.level, a.steps)
     f = FRACTALS[a.fractal]
