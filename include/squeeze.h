@@ -305,7 +305,9 @@ int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads
                        uint32_t *smem_bytes);
 
 /* squeeze_batch_run -- n_steps steps of every instance on `stream`, one
- * launch per instantiation and step; with graphs on, the launches are captured once
+ * launch per instantiation and step or pair of steps (two steps per launch
+ * where the programs allow; the launch count keeps the parity of n_steps);
+ * with graphs on, the launches are captured once
  * (per distinct n_steps and starting buffer) and replayed.  The batch keeps
  * the step count across calls: every instance's state is in d_buf0 after an
  * even total number of steps since squeeze_batch_create and in d_buf1 after

@@ -9,8 +9,9 @@
 // shared memory.  Each launch's CTAs walk a host-built schedule of (instance,
 // group range) entries, cut so that every CTA gets about the same number of
 // group slots (a group costs about the same whether its 32 tile lanes are
-// full or not).  n_steps steps are captured once into a CUDA graph (the
-// launches of one step, then the next step's, buffers ping-ponging) and
+// full or not).  Launches advance two steps where the items' programs allow
+// (the intermediate step stays in shared memory).  The launches of n_steps
+// steps are captured once into a CUDA graph (buffers ping-ponging) and
 // replayed on later calls.
 #include <stdio.h>
 #include <string.h>
@@ -27,8 +28,9 @@ using namespace sq;
 struct BatchPlan {
   int kind;                 // 27, 25, 8, 16, 64 or 0 (see sq_tile_kind)
   bool life;                // every item of the plan runs B3/S23
+  bool two_step;            // every item's program also runs two steps per launch
   TileLayout lay;           // the maxima of the items' shared-memory needs
-  int threads, grid;
+  int threads, grid, grid2; // CTA size; persistent grids of the one- and two-step kernels
   BatchWork *d_work;
   uint32_t *d_sched;
 };
@@ -134,6 +136,7 @@ int setup(squeeze_batch *b) {
     BatchPlan p{};
     p.kind = kind;
     p.life = true;
+    p.two_step = true;
     bool first = true;
     int own_threads = 0;
     std::vector<uint32_t> idx;
@@ -146,6 +149,7 @@ int setup(squeeze_batch *b) {
       p.lay = first ? l : sq_tile_layout_max(p.lay, l);
       first = false;
       p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
+      p.two_step = p.two_step && sp.two_step;
       own_threads = sp.threads > own_threads ? sp.threads : own_threads;
       idx.push_back(i);
       // a group costs about the same whatever its fill: weigh it by its slots
@@ -154,13 +158,20 @@ int setup(squeeze_batch *b) {
     }
     if (p.lay.smem > 200 * 1024) return SQUEEZE_ERR_UNSUPPORTED;
     p.threads = b->threads ? b->threads : own_threads;
-    const int occ = sq_batch_occupancy(p.life, kind, p.threads, p.lay.smem);
-    if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
-    const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
     uint64_t total_groups = 0;
     for (uint64_t g : groups) total_groups += g;
-    const uint64_t grid = (uint64_t)per_sm * sms;
-    p.grid = (int)(grid < total_groups ? grid : total_groups);
+    // One schedule serves both kernels: it is cut for the smaller grid, and
+    // the other kernel launches that many CTAs too.
+    int grids[2] = {0, 0};
+    for (uint32_t steps = 1; steps <= (p.two_step ? 2u : 1u); ++steps) {
+      const int occ = sq_batch_occupancy(p.life, kind, steps, p.threads, p.lay.smem);
+      if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
+      const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
+      const uint64_t grid = (uint64_t)per_sm * sms;
+      grids[steps - 1] = (int)(grid < total_groups ? grid : total_groups);
+    }
+    p.grid = p.two_step && grids[1] < grids[0] ? grids[1] : grids[0];
+    p.grid2 = p.grid;
     std::vector<BatchWork> work;
     std::vector<uint32_t> start;
     build_schedule(weight, groups, p.grid, work, start);
@@ -192,12 +203,31 @@ int setup(squeeze_batch *b) {
   return SQUEEZE_OK;
 }
 
+// Launches of n_steps steps: two steps per launch where every plan can, with
+// the launch count of n_steps' parity (each launch swaps the buffers; the
+// state after an even number of steps belongs in buffer 0), so an odd
+// number of two-step launches gives one up for two one-step launches.
+void launch_plan(const squeeze_batch *b, uint64_t n_steps, uint64_t &doubles, uint64_t &singles) {
+  bool two = true;
+  for (const BatchPlan &p : b->plans) two = two && p.two_step;
+  doubles = two ? n_steps / 2 : 0;
+  singles = n_steps - 2 * doubles;
+  if (doubles & 1u) {
+    doubles -= 1;
+    singles += 2;
+  }
+}
+
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
-  for (uint64_t t = 0; t < n_steps; ++t) {
+  uint64_t doubles, singles;
+  launch_plan(b, n_steps, doubles, singles);
+  for (uint64_t t = 0; t < doubles + singles; ++t) {
     const uint32_t parity = (uint32_t)((b->parity + t) & 1u);
+    const uint32_t steps = t < doubles ? 2u : 1u;
     for (const BatchPlan &p : b->plans) {
       int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
-                               p.grid, p.threads, p.life, p.kind, parity, st);
+                               steps == 2 ? p.grid2 : p.grid, p.threads, p.life, p.kind, steps,
+                               parity, st);
       if (rc) return rc;
     }
   }

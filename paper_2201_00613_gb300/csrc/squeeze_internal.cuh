@@ -355,12 +355,13 @@ int sq_tiled_describe(const squeeze_handle *h, sq::TiledDev *d, sq::TileSpec *sp
 // Tile-row instantiation of a program: 8 or 16 (rows sharing a slot word),
 // 27, 25 or 64 (their own instantiations), 0 (width taken at run time).
 int sq_tile_kind(const sq::TileSpec &sp);
-// CTAs per SM of the batched kernel instance for this shape (0 if it cannot run).
-int sq_batch_occupancy(bool life, int kind, int threads, uint32_t smem);
+// CTAs per SM of the batched kernel instance for this shape (0 if it cannot
+// run); steps = 1 or 2 per launch.
+int sq_batch_occupancy(bool life, int kind, uint32_t steps, int threads, uint32_t smem);
 int sq_batch_launch(const sq::TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const sq::BatchWork *d_work, const uint32_t *d_sched,
                     const sq::TileLayout &lay, int grid, int threads, bool life, int kind,
-                    uint32_t parity, cudaStream_t st);
+                    uint32_t steps, uint32_t parity, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,

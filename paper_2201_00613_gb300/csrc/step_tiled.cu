@@ -953,14 +953,14 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   settle_abort();
 }
 
-// One step of many instances (each with its own fractal, level and
+// kT steps (1 or 2) of many instances (each with its own fractal, level and
 // buffers) that share one tile-row instantiation, in a single persistent
-// launch.  parity selects the step's input: buffer 0 on even steps, buffer 1
-// on odd ones.  CTA c walks its schedule entries, each a contiguous run of
-// groups of one instance; the instance's description is copied to shared
-// memory for the run (its fields are read throughout the group loop).
-template <bool kLife, int kTW>
-__global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
+// launch.  parity selects the launch's input: buffer 0 or buffer 1.  CTA c
+// walks its schedule entries, each a contiguous run of groups of one
+// instance; the instance's description is copied to shared memory for the
+// run (its fields are read throughout the group loop).
+template <bool kLife, int kTW, int kT>
+__global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
     uint8_t *const *__restrict__ buf1, const BatchWork *__restrict__ work,
     const uint32_t *__restrict__ sched_start, TileLayout lay, uint32_t parity) {
@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_batch_kernel(
     __syncthreads();  // s_dev complete: run_groups reads its sizes before its own first barrier
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
-    run_groups<kLife, kTW, 1>(s_dev, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it);
+    run_groups<kLife, kTW, kT>(s_dev, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it);
   }
   bulk_wait_all();
   settle_abort();
@@ -1014,15 +1014,21 @@ __global__ void build_adjacency_kernel(FracDev f, TiledDev p, uint32_t *__restri
 // ---- host side: the level-L neighbour program ------------------------------
 
 // The batched kernel of one tile-row instantiation (see tiled_kernel_for).
-const void *batch_kernel_for(bool life, int kind) {
+template <bool kLife, int kT>
+const void *batch_kernel_of(int kind) {
   switch (kind) {
-    case 27: return life ? (const void *)step_batch_kernel<true, 27> : (const void *)step_batch_kernel<false, 27>;
-    case 25: return life ? (const void *)step_batch_kernel<true, 25> : (const void *)step_batch_kernel<false, 25>;
-    case 8: return life ? (const void *)step_batch_kernel<true, 8> : (const void *)step_batch_kernel<false, 8>;
-    case 16: return life ? (const void *)step_batch_kernel<true, 16> : (const void *)step_batch_kernel<false, 16>;
-    case 64: return life ? (const void *)step_batch_kernel<true, 64> : (const void *)step_batch_kernel<false, 64>;
-    default: return life ? (const void *)step_batch_kernel<true, 0> : (const void *)step_batch_kernel<false, 0>;
+    case 27: return (const void *)step_batch_kernel<kLife, 27, kT>;
+    case 25: return (const void *)step_batch_kernel<kLife, 25, kT>;
+    case 8: return (const void *)step_batch_kernel<kLife, 8, kT>;
+    case 16: return (const void *)step_batch_kernel<kLife, 16, kT>;
+    case 64: return (const void *)step_batch_kernel<kLife, 64, kT>;
+    default: return (const void *)step_batch_kernel<kLife, 0, kT>;
   }
+}
+
+const void *batch_kernel_for(bool life, int kind, uint32_t steps) {
+  if (steps == 2) return life ? batch_kernel_of<true, 2>(kind) : batch_kernel_of<false, 2>(kind);
+  return life ? batch_kernel_of<true, 1>(kind) : batch_kernel_of<false, 1>(kind);
 }
 
 // The instantiation for a program: rows shared by slot words (rpw 4 or 2) and
@@ -1547,8 +1553,8 @@ int sq_tile_kind(const TileSpec &sp) {
   return 0;
 }
 
-int sq_batch_occupancy(bool life, int kind, int threads, uint32_t smem) {
-  const void *fn = batch_kernel_for(life, kind);
+int sq_batch_occupancy(bool life, int kind, uint32_t steps, int threads, uint32_t smem) {
+  const void *fn = batch_kernel_for(life, kind, steps);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -1559,11 +1565,12 @@ int sq_batch_occupancy(bool life, int kind, int threads, uint32_t smem) {
 
 int sq_batch_launch(const TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const BatchWork *d_work, const uint32_t *d_sched, const TileLayout &lay,
-                    int grid, int threads, bool life, int kind, uint32_t parity, cudaStream_t st) {
+                    int grid, int threads, bool life, int kind, uint32_t steps, uint32_t parity,
+                    cudaStream_t st) {
   TileLayout l = lay;
   void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity};
-  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, kind), dim3(grid), dim3(threads), args, l.smem,
-                           st));
+  SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, kind, steps), dim3(grid), dim3(threads), args,
+                           l.smem, st));
   SQ_CUDA(cudaGetLastError());
   return SQUEEZE_OK;
 }
