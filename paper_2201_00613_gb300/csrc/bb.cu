@@ -12,7 +12,7 @@ namespace sq {
 namespace {
 
 constexpr int kBBRows = 64;      // rows per thread strip
-constexpr int kBBAhead = 4;      // rows whose loads are in flight ahead of the row computed
+constexpr int kBBRing = 8;       // rows in a thread's shared-memory ring (up to 6 in flight)
 constexpr int kBBThreads = 256;  // 16-byte chunks per block along a row
 
 __global__ void bb_init_kernel(FracDev f, uint8_t *__restrict__ grid, uint64_t seed,
@@ -85,93 +85,113 @@ __device__ __forceinline__ uint32_t swar_rule(Rule rule, uint32_t cnt, uint32_t 
 }
 
 struct Row16 {
-  uint32_t a[4];  // alive bits (0x01 per byte)
-  uint32_t h[4];  // horizontal 3-sums
+  uint32_t h[4];  // horizontal 3-sums of the alive bits (one count per byte)
 };
 
 __device__ __forceinline__ void make_row(const uint4 &v, uint32_t left, uint32_t right, Row16 &o) {
-  uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int j = 0; j < 4; ++j) o.a[j] = w[j] & 0x01010101u;
+  uint32_t a[4] = {v.x & 0x01010101u, v.y & 0x01010101u, v.z & 0x01010101u, v.w & 0x01010101u};
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    uint32_t lw = j ? (o.a[j - 1] >> 24) : (left & 1u);
-    uint32_t rw = j < 3 ? (o.a[j + 1] << 24) : ((right & 1u) << 24);
-    uint32_t L = (o.a[j] << 8) | lw;
-    uint32_t R = (o.a[j] >> 8) | rw;
-    o.h[j] = o.a[j] + L + R;
+    uint32_t lw = j ? (a[j - 1] >> 24) : (left & 1u);
+    uint32_t rw = j < 3 ? (a[j + 1] << 24) : ((right & 1u) << 24);
+    uint32_t L = (a[j] << 8) | lw;
+    uint32_t R = (a[j] >> 8) | rw;
+    o.h[j] = a[j] + L + R;
   }
 }
 
-// One row's 16-byte chunk as loaded (zeros off the box) and, for the warp's
-// edge lanes, the byte just outside the warp's 512 bytes on that side.
-struct RowLoad {
-  uint4 v;
-  uint32_t edge;
-};
-
-__device__ __forceinline__ RowLoad load_row(const uint8_t *__restrict__ in, uint32_t n, int64_t y,
-                                            uint32_t chunk, uint32_t nchunks) {
-  RowLoad o;
-  o.v = make_uint4(0, 0, 0, 0);
-  o.edge = 0;
-  const bool in_box = y >= 0 && y < (int64_t)n;
-  const uint8_t *row = in + (uint64_t)(in_box ? y : 0) * n;
-  if (in_box && chunk < nchunks) o.v = __ldg(reinterpret_cast<const uint4 *>(row) + chunk);
-  const unsigned lane = threadIdx.x & 31u;
-  if (in_box && lane == 0 && chunk > 0 && chunk < nchunks) o.edge = __ldg(row + chunk * 16 - 1);
-  if (in_box && lane == 31 && chunk + 1 < nchunks) o.edge = __ldg(row + chunk * 16 + 16);
-  return o;
+// Asynchronous 16-byte global -> shared copies (cp.async, tracked per thread
+// in commit groups; no registers are held while a copy is in flight).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int kN>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kN) : "memory");
 }
 
-// Horizontal sums of a loaded row: the bytes left and right of the chunk come
-// from the neighbouring lanes (the warp's edge lanes loaded theirs).
-__device__ __forceinline__ void row_sums(const RowLoad &l, Row16 &o) {
-  const unsigned lane = threadIdx.x & 31u;
-  uint32_t left = __shfl_up_sync(0xFFFFFFFFu, l.v.w >> 24, 1);
-  uint32_t right = __shfl_down_sync(0xFFFFFFFFu, l.v.x, 1) & 0xFFu;
-  if (lane == 0) left = l.edge;
-  if (lane == 31) right = l.edge;
-  make_row(l.v, left, right, o);
-}
-
-// SWAR step; requires n % 16 == 0.  Block: kBBThreads consecutive chunks of a
-// row; grid.y: strips of kBBRows rows.  The loads of the next kBBAhead rows
-// are in flight while a row is computed (the rows are kept in a register
-// queue indexed at compile time), so each thread keeps several 16-byte loads
-// outstanding; every row is read (kBBRows + 2) / kBBRows times (3 % more than once).
+// SWAR step; requires n % 16 == 0.  Block: kBBThreads consecutive 16-byte
+// chunks of a row; grid.y: strips of kBBRows rows.  Every thread streams its
+// column of chunks through a ring of kBBRing rows in shared memory with
+// cp.async, so up to kBBRing - 2 rows of loads are in flight per thread
+// without holding registers; the warp's edge lanes also stream the chunk just
+// outside the warp for the edge byte.  A thread reads only its own ring
+// slots, so no barrier is needed.  The horizontal 3-sums of the rows above,
+// at and below the row computed roll through registers.  Each row is read
+// (kBBRows + 2) / kBBRows times (3 % more than once).
 template <bool kLife>
 __global__ void __launch_bounds__(kBBThreads) bb_step_swar(uint32_t n, Rule rule,
                                                            const uint8_t *__restrict__ in,
                                                            uint8_t *__restrict__ out) {
+  __shared__ __align__(16) uint4 ring[kBBRing][kBBThreads];
+  __shared__ __align__(16) uint4 edge[kBBRing][kBBThreads / 32][2];
   const uint32_t nchunks = n / 16;
   const uint32_t chunk = blockIdx.x * kBBThreads + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const int64_t y0 = (int64_t)blockIdx.y * kBBRows;
+  const int64_t y_last = y0 + kBBRows;   // the strip's last neighbour row
+  // Row y into ring slot `slot` (zeros off the box, past the row, or past the
+  // strip's rows), as one commit group.
+  auto issue = [&](int64_t y, int slot) {
+    const bool in_box = y >= 0 && y < (int64_t)n && y <= y_last;
+    const uint8_t *row = in + (uint64_t)(in_box ? y : 0) * n;
+    uint4 *dst = &ring[slot][threadIdx.x];
+    if (in_box && chunk < nchunks) cp_async16(dst, row + (uint64_t)chunk * 16);
+    else *dst = make_uint4(0, 0, 0, 0);
+    if (lane == 0) {
+      uint4 *e = &edge[slot][warp][0];
+      if (in_box && chunk > 0 && chunk < nchunks) cp_async16(e, row + (uint64_t)(chunk - 1) * 16);
+      else *e = make_uint4(0, 0, 0, 0);
+    }
+    if (lane == 31) {
+      uint4 *e = &edge[slot][warp][1];
+      if (in_box && chunk + 1 < nchunks) cp_async16(e, row + (uint64_t)(chunk + 1) * 16);
+      else *e = make_uint4(0, 0, 0, 0);
+    }
+    cp_async_commit();
+  };
+  // Horizontal sums of the row in `slot` (edge bytes from the neighbouring
+  // lanes, or from the edge chunks for the warp's edge lanes).
+  auto sums = [&](int slot, uint4 &v, Row16 &o) {
+    v = ring[slot][threadIdx.x];
+    uint32_t left = __shfl_up_sync(0xFFFFFFFFu, v.w >> 24, 1);
+    uint32_t right = __shfl_down_sync(0xFFFFFFFFu, v.x, 1) & 0xFFu;
+    if (lane == 0) left = edge[slot][warp][0].w >> 24;
+    if (lane == 31) right = edge[slot][warp][1].x & 0xFFu;
+    make_row(v, left, right, o);
+  };
+  // row y0 - 1 + k -> slot k % kBBRing
+#pragma unroll
+  for (int k = 0; k < kBBRing; ++k) issue(y0 - 1 + k, k);
+  cp_async_wait<kBBRing - 2>();   // rows y0 - 1 and y0 have landed
   Row16 up, cur;
-  row_sums(load_row(in, n, y0 - 1, chunk, nchunks), up);
-  const RowLoad l0 = load_row(in, n, y0, chunk, nchunks);
-  row_sums(l0, cur);
-  uint4 vcur = l0.v;
-  RowLoad q[kBBAhead];   // q[k] holds row y + 1 + k at the top of step k of a round
+  uint4 vup, vcur;
+  sums(0, vup, up);
+  sums(1, vcur, cur);
+  for (int i0 = 0; i0 < kBBRows; i0 += kBBRing) {
 #pragma unroll
-  for (int k = 0; k < kBBAhead; ++k) q[k] = load_row(in, n, y0 + 1 + k, chunk, nchunks);
-  for (int i0 = 0; i0 < kBBRows; i0 += kBBAhead) {
-#pragma unroll
-    for (int k = 0; k < kBBAhead; ++k) {
+    for (int k = 0; k < kBBRing; ++k) {
       const int64_t y = y0 + i0 + k;
       if (y >= n) break;  // uniform across the block
+      cp_async_wait<kBBRing - 3>();   // row y + 1 has landed
       Row16 dn;
-      row_sums(q[k], dn);
-      const uint4 vnext = q[k].v;
-      // (rows past the strip's last neighbour row are not needed: not loaded)
-      if (i0 + k + 1 + kBBAhead <= kBBRows) q[k] = load_row(in, n, y + 1 + kBBAhead, chunk, nchunks);
+      uint4 vnext;
+      sums((k + 2) % kBBRing, vnext, dn);
+      issue(y - 1 + kBBRing, k % kBBRing);   // the slot of row y - 1 is free now
       if (chunk < nchunks) {
         const uint32_t w[4] = {vcur.x, vcur.y, vcur.z, vcur.w};
         uint32_t o[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const uint32_t cnt = up.h[j] + dn.h[j] + cur.h[j] - cur.a[j];
-          const uint32_t next = swar_rule<kLife>(rule, cnt, cur.a[j]);
+          const uint32_t alive = w[j] & 0x01010101u;
+          const uint32_t cnt = up.h[j] + dn.h[j] + cur.h[j] - alive;
+          const uint32_t next = swar_rule<kLife>(rule, cnt, alive);
           o[j] = (w[j] & 0x02020202u) | (next & (w[j] >> 1) & 0x01010101u);
         }
         reinterpret_cast<uint4 *>(out + (uint64_t)y * n)[chunk] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -181,6 +201,7 @@ __global__ void __launch_bounds__(kBBThreads) bb_step_swar(uint32_t n, Rule rule
       vcur = vnext;
     }
   }
+  cp_async_wait<0>();   // nothing left in flight when the block ends
 }
 
 __global__ void bb_gather_kernel(FracDev f, const uint8_t *__restrict__ grid,

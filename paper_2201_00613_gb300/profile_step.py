@@ -3,12 +3,14 @@
   python -m paper_2201_00613_gb300.profile_step --level 18 --steps 3 [--kind tiled|alu|tc]
       [--fractal triangle|carpet|vicsek|menger|tetrahedron] [--maps N]
   python -m paper_2201_00613_gb300.profile_step --batch-mix --steps 12
+  python -m paper_2201_00613_gb300.profile_step --bb --level 15 --steps 3
 
 Initialises the seeded Bernoulli(0.5) state of the fractal at the given level
 and runs `steps` steps, one kernel launch per step (the three-dimensional
 fractals take the per-cell 3-D step; --kind and --maps apply to the planar
 ones).  --batch-mix steps the 256-instance mixed batch (default launch
-shape, no tuning) `steps` times through its CUDA graph instead.  Used with
+shape, no tuning) `steps` times through its CUDA graph instead; --bb runs
+the same-GPU bounding-box step on the level's expanded box.  Used with
 ncu on a case that is larger than L2 but small enough for a multi-pass
 capture.
 """
@@ -49,6 +51,18 @@ def run_batch_mix(steps):
         return 0 if not any(st) else 1
 
 
+def run_bb(f, level, steps):
+    with sq.Handle(f, level) as h:
+        g0 = torch.empty(h.side * h.side, dtype=torch.uint8, device="cuda")
+        g1 = torch.empty_like(g0)
+        sq.squeeze_bb_init(h.h, g0, 3, I.p_q24(0.5))
+        sq.squeeze_bb_step(h.h, g0, g1, steps)
+        torch.cuda.synchronize()
+        st = sq.squeeze_device_status(h.h)
+        print("bounding box level %d side %d steps %d status %d" % (level, h.side, steps, st))
+        return 0 if st == 0 else 1
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--level", type=int, default=18)
@@ -60,9 +74,12 @@ def main(argv=None):
                         "on the tensor cores, else on the ALU)")
     p.add_argument("--batch-mix", action="store_true",
                    help="step the 256-instance mixed batch instead of one fractal")
+    p.add_argument("--bb", action="store_true", help="the bounding-box step instead")
     a = p.parse_args(argv)
     if a.batch_mix:
         return run_batch_mix(a.steps)
+    if a.bb:
+        return run_bb(FRACTALS[a.fractal], a.level, a.steps)
     if a.fractal in FRACTALS_3D:
         return run_3d(FRACTALS_3D[a.fractal], a.level, a.steps)
     f = FRACTALS[a.fractal]
