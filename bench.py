@@ -619,13 +619,16 @@ def workload_compare(sq, torch, dev, stream):
 
 
 def nbb3d_compare(sq, torch, dev, stream, steps=4):
-    """Three-dimensional fractals: the per-cell step (26 neighbours, B5/S45) on
-    the Menger sponge at level 7 (1.28e9 cells) and the Sierpinski tetrahedron
-    at level 15 (1.07e9 cells); hbm_frac counts two bytes per cell-update
-    against the copy bandwidth."""
+    """Three-dimensional fractals (26 neighbours, B5/S45): the Sierpinski
+    tetrahedron at level 15 (1.07e9 cells) with the bit-sliced tile kernel and
+    with the per-cell kernel, the Menger sponge at level 7 (1.28e9 cells, rows
+    of 20 cells: per-cell kernel only); hbm_frac counts two bytes per
+    cell-update against the copy bandwidth."""
     out = {"unit": "cell-updates/s", "steps": steps, "rule": "B5/S45, 26 neighbours"}
-    for f, r in ((I.MENGER, 7), (I.TETRA, 15)):
+    for f, r, kernel in ((I.TETRA, 15, "tiled"), (I.TETRA, 15, "per_cell"), (I.MENGER, 7, "auto")):
         with sq.Handle3(f, r) as h:
+            if kernel == "per_cell":
+                sq.squeeze_3d_set_tiled_level(h.h, 0)
             a = torch.empty(h.cells, dtype=torch.uint8, device=dev)
             b = torch.empty_like(a)
             sq.squeeze_3d_init_bernoulli(h.h, a, 3, I.p_q24(0.3), stream)
@@ -639,10 +642,11 @@ def nbb3d_compare(sq, torch, dev, stream, steps=4):
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / 1e3
             rate = h.cells * steps / t
-            out["%s_r%d" % (f.name, r)] = {"cells": h.cells, "ms_per_step": 1e3 * t / steps,
-                                           "cell_updates_per_s": rate,
-                                           "hbm_frac": 2 * rate / 1e9 / peaks()[0],
-                                           "status": sq.squeeze_3d_device_status(h.h)}
+            level = sq.squeeze_3d_tiled_level(h.h)
+            out["%s_r%d_%s" % (f.name, r, "tiled" if level else "per_cell")] = {
+                "cells": h.cells, "ms_per_step": 1e3 * t / steps, "cell_updates_per_s": rate,
+                "hbm_frac": 2 * rate / 1e9 / peaks()[0], "tile_level": level,
+                "status": sq.squeeze_3d_device_status(h.h)}
             del a, b
     torch.cuda.empty_cache()
     return out

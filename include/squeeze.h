@@ -479,14 +479,32 @@ int squeeze_3d_nu(const squeeze_3d_handle *h, const int32_t *d_xyz, uint64_t *d_
 int squeeze_3d_init_bernoulli(const squeeze_3d_handle *h, uint8_t *d_state, uint64_t seed,
                               uint32_t p_q24, void *stream);
 
-/* squeeze_3d_step -- n_steps steps, one thread per compact cell: lambda's
- * digits, each neighbour by the carry walk of nu from the cell's own digits,
- * the rule into the other buffer.  Result in d_buf0 when n_steps is even,
+/* squeeze_3d_step -- n_steps steps: the bit-sliced tile kernel where it
+ * applies (squeeze_3d_set_tiled_level), else one thread per compact cell:
+ * lambda's digits, each neighbour by the carry walk of nu from the cell's own
+ * digits, the rule into the other buffer.  Result in d_buf0 when n_steps is even,
  * d_buf1 when odd; the buffers (k^r bytes each) must differ.  A neighbour
  * index past the state (impossible for a valid handle) is skipped and
  * latches DEVICE_BOUNDS. */
 int squeeze_3d_step(squeeze_3d_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                     void *stream);
+
+/* squeeze_3d_set_tiled_level -- which kernel squeeze_3d_step runs.  The
+ * bit-sliced tile kernel (level-L sub-replicas of k^L cells as tiles, a
+ * host-built 26-neighbour program per level, the adjacent tile in each of the
+ * 26 directions from a per-handle table, 32 tiles per CTA bit-sliced into
+ * 32-bit words) takes levels whose tile rows hold 8 or 16 cells
+ * (k^ceil(L/3) = 8 or 16), with W_x a multiple of 16 and 16-byte aligned
+ * buffers; otherwise (the Menger sponge, say) the per-cell kernel runs.
+ *   level 0      the per-cell kernel always;
+ *   0 < L <= r   the tile kernel at level L (UNSUPPORTED if it cannot take L).
+ * By default the largest level with at most 1024 slot words is used.  The
+ * results are the same bit for bit. */
+int squeeze_3d_set_tiled_level(squeeze_3d_handle *h, uint32_t level);
+
+/* squeeze_3d_tiled_level -- the level the tile kernel runs at (aligned
+ * buffers), or 0 when squeeze_3d_step runs the per-cell kernel. */
+int squeeze_3d_tiled_level(const squeeze_3d_handle *h);
 
 /* squeeze_3d_device_status -- as squeeze_device_status, for a 3-D handle. */
 int squeeze_3d_device_status(squeeze_3d_handle *h, int *status);

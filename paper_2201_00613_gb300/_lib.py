@@ -124,6 +124,8 @@ _SIGS = {
     "squeeze_3d_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                          ctypes.c_void_p], ctypes.c_int),
     "squeeze_3d_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "squeeze_3d_set_tiled_level": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
+    "squeeze_3d_tiled_level": ([ctypes.c_void_p], ctypes.c_int),
     "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_set_wait_limit": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
     "squeeze_set_fault_injection": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
@@ -432,6 +434,17 @@ def squeeze_3d_init_bernoulli(h, d_state, seed: int, p_q24: int, stream=None):
 def squeeze_3d_step(h, d_buf0, d_buf1, n_steps: int, stream=None):
     _check(_load().squeeze_3d_step(h, _ptr(d_buf0), _ptr(d_buf1), n_steps, _stream(stream)),
            "squeeze_3d_step")
+
+
+def squeeze_3d_set_tiled_level(h, level: int) -> None:
+    _check(_load().squeeze_3d_set_tiled_level(h, level), "squeeze_3d_set_tiled_level")
+
+
+def squeeze_3d_tiled_level(h) -> int:
+    rc = _load().squeeze_3d_tiled_level(h)
+    if rc < 0:
+        raise SqueezeError(rc, "squeeze_3d_tiled_level")
+    return rc
 
 
 def squeeze_3d_device_status(h) -> int:

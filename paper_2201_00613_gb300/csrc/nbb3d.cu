@@ -19,6 +19,8 @@ struct squeeze_3d_handle {
   Frac3Dev f;
   int *d_status;   // device status word (SQUEEZE_OK / DEVICE_*)
   int device;
+  int tiled_level;        // -1: the default level; 0: the per-cell kernel only; else L
+  Tile3Program *tiled;    // the tile kernel's program, built on the first step
 };
 
 namespace {
@@ -168,6 +170,7 @@ int squeeze_3d_create(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r
   squeeze_3d_handle *h = new (std::nothrow) squeeze_3d_handle;
   if (!h) return SQUEEZE_ERR_OOM;
   memset(h, 0, sizeof(*h));
+  h->tiled_level = -1;
   h->f = f;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
@@ -184,6 +187,7 @@ int squeeze_3d_create(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r
 int squeeze_3d_destroy(squeeze_3d_handle *h) {
   if (!h) return SQUEEZE_OK;
   cudaError_t e = cudaDeviceSynchronize();
+  sq3_tile_free(h->tiled);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
   return e == cudaSuccess ? SQUEEZE_OK : sq_cuda_fail(e);
@@ -210,6 +214,12 @@ int squeeze_3d_set_rule(squeeze_3d_handle *h, uint32_t birth, uint32_t survive) 
 int squeeze_3d_set_neighbourhood(squeeze_3d_handle *h, uint32_t mask) {
   if (!h || mask >= (1u << 27) || (mask & (1u << 13))) return SQUEEZE_ERR_INVALID_ARG;
   h->f.nbhd = mask;
+  if (h->tiled) {   // the program's references depend on the neighbourhood
+    const cudaError_t e = cudaDeviceSynchronize();
+    sq3_tile_free(h->tiled);
+    h->tiled = nullptr;
+    if (e != cudaSuccess) return sq_cuda_fail(e);
+  }
   return SQUEEZE_OK;
 }
 
@@ -244,10 +254,35 @@ int squeeze_3d_init_bernoulli(const squeeze_3d_handle *h, uint8_t *d_state, uint
   return SQUEEZE_OK;
 }
 
+// The level the tile kernel runs at for this handle, or 0 for the per-cell kernel.
+static uint32_t tiled_level_of(const squeeze_3d_handle *h) {
+  if (h->tiled_level == 0) return 0;
+  return h->tiled_level > 0 ? (uint32_t)h->tiled_level : sq3_tile_default_level(h->f);
+}
+
 int squeeze_3d_step(squeeze_3d_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                     void *stream) {
   if (!h || !d_buf0 || !d_buf1 || d_buf0 == d_buf1) return SQUEEZE_ERR_INVALID_ARG;
+  if (!n_steps) return SQUEEZE_OK;
   uint8_t *a = d_buf0, *b = d_buf1;
+  const uint32_t L = tiled_level_of(h);
+  if (L && !(((uintptr_t)d_buf0 | (uintptr_t)d_buf1) & 15u)) {
+    if (!h->tiled) {
+      const int rc = sq3_tile_prepare(h->f, L, h->device, &h->tiled);
+      if (rc && (rc != SQUEEZE_ERR_UNSUPPORTED || h->tiled_level > 0)) return rc;
+    }
+    if (h->tiled) {
+      for (uint64_t i = 0; i < n_steps; ++i) {
+        const int rc = sq3_tile_launch(h->tiled, h->f.birth, h->f.survive, h->d_status, a, b,
+                                       (cudaStream_t)stream);
+        if (rc) return rc;
+        uint8_t *tmp = a;
+        a = b;
+        b = tmp;
+      }
+      return SQUEEZE_OK;
+    }
+  }
   const unsigned grid = grid_for(h->f.cells, kThreads);
   for (uint64_t i = 0; i < n_steps; ++i) {
     step3_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(h->f, a, b, h->d_status);
@@ -257,6 +292,28 @@ int squeeze_3d_step(squeeze_3d_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint
     b = tmp;
   }
   return SQUEEZE_OK;
+}
+
+int squeeze_3d_set_tiled_level(squeeze_3d_handle *h, uint32_t level) {
+  if (!h || level > h->f.r) return SQUEEZE_ERR_INVALID_ARG;
+  if (level) {
+    uint32_t TX, TY, TZ, slots;
+    uint64_t box;
+    if (!sq3_tile_shape(h->f, level, TX, TY, TZ, slots, box)) return SQUEEZE_ERR_UNSUPPORTED;
+  }
+  if (h->tiled) {
+    const cudaError_t e = cudaDeviceSynchronize();
+    sq3_tile_free(h->tiled);
+    h->tiled = nullptr;
+    if (e != cudaSuccess) return sq_cuda_fail(e);
+  }
+  h->tiled_level = (int)level;
+  return SQUEEZE_OK;
+}
+
+int squeeze_3d_tiled_level(const squeeze_3d_handle *h) {
+  if (!h) return SQUEEZE_ERR_INVALID_ARG;
+  return (int)tiled_level_of(h);
 }
 
 int squeeze_3d_device_status(squeeze_3d_handle *h, int *status) {

@@ -202,3 +202,16 @@ __host__ __device__ inline bool neighbour3(const Frac3Dev &f, const Tables3 &t, 
 }
 
 }  // namespace sq3
+
+// ---- the bit-sliced tile kernel (tile3d.cu), host side ----------------------
+struct Tile3Program;
+// Tile shape of level L (rows of 8 or 16 cells, W_x a multiple of 16, at most
+// 4096 slot words), or false when the tile kernel cannot take this level.
+bool sq3_tile_shape(const sq3::Frac3Dev &f, uint32_t L, uint32_t &TX, uint32_t &TY,
+                    uint32_t &TZ, uint32_t &slots, uint64_t &box);
+// The largest level whose program has at most 1024 slot words, or 0 if none.
+uint32_t sq3_tile_default_level(const sq3::Frac3Dev &f);
+int sq3_tile_prepare(const sq3::Frac3Dev &f, uint32_t L, int device, Tile3Program **out);
+void sq3_tile_free(Tile3Program *p);
+int sq3_tile_launch(const Tile3Program *p, uint32_t birth, uint32_t survive, int *status,
+                    const uint8_t *in, uint8_t *out, cudaStream_t st);

@@ -5,6 +5,21 @@
 #include "nbb3d.cu"
 
 int sq_cuda_fail(cudaError_t) { return SQUEEZE_ERR_CUDA; }   // never reached: no CUDA calls here
+// The tile kernel (tile3d.cu) is not part of this host library; the step
+// entry point that would reach it is never called here.
+bool sq3_tile_shape(const Frac3Dev &, uint32_t, uint32_t &, uint32_t &, uint32_t &, uint32_t &,
+                    uint64_t &) {
+  return false;
+}
+uint32_t sq3_tile_default_level(const Frac3Dev &) { return 0; }
+int sq3_tile_prepare(const Frac3Dev &, uint32_t, int, Tile3Program **) {
+  return SQUEEZE_ERR_UNSUPPORTED;
+}
+void sq3_tile_free(Tile3Program *) {}
+int sq3_tile_launch(const Tile3Program *, uint32_t, uint32_t, int *, const uint8_t *, uint8_t *,
+                    cudaStream_t) {
+  return SQUEEZE_ERR_UNSUPPORTED;
+}
 
 namespace {
 void tables_of(const Frac3Dev &f, Tables3 &t) {
