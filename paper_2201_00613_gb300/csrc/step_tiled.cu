@@ -766,7 +766,9 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         for (int k = 0; k < kR; ++k)
           if (vrow(u0, k) < VR) yw[vrow(u0, k) * 32u + lane] = nx[k];
       }
-      for (uint32_t i = warp * 32u + lane; i < p.nhalo1; i += nw * 32u)
+      // (the first ring from the last warp down: warp 0 issues the loads and the
+      // low warps gather halo bytes, so the last warp has the least other work)
+      for (uint32_t i = (nw - 1u - warp) * 32u + lane; i < p.nhalo1; i += nw * 32u)
         yw[slots + i] = rule_at<kLife>(p, wbase, slots + i) & emask[hdir[i]];
       __syncthreads();   // step 1 complete; every warp is done reading X
       rbase = smem + win_bytes;
