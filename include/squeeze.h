@@ -159,9 +159,9 @@ int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t s
  * kernel.  A level whose tiled program would not fit is UNSUPPORTED for
  * TILED (AUTO falls back to the per-cell ALU kernel only when no tile level
  * fits at all).  squeeze_last_step_info() tells which kernel AUTO chose.
- * The tiled kernel advances two steps per launch where its program allows
- * (the state of the intermediate step stays in shared memory), so d_buf1
- * holds no particular step afterwards; the result is the same bit for bit. */
+ * The tiled kernel advances up to four steps per launch where its program
+ * allows (the intermediate states stay in shared memory), so d_buf1 holds no
+ * particular step afterwards; the result is the same bit for bit. */
 int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                  int kind, void *stream);
 
@@ -169,12 +169,13 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
  * call ran: *kind = SQUEEZE_STEP_TILED, SQUEEZE_MAP_ALU or SQUEEZE_MAP_TC_BF16
  * (0 before the first step), so that a caller of AUTO can see a fall-back to
  * the per-cell ALU kernel (misaligned buffers; about 300x slower than the
- * tiled kernel); *launches = kernel launches it enqueued; *two_step = how
- * many of them advanced two steps (the tiled kernel runs n steps as two-step
- * launches where it can: n = 100 is 50 launches).  Any pointer may be NULL.
- * INVALID_ARG for a null handle. */
+ * tiled kernel); *launches = kernel launches it enqueued; *two_step and
+ * *four_step = how many of them advanced two and four steps (the tiled kernel
+ * runs n steps as four-, two- and one-step launches whose count has the
+ * parity of n: n = 100 is 24 four-step and 2 two-step launches).  Any pointer
+ * may be NULL.  INVALID_ARG for a null handle. */
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
-                           uint64_t *two_step);
+                           uint64_t *two_step, uint64_t *four_step);
 
 /* squeeze_step_host -- the same run from and to HOST memory: copies h_in
  * (k^r bytes, ideally pinned) into d_buf0, runs n_steps, copies the result to
@@ -305,8 +306,9 @@ int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads
                        uint32_t *smem_bytes);
 
 /* squeeze_batch_run -- n_steps steps of every instance on `stream`, one
- * launch per instantiation and step or pair of steps (two steps per launch
- * where the programs allow; the launch count keeps the parity of n_steps);
+ * launch per instantiation and step, pair or quadruple of steps (up to four
+ * steps per launch where the programs allow; the launch count keeps the
+ * parity of n_steps);
  * with graphs on, the launches are captured once
  * (per distinct n_steps and starting buffer) and replayed.  The batch keeps
  * the step count across calls: every instance's state is in d_buf0 after an

@@ -130,8 +130,8 @@ _SIGS = {
     "squeeze_set_wait_limit": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
     "squeeze_set_fault_injection": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "squeeze_last_step_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
-                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
-                               ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "squeeze_last_cuda_error": ([], ctypes.c_char_p),
 }
@@ -468,11 +468,14 @@ def squeeze_set_fault_injection(h, flags: int) -> None:
 
 
 def squeeze_last_step_info(h) -> tuple:
-    """(kind, launches, two-step launches) of the handle's last squeeze_step."""
-    kind, launches, two = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+    """(kind, launches, two-step launches, four-step launches) of the handle's
+    last squeeze_step."""
+    kind, launches = ctypes.c_int(), ctypes.c_uint64()
+    two, four = ctypes.c_uint64(), ctypes.c_uint64()
     _check(_load().squeeze_last_step_info(h, ctypes.byref(kind), ctypes.byref(launches),
-                                          ctypes.byref(two)), "squeeze_last_step_info")
-    return int(kind.value), int(launches.value), int(two.value)
+                                          ctypes.byref(two), ctypes.byref(four)),
+           "squeeze_last_step_info")
+    return int(kind.value), int(launches.value), int(two.value), int(four.value)
 
 
 def squeeze_status_string(code: int) -> str:

@@ -28,9 +28,9 @@ using namespace sq;
 struct BatchPlan {
   int kind;                 // 27, 25, 8, 16, 64 or 0 (see sq_tile_kind)
   bool life;                // every item of the plan runs B3/S23
-  bool two_step;            // every item's program also runs two steps per launch
+  uint32_t passes;          // steps per launch every item's program allows (1, 2 or 4)
   TileLayout lay;           // the maxima of the items' shared-memory needs
-  int threads, grid, grid2; // CTA size; persistent grids of the one- and two-step kernels
+  int threads, grid;        // CTA size; persistent grid (the same for every steps per launch)
   BatchWork *d_work;
   uint32_t *d_sched;
 };
@@ -136,7 +136,7 @@ int setup(squeeze_batch *b) {
     BatchPlan p{};
     p.kind = kind;
     p.life = true;
-    p.two_step = true;
+    p.passes = 4;
     bool first = true;
     int own_threads = 0;
     std::vector<uint32_t> idx;
@@ -149,7 +149,7 @@ int setup(squeeze_batch *b) {
       p.lay = first ? l : sq_tile_layout_max(p.lay, l);
       first = false;
       p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
-      p.two_step = p.two_step && sp.two_step;
+      p.passes = sp.passes < p.passes ? sp.passes : p.passes;
       own_threads = sp.threads > own_threads ? sp.threads : own_threads;
       idx.push_back(i);
       // a group costs about the same whatever its fill: weigh it by its slots
@@ -160,18 +160,17 @@ int setup(squeeze_batch *b) {
     p.threads = b->threads ? b->threads : own_threads;
     uint64_t total_groups = 0;
     for (uint64_t g : groups) total_groups += g;
-    // One schedule serves both kernels: it is cut for the smaller grid, and
-    // the other kernel launches that many CTAs too.
-    int grids[2] = {0, 0};
-    for (uint32_t steps = 1; steps <= (p.two_step ? 2u : 1u); ++steps) {
+    // One schedule serves every steps-per-launch kernel: it is cut for the
+    // smallest of their grids, and each launches that many CTAs.
+    p.grid = 0;
+    for (uint32_t steps = 1; steps <= p.passes; steps *= 2) {
       const int occ = sq_batch_occupancy(p.life, kind, steps, p.threads, p.lay.smem);
       if (occ < 1) return SQUEEZE_ERR_UNSUPPORTED;
       const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
       const uint64_t grid = (uint64_t)per_sm * sms;
-      grids[steps - 1] = (int)(grid < total_groups ? grid : total_groups);
+      const int g = (int)(grid < total_groups ? grid : total_groups);
+      p.grid = p.grid == 0 || g < p.grid ? g : p.grid;
     }
-    p.grid = p.two_step && grids[1] < grids[0] ? grids[1] : grids[0];
-    p.grid2 = p.grid;
     std::vector<BatchWork> work;
     std::vector<uint32_t> start;
     build_schedule(weight, groups, p.grid, work, start);
@@ -203,31 +202,20 @@ int setup(squeeze_batch *b) {
   return SQUEEZE_OK;
 }
 
-// Launches of n_steps steps: two steps per launch where every plan can, with
-// the launch count of n_steps' parity (each launch swaps the buffers; the
-// state after an even number of steps belongs in buffer 0), so an odd
-// number of two-step launches gives one up for two one-step launches.
-void launch_plan(const squeeze_batch *b, uint64_t n_steps, uint64_t &doubles, uint64_t &singles) {
-  bool two = true;
-  for (const BatchPlan &p : b->plans) two = two && p.two_step;
-  doubles = two ? n_steps / 2 : 0;
-  singles = n_steps - 2 * doubles;
-  if (doubles & 1u) {
-    doubles -= 1;
-    singles += 2;
-  }
-}
-
+// Launches of n_steps steps: up to four steps per launch where every plan
+// can, with a launch count of n_steps' parity (each launch swaps the
+// buffers; the state after an even number of steps belongs in buffer 0).
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
-  uint64_t doubles, singles;
-  launch_plan(b, n_steps, doubles, singles);
-  for (uint64_t t = 0; t < doubles + singles; ++t) {
+  uint32_t passes = 4;
+  for (const BatchPlan &p : b->plans) passes = p.passes < passes ? p.passes : passes;
+  uint64_t quads, doubles, singles;
+  sq_launch_plan(n_steps, passes, quads, doubles, singles);
+  for (uint64_t t = 0; t < quads + doubles + singles; ++t) {
     const uint32_t parity = (uint32_t)((b->parity + t) & 1u);
-    const uint32_t steps = t < doubles ? 2u : 1u;
+    const uint32_t steps = t < quads ? 4u : (t < quads + doubles ? 2u : 1u);
     for (const BatchPlan &p : b->plans) {
       int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
-                               steps == 2 ? p.grid2 : p.grid, p.threads, p.life, p.kind, steps,
-                               parity, st);
+                               p.grid, p.threads, p.life, p.kind, steps, parity, st);
       if (rc) return rc;
     }
   }

@@ -229,25 +229,18 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     if (rc) return rc;
   }
   h->last_kind = kind;
-  // The tiled kernel runs two steps per launch where its program allows:
-  // n = 2p + s steps as p two-step launches and s one-step ones, except that
-  // the launch count must have the parity of n (every launch swaps the
-  // buffers, and the result belongs in d_buf[n & 1]), so an odd p gives one
-  // of its two-step launches up for two one-step launches.
-  uint64_t doubles = 0, singles = n_steps;
-  if (kind == SQUEEZE_STEP_TILED && sq_tiled_two_step(h)) {
-    doubles = n_steps / 2;
-    singles = n_steps % 2;
-    if (doubles & 1u) {
-      doubles -= 1;
-      singles += 2;
-    }
-  }
+  // The tiled kernel runs up to four steps per launch where its program
+  // allows (sq_launch_plan: four-, two- and one-step launches whose count has
+  // the parity of n_steps, since every launch swaps the buffers and the
+  // result belongs in d_buf[n_steps & 1]).
+  uint64_t quads = 0, doubles = 0, singles = n_steps;
+  if (kind == SQUEEZE_STEP_TILED) sq_launch_plan(n_steps, sq_tiled_passes(h), quads, doubles, singles);
   uint8_t *a = d_buf0, *b = d_buf1;
-  for (uint64_t t = 0; t < doubles + singles; ++t) {
+  for (uint64_t t = 0; t < quads + doubles + singles; ++t) {
     int rc;
+    const uint32_t steps = t < quads ? 4u : (t < quads + doubles ? 2u : 1u);
     switch (kind) {
-      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, t < doubles ? 2u : 1u, st); break;
+      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, steps, st); break;
       case SQUEEZE_MAP_TC_BF16: rc = sq_launch_step_tc(h, a, b, st); break;
       default: rc = sq_launch_step_alu(h, a, b, st); break;
     }
@@ -256,8 +249,9 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     a = b;
     b = tmp;
   }
-  h->last_launches = doubles + singles;
+  h->last_launches = quads + doubles + singles;
   h->last_two_step = doubles;
+  h->last_four_step = quads;
   return SQUEEZE_OK;
 }
 
@@ -340,11 +334,12 @@ int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_
 }
 
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
-                           uint64_t *two_step_launches) {
+                           uint64_t *two_step_launches, uint64_t *four_step_launches) {
   if (check_handle(h)) return SQUEEZE_ERR_INVALID_ARG;
   if (kind) *kind = h->last_kind;
   if (launches) *launches = h->last_launches;
   if (two_step_launches) *two_step_launches = h->last_two_step;
+  if (four_step_launches) *four_step_launches = h->last_four_step;
   return SQUEEZE_OK;
 }
 

@@ -211,8 +211,8 @@ struct TiledDev {
   const uint8_t *halo_dir;   // nhalo direction indices
   const uint32_t *adj;       // ndirs x tiles adjacent tile indices (~0: none)
   int *status;
-  uint32_t nhalo1;           // first-ring halo words (the rest, if any, are the second ring)
-  uint32_t halo2_start[10];  // second-ring words of direction j: [halo2_start[j], halo2_start[j+1])
+  uint32_t ring_end[5];        // halo words of rings 1..k: [0, ring_end[k])
+  uint32_t ring_start[3][10];  // words of ring k + 2 in direction j
   uint64_t wait_ns;          // a bulk-copy wait gives up after this many ns
   uint32_t fault;            // SQUEEZE_FAULT_* (test hook), normally 0
   uint32_t pad_;
@@ -236,17 +236,16 @@ struct TileLayout {
 // tables live.
 struct TileSpec {
   uint32_t L, TW, TH, rpw, cells, slots, nhalo, ndirs, dir_mask;
-  uint32_t nhalo1;     // halo words the one-step program reads (the first ring)
-  uint32_t two_step;   // 1: the program also runs two steps per launch (second ring built)
+  uint32_t passes;     // steps one launch of the program can advance: 1, 2 or 4
+  uint32_t ring_end[5];      // halo words of rings 1..k: [0, ring_end[k]) (ring_end[passes] = nhalo)
   uint8_t dir_list[9];
   uint32_t halo_start[10];   // first-ring words of direction j: [halo_start[j], halo_start[j+1])
-  uint32_t halo2_start[10];  // second-ring words of direction j (indices >= nhalo1)
+  uint32_t ring_start[3][10];  // words of ring k + 2 in direction j: [ring_start[k][j], ring_start[k][j+1])
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
   size_t smem;
-  int grid, threads;   // grid of the B3/S23 instantiation (one step per launch)
-  int grid_rule;       // grid of the generic-rule instantiation
-  int grid2, grid2_rule;   // the same for the two-step instantiations
+  int threads;
+  int grid[3][2];      // persistent grid per steps-per-launch (1, 2, 4) and rule (generic, B3/S23)
 };
 
 // Capacities needed to build the program of one tile level.
@@ -266,10 +265,10 @@ struct TileBuild {
   uint32_t *halo_off;
   uint8_t *halo_dir;
   uint64_t box_cap, cells_cap, slots_cap, halo_cap;
-  // 1: also build the second halo ring and the first ring's references, so
-  // that the program runs two steps per launch (refs and refs16 then need
-  // (slots + halo_cap) * 8 entries).
-  uint32_t two_step;
+  // Steps per launch the program is built for (1, 2 or 4): for P > 1 the halo
+  // rings 2..P are built too, and references for rings 1..P-1 (refs and
+  // refs16 then need (slots + halo_cap) * 8 entries).
+  uint32_t passes;
 };
 
 // One entry of a batched launch's schedule: CTA c processes entries
@@ -306,6 +305,7 @@ struct squeeze_handle {
   int last_kind;             // kind the last squeeze_step ran (0 before the first)
   uint64_t last_launches;    // kernel launches of that call
   uint64_t last_two_step;    // of which two steps per launch
+  uint64_t last_four_step;   // and four steps per launch
 };
 
 // Error plumbing and descriptor validation (handle.cu).
@@ -328,11 +328,16 @@ int sq_launch_init(const squeeze_handle *h, uint8_t *state, uint64_t seed, uint3
 int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                        cudaStream_t st);
 int sq_tiled_prepare(squeeze_handle *h);
-// One launch of the handle's tiled program: steps = 1, or 2 when the
-// program was built for two steps per launch (sq_tiled_two_step).
+// One launch of the handle's tiled program: steps = 1, 2 or 4, at most the
+// passes the program was built for (sq_tiled_passes).
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                          uint32_t steps, cudaStream_t st);
-bool sq_tiled_two_step(const squeeze_handle *h);
+uint32_t sq_tiled_passes(const squeeze_handle *h);
+// Launches of n steps at up to `passes` steps each (4, 2 and 1), with a launch
+// count of n's parity (every launch swaps the buffers; the result belongs in
+// buffer n & 1).
+void sq_launch_plan(uint64_t n, uint32_t passes, uint64_t &quads, uint64_t &doubles,
+                    uint64_t &singles);
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
 int sq_tiled_default_level_for(const sq::FracDev &f);
@@ -347,7 +352,7 @@ sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint3
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
 int sq_tile_build_adjacency(const sq::FracDev &f, const sq::TiledDev &d, uint32_t *adj,
                             cudaStream_t st);
-// One launch of the tiled kernel: steps = 1, or 2 (program built with two_step).
+// One launch of the tiled kernel: steps = 1, 2 or 4 (at most the program's passes).
 int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t *in,
                    uint8_t *out, uint32_t steps, cudaStream_t st);
 // The handle's prepared tiled program (sq_tiled_prepare first).

@@ -49,6 +49,7 @@ namespace sq {
 namespace {
 
 constexpr int kTiledMaxThreads = 384;
+constexpr uint32_t kTiledPasses = 4;            // steps per launch the handle's program is built for
 constexpr size_t kTiledSmemCap = 56 * 1024;     // default level: 4 CTAs per SM
 constexpr size_t kTiledSmemLimit = 200 * 1024;  // any level: one CTA per SM
 
@@ -543,15 +544,15 @@ __device__ __forceinline__ uint32_t rule_at(const TiledDev &p, const unsigned ch
 // the groups this CTA has processed (it selects buffers and mbarrier phases)
 // and carries over from one call to the next.
 //
-// kT = 2 (two steps per launch): the packed words of a group go to word
-// buffer X (buffer 0), together with both halo rings and the per-direction
-// masks of which adjacent tiles exist; after the barrier a first rule pass
-// writes step 1 of every slot and of the first halo ring to buffer Y (a
-// first-ring cell of a missing tile stays dead), and after a second barrier
-// the usual rule pass computes step 2 from Y and writes it back.  X is free
-// again once every warp has passed the second barrier, and Y once every warp
-// has passed the next group's first barrier, so the two buffers need no
-// double-buffering by group.
+// kT = 2 or 4 (steps per launch): the packed words of a group go to word
+// buffer X (buffer 0), together with halo rings 1..kT and the per-direction
+// masks of which adjacent tiles exist.  After the barrier, rule pass t
+// (t = 1 .. kT - 1) writes step t of every slot and of rings 1..kT-t from one
+// buffer into the other (X -> Y, Y -> X, X -> Y; a ring cell of a missing
+// tile stays dead), each followed by a barrier, and the final rule pass
+// computes step kT from Y and writes it back.  X's last reader is pass kT - 1
+// and Y's the final pass, so the next group can fill X after the final pass
+// and Y after its own first barrier: two buffers suffice for an even kT.
 template <bool kLife, int kTW, int kT>
 __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &lay,
                                            const uint8_t *__restrict__ in,
@@ -594,8 +595,8 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   // this instance's output is not valid either, so its status says so.
   if (tid == 0 && cta_aborted()) flag(p.status, SQUEEZE_ERR_DEVICE_TIMEOUT);
   for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
-  if constexpr (kT == 2)
-    for (uint32_t i = tid; i < p.nhalo1; i += nthreads) hdir[i] = p.halo_dir[i];
+  if constexpr (kT > 1)
+    for (uint32_t i = tid; i < p.ring_end[kT - 1]; i += nthreads) hdir[i] = p.halo_dir[i];
   if (tid == 0) {
     reinterpret_cast<uint32_t *>(smem)[slots + nhalo] = 0u;  // "no neighbour" words
     reinterpret_cast<uint32_t *>(smem + win_bytes)[slots + nhalo] = 0u;
@@ -616,10 +617,10 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   for (uint64_t g = g_first; g < g_end; g += g_stride, ++it) {
     const uint32_t b = it & 1u;
     // Word buffer of the packed input: by group parity for one step per
-    // launch; buffer 0 (X) for two.
-    unsigned char *wbase = smem + (kT == 2 ? 0u : b) * win_bytes;
+    // launch; buffer 0 (X) for more.
+    unsigned char *wbase = smem + (kT > 1 ? 0u : b) * win_bytes;
     uint32_t *win = reinterpret_cast<uint32_t *>(wbase);
-    uint32_t *emask = win + slots + nhalo + 1;   // kT = 2: which adjacent tiles exist, per direction
+    uint32_t *emask = win + slots + nhalo + 1;   // kT > 1: which adjacent tiles exist, per direction
     uint8_t *stage = stage_base + b * stage_bytes;
     const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
     uint32_t *stage32w = reinterpret_cast<uint32_t *>(stage);
@@ -659,9 +660,11 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         }
       }
       if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
-      if constexpr (kT == 2) {
-        gather_halo<kHaloBatch>(p, TW, t_cur, p.halo2_start[warp], p.halo2_start[warp + 1], hoff,
-                                win + slots, in, lane);
+      if constexpr (kT > 1) {
+#pragma unroll
+        for (int k = 0; k < kT - 1; ++k)   // rings 2 .. kT
+          gather_halo<kHaloBatch>(p, TW, t_cur, p.ring_start[k][warp], p.ring_start[k][warp + 1],
+                                  hoff, win + slots, in, lane);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, t_cur != ~0u);
         if (lane == 0) emask[warp] = m;
       }
@@ -670,9 +673,11 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       const uint32_t t = adjacent_of(p, G, j, lane);
       gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff, win + slots,
                               in, lane);
-      if constexpr (kT == 2) {
-        gather_halo<kHaloBatch>(p, TW, t, p.halo2_start[j], p.halo2_start[j + 1], hoff,
-                                win + slots, in, lane);
+      if constexpr (kT > 1) {
+#pragma unroll
+        for (int k = 0; k < kT - 1; ++k)
+          gather_halo<kHaloBatch>(p, TW, t, p.ring_start[k][j], p.ring_start[k][j + 1], hoff,
+                                  win + slots, in, lane);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, t != ~0u);
         if (lane == 0) emask[j] = m;
       }
@@ -753,25 +758,30 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
 
-    // kT = 2: step 1 of the own slot rows and of the first halo ring, X -> Y.
+    // kT > 1: steps 1 .. kT-1 of the own slot rows and of the halo rings that
+    // the later steps still need, alternating between X and Y.
     const unsigned char *rbase = wbase;   // the words the final rule pass reads
-    if constexpr (kT == 2) {
-      uint32_t *yw = reinterpret_cast<uint32_t *>(smem + win_bytes);
-      for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
-        uint32_t nx[kR];
+    if constexpr (kT > 1) {
+#pragma unroll 1
+      for (int t = 1; t < kT; ++t) {
+        const unsigned char *src = smem + (t & 1 ? 0u : win_bytes);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(smem + (t & 1 ? win_bytes : 0u));
+        for (uint32_t u0 = warp; u0 < NU; u0 += kU * nw) {
+          uint32_t nx[kR];
 #pragma unroll
-        for (int k = 0; k < kR; ++k)
-          nx[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, wbase, vrow(u0, k) * 32u + lane) : 0u;
+          for (int k = 0; k < kR; ++k)
+            nx[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, src, vrow(u0, k) * 32u + lane) : 0u;
 #pragma unroll
-        for (int k = 0; k < kR; ++k)
-          if (vrow(u0, k) < VR) yw[vrow(u0, k) * 32u + lane] = nx[k];
+          for (int k = 0; k < kR; ++k)
+            if (vrow(u0, k) < VR) dst[vrow(u0, k) * 32u + lane] = nx[k];
+        }
+        // (rings from the last warp down: warp 0 issues the loads and the low
+        // warps gather halo bytes, so the last warps have the least other work)
+        for (uint32_t i = (nw - 1u - warp) * 32u + lane; i < p.ring_end[kT - t]; i += nw * 32u)
+          dst[slots + i] = rule_at<kLife>(p, src, slots + i) & emask[hdir[i]];
+        __syncthreads();   // step t complete; every warp is done reading src
       }
-      // (the first ring from the last warp down: warp 0 issues the loads and the
-      // low warps gather halo bytes, so the last warp has the least other work)
-      for (uint32_t i = (nw - 1u - warp) * 32u + lane; i < p.nhalo1; i += nw * 32u)
-        yw[slots + i] = rule_at<kLife>(p, wbase, slots + i) & emask[hdir[i]];
-      __syncthreads();   // step 1 complete; every warp is done reading X
-      rbase = smem + win_bytes;
+      rbase = smem + win_bytes;   // Y: kT is even
     }
 
     // Rule, inverse transpose and write-back of the own rows.
@@ -983,6 +993,7 @@ const void *batch_kernel_of(int kind) {
 }
 
 const void *batch_kernel_for(bool life, int kind, uint32_t steps) {
+  if (steps == 4) return life ? batch_kernel_of<true, 4>(kind) : batch_kernel_of<false, 4>(kind);
   if (steps == 2) return life ? batch_kernel_of<true, 2>(kind) : batch_kernel_of<false, 2>(kind);
   return life ? batch_kernel_of<true, 1>(kind) : batch_kernel_of<false, 1>(kind);
 }
@@ -1001,9 +1012,12 @@ const void *tiled_kernel_of(uint32_t TW, uint32_t rpw) {
 }
 
 const void *tiled_kernel_for(bool life, uint32_t TW, uint32_t rpw, uint32_t steps) {
+  if (steps == 4) return life ? tiled_kernel_of<true, 4>(TW, rpw) : tiled_kernel_of<false, 4>(TW, rpw);
   if (steps == 2) return life ? tiled_kernel_of<true, 2>(TW, rpw) : tiled_kernel_of<false, 2>(TW, rpw);
   return life ? tiled_kernel_of<true, 1>(TW, rpw) : tiled_kernel_of<false, 1>(TW, rpw);
 }
+
+int steps_index(uint32_t steps) { return steps == 4 ? 2 : (steps == 2 ? 1 : 0); }
 
 
 uint64_t ipow(uint64_t b, uint32_t e) {
@@ -1135,8 +1149,9 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   d.status = status;
   d.wait_ns = kDefaultWaitNs;
   d.fault = 0;
-  d.nhalo1 = sp.nhalo1;
-  for (int i = 0; i < 10; ++i) d.halo2_start[i] = sp.halo2_start[i];
+  for (int i = 0; i < 5; ++i) d.ring_end[i] = sp.ring_end[i];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 10; ++i) d.ring_start[k][i] = sp.ring_start[k][i];
   return d;
 }
 
@@ -1180,9 +1195,14 @@ uint32_t count_halo(const FracDev &f, uint32_t L) {
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
-                 z.box, z.cells, z.slots, z.halo, 1u};
+                 z.box, z.cells, z.slots, z.halo, kTiledPasses};
   TileSpec sp;
-  if (sq_tile_build(f, L, B, sp) != SQUEEZE_OK) return 0xFFFFu;   // too large to build
+  int rc = sq_tile_build(f, L, B, sp);
+  for (uint32_t fewer = kTiledPasses / 2; rc == SQUEEZE_ERR_UNSUPPORTED && fewer >= 1; fewer /= 2) {
+    B.passes = fewer;
+    rc = sq_tile_build(f, L, B, sp);
+  }
+  if (rc != SQUEEZE_OK) return 0xFFFFu;   // too large to build
   return sp.nhalo;
 }
 
@@ -1212,16 +1232,15 @@ void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
 // local lambda and its inverse over the level-L box, 8 references per slot
 // (local slot, halo word or the zero word), halo words sorted by direction.
 //
-// With B.two_step the program also serves launches that run two steps: the
-// first ring of halo cells (the cells of adjacent blocks that are neighbours
-// of the tile's cells) gets references of its own, to the tile's slots, the
-// first ring and a second ring (their neighbours outside the tile and the
-// first ring), so that a launch can advance the tile and the first ring by
-// one step in shared memory and then the tile by a second step.  Halo words
-// are numbered first ring first ([0, nhalo1), sorted by direction), then the
-// second ring ([nhalo1, nhalo), sorted by direction); one-step launches read
-// the first ring only.  Word array: slots | first ring | second ring | zero
-// word | 9 words of per-direction "adjacent tile exists" masks.
+// With B.passes = P > 1 the program also serves launches that run up to P
+// steps: ring 1 of halo cells (the cells of adjacent blocks that neighbour the
+// tile's cells), ring 2 (their neighbours outside the tile and ring 1), ...,
+// ring P are built, and rings 1 .. P-1 get references of their own, so that a
+// launch can advance the tile and rings 1..P-t by step t in shared memory
+// and the tile alone by step P.  Halo words are numbered ring by ring, each
+// ring sorted by direction: ring k is [ring_end[k-1], ring_end[k]); a launch
+// of fewer steps reads the first rings only.  Word array: slots | rings |
+// zero word | 9 words of per-direction "adjacent tile exists" masks.
 int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp) {
   if (L == 0 || L > f.r) return SQUEEZE_ERR_UNSUPPORTED;
   uint64_t TW64 = ipow(f.k, (L + 1) / 2), TH64 = ipow(f.k, L / 2);
@@ -1243,15 +1262,18 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
     inv[(size_t)B.Y[c] * side + B.X[c]] = (int32_t)c;
   }
   auto slot_of = [&](uint32_t c) { return tile_slot_of(c, TW, rpw, wpr); };
-  const uint32_t kNone = 0xFFFFFFFFu, kFull = 0xFFFFFFFEu;
+  const uint32_t kNone = 0xFFFFFFFFu, kFull = 0xFFFFFFFEu, kFar = 0xFFFFFFFDu;
   uint32_t *refs = B.refs;
   uint32_t nhalo = 0;
   // Reference to the point (qx, qy) of the expanded plane, relative to the
   // tile's own level-L box: a local slot, slots + a halo index (a halo cell is
-  // registered on first sight), kNone for a hole, or kFull when the halo list
-  // is full.  Points up to two cells outside the box lie in the 8 adjacent
-  // boxes, since a box is at least 2 cells wide.
+  // registered on first sight), kNone for a hole, kFull when the halo list
+  // is full, or kFar for a point beyond the 8 adjacent boxes (a ring deeper
+  // than the box is wide).
   auto ref_of = [&](int64_t qx, int64_t qy) -> uint32_t {
+    if (qx < -(int64_t)side || qy < -(int64_t)side || qx >= 2 * (int64_t)side ||
+        qy >= 2 * (int64_t)side)
+      return kFar;
     const int bx = qx < 0 ? -1 : (qx >= side ? 1 : 0), by = qy < 0 ? -1 : (qy >= side ? 1 : 0);
     const int64_t lxp = qx - (int64_t)bx * side, lyp = qy - (int64_t)by * side;
     const int32_t target = inv[(size_t)lyp * side + lxp];
@@ -1275,7 +1297,7 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
       if (d == 4) continue;
       uint32_t ref = kNone;
       if ((f.nbhd >> d) & 1u) ref = ref_of(px + d % 3 - 1, py + d / 3 - 1);
-      if (ref == kFull) return false;
+      if (ref == kFull || ref == kFar) return false;
       row[k8++] = ref;
     }
     return true;
@@ -1283,23 +1305,25 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   for (size_t i = 0; i < (size_t)slots * 8; ++i) refs[i] = kNone;   // slots without a cell
   for (uint32_t c = 0; c < cells; ++c)
     if (!fill_refs(B.X[c], B.Y[c], refs + (size_t)slot_of(c) * 8)) return SQUEEZE_ERR_UNSUPPORTED;
-  const uint32_t n1 = nhalo;
-  if (B.two_step) {
-    // References of the first ring (its neighbours may add the second ring).
-    for (uint32_t i = 0; i < n1; ++i) {
+  const uint32_t P = B.passes == 4 ? 4u : (B.passes == 2 ? 2u : 1u);
+  uint32_t ends[5] = {0, nhalo, 0, 0, 0};
+  for (uint32_t k = 1; k < P; ++k) {
+    // References of ring k (its neighbours outside the tile and rings 1..k
+    // make up ring k + 1).
+    for (uint32_t i = ends[k - 1]; i < ends[k]; ++i) {
       const uint64_t key = B.halo_key[i];
       const uint32_t d = (uint32_t)(key >> 32), t = (uint32_t)key;
       const int64_t px = (int64_t)B.X[t] + ((int)(d % 3) - 1) * (int64_t)side;
       const int64_t py = (int64_t)B.Y[t] + ((int)(d / 3) - 1) * (int64_t)side;
       if (!fill_refs(px, py, refs + (size_t)(slots + i) * 8)) return SQUEEZE_ERR_UNSUPPORTED;
     }
+    ends[k + 1] = nhalo;
   }
-  // Sort each ring by direction (then local cell) and renumber: the first
-  // ring takes [0, n1), the second [n1, nhalo).
+  for (uint32_t k = P + 1; k <= 4; ++k) ends[k] = nhalo;
+  // Sort each ring by direction (then local cell) and renumber within it.
   for (uint32_t i = 0; i < nhalo; ++i) B.order[i] = i;
   auto by_key = [&](uint32_t x, uint32_t y) { return B.halo_key[x] < B.halo_key[y]; };
-  std::sort(B.order, B.order + n1, by_key);
-  std::sort(B.order + n1, B.order + nhalo, by_key);
+  for (uint32_t k = 1; k <= P; ++k) std::sort(B.order + ends[k - 1], B.order + ends[k], by_key);
   for (uint32_t i = 0; i < nhalo; ++i) B.rank[B.order[i]] = i;
   uint64_t *sorted = B.halo_sorted;
   for (uint32_t i = 0; i < nhalo; ++i) sorted[B.rank[i]] = B.halo_key[i];
@@ -1313,10 +1337,9 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   };
   for (uint32_t c = 0; c < slots; ++c)
     for (uint32_t d = 0; d < 8; ++d) B.refs16[(size_t)c * 8 + d] = enc(refs[(size_t)c * 8 + d]);
-  if (B.two_step)
-    for (uint32_t i = 0; i < n1; ++i)
-      for (uint32_t d = 0; d < 8; ++d)
-        B.refs16[(size_t)(slots + B.rank[i]) * 8 + d] = enc(refs[(size_t)(slots + i) * 8 + d]);
+  for (uint32_t i = 0; i < ends[P - 1]; ++i)   // rings with references, in sorted order
+    for (uint32_t d = 0; d < 8; ++d)
+      B.refs16[(size_t)(slots + B.rank[i]) * 8 + d] = enc(refs[(size_t)(slots + i) * 8 + d]);
   uint32_t dir_mask = 0;
   for (uint32_t i = 0; i < nhalo; ++i) dir_mask |= 1u << (uint32_t)(sorted[i] >> 32);
   memset(&sp, 0, sizeof(sp));
@@ -1326,17 +1349,21 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
       dir_index[d] = (uint8_t)sp.ndirs;
       sp.dir_list[sp.ndirs++] = (uint8_t)d;
     }
-  for (uint32_t j = 0; j < 10; ++j) sp.halo2_start[j] = n1;
+  // per ring and direction: the range of its words ([ends[k-1], ends[k]) sorted by direction)
+  uint32_t *starts[4] = {sp.halo_start, sp.ring_start[0], sp.ring_start[1], sp.ring_start[2]};
+  for (uint32_t k = 0; k < 4; ++k)
+    for (uint32_t j = 0; j < 10; ++j) starts[k][j] = ends[k];
   for (uint32_t i = 0; i < nhalo; ++i) {
     uint32_t d = (uint32_t)(sorted[i] >> 32), lc = (uint32_t)sorted[i];
     B.halo_dir[i] = dir_index[d];
     B.halo_off[i] = (lc / TW) * f.W + lc % TW;
-    (i < n1 ? sp.halo_start : sp.halo2_start)[dir_index[d] + 1] = i + 1;
+    uint32_t k = 0;
+    while (i >= ends[k + 1]) ++k;
+    starts[k][dir_index[d] + 1] = i + 1;
   }
-  for (uint32_t j = 1; j <= 9; ++j) {
-    if (sp.halo_start[j] < sp.halo_start[j - 1]) sp.halo_start[j] = sp.halo_start[j - 1];
-    if (sp.halo2_start[j] < sp.halo2_start[j - 1]) sp.halo2_start[j] = sp.halo2_start[j - 1];
-  }
+  for (uint32_t k = 0; k < 4; ++k)
+    for (uint32_t j = 1; j <= 9; ++j)
+      if (starts[k][j] < starts[k][j - 1]) starts[k][j] = starts[k][j - 1];
   sp.L = L;
   sp.TW = TW;
   sp.TH = TH;
@@ -1344,8 +1371,8 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.cells = cells;
   sp.slots = slots;
   sp.nhalo = nhalo;
-  sp.nhalo1 = n1;
-  sp.two_step = B.two_step ? 1u : 0u;
+  sp.passes = P;
+  for (uint32_t k = 0; k <= 4; ++k) sp.ring_end[k] = ends[k];
   sp.dir_mask = dir_mask;
   sp.tiles_x = f.W / TW;
   sp.tiles_y = f.H / TH;
@@ -1377,7 +1404,7 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return sq_cuda_fail(e);
-  for (uint32_t steps = 1; steps <= (sp.two_step ? 2u : 1u); ++steps)
+  for (uint32_t steps = 1; steps <= sp.passes; steps *= 2)
     for (int life = 0; life < 2; ++life) {
       const void *fn = tiled_kernel_for(life != 0, sp.TW, sp.rpw, steps);
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
@@ -1387,9 +1414,7 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
       if (e != cudaSuccess) return sq_cuda_fail(e);
       if (n < 1) return SQUEEZE_ERR_UNSUPPORTED;
       const uint64_t grid = (uint64_t)n * sms;
-      const int g = (int)(grid < sp.groups ? grid : sp.groups);
-      if (steps == 1) (life ? sp.grid : sp.grid_rule) = g;
-      else (life ? sp.grid2 : sp.grid2_rule) = g;
+      sp.grid[steps_index(steps)][life] = (int)(grid < sp.groups ? grid : sp.groups);
     }
   return SQUEEZE_OK;
 }
@@ -1405,12 +1430,12 @@ int sq_tile_build_adjacency(const FracDev &f, const TiledDev &d, uint32_t *adj, 
 int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uint8_t *out,
                    uint32_t steps, cudaStream_t st) {
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
-  if (steps != 1 && !(steps == 2 && sp.two_step)) return SQUEEZE_ERR_INVALID_ARG;
+  if ((steps != 1 && steps != 2 && steps != 4) || steps > sp.passes) return SQUEEZE_ERR_INVALID_ARG;
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
   TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
   void *args[] = {&dd, &lay, &in, &out};
-  const int grid = steps == 2 ? (life ? sp.grid2 : sp.grid2_rule) : (life ? sp.grid : sp.grid_rule);
+  const int grid = sp.grid[steps_index(steps)][life ? 1 : 0];
   SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw, steps), dim3(grid),
                            dim3(sp.threads), args, sp.smem, st));
   SQ_CUDA(cudaGetLastError());
@@ -1435,10 +1460,14 @@ int sq_tiled_prepare(squeeze_handle *h) {
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
-                 z.box, z.cells, z.slots, z.halo, 1u};
+                 z.box, z.cells, z.slots, z.halo, kTiledPasses};
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
   int rc = sq_tile_build(f, L, B, p->spec);
+  for (uint32_t fewer = kTiledPasses / 2; rc == SQUEEZE_ERR_UNSUPPORTED && fewer >= 1; fewer /= 2) {
+    B.passes = fewer;   // e.g. the rings do not fit the 16-bit word offsets
+    rc = sq_tile_build(f, L, B, p->spec);
+  }
   if (rc == SQUEEZE_OK) rc = sq_tile_launch_config(p->spec, h->device);
   if (rc != SQUEEZE_OK) {
     delete p;
@@ -1446,7 +1475,8 @@ int sq_tiled_prepare(squeeze_handle *h) {
   }
   const TileSpec &sp = p->spec;
   uint32_t nhalo = sp.nhalo;
-  const size_t ref_bytes = (size_t)(sp.slots + sp.nhalo1) * 16;   // slots, then the first ring
+  // slots, then the rings with references (1 .. passes - 1)
+  const size_t ref_bytes = (size_t)(sp.slots + sp.ring_end[sp.passes - 1]) * 16;
   cudaError_t e = cudaMalloc(&p->d_refs, ref_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
@@ -1489,7 +1519,23 @@ int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *ou
   return sq_tile_launch(d, p->spec, in, out, steps, st);
 }
 
-bool sq_tiled_two_step(const squeeze_handle *h) { return h->tiled && h->tiled->spec.two_step; }
+uint32_t sq_tiled_passes(const squeeze_handle *h) { return h->tiled ? h->tiled->spec.passes : 1u; }
+
+void sq_launch_plan(uint64_t n, uint32_t passes, uint64_t &quads, uint64_t &doubles,
+                    uint64_t &singles) {
+  quads = passes >= 4 ? n / 4 : 0;
+  doubles = passes >= 2 ? (n - 4 * quads) / 2 : 0;
+  singles = n - 4 * quads - 2 * doubles;
+  if ((quads + doubles) & 1u) {     // launches must have the parity of n (= that of singles)
+    if (quads) {
+      quads -= 1;
+      doubles += 2;
+    } else {
+      doubles -= 1;
+      singles += 2;
+    }
+  }
+}
 
 int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
   const TiledProgram *p = h->tiled;

@@ -50,12 +50,12 @@ def ptr(a):
     return a.ctypes.data_as(P)
 
 
-def program(lib, f, r, L, nbhd, two_step=0):
+def program(lib, f, r, L, nbhd, passes=1):
     off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
     caps = np.zeros(3, dtype=np.uint64)
     assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
     cells, slots, halo = (int(v) for v in caps)
-    info = np.zeros(9, dtype=np.uint32)
+    info = np.zeros(14, dtype=np.uint32)
     slot = np.zeros(cells, dtype=np.uint32)
     X = np.zeros(cells, dtype=np.uint32)
     Y = np.zeros(cells, dtype=np.uint32)
@@ -63,13 +63,17 @@ def program(lib, f, r, L, nbhd, two_step=0):
     halo_off = np.zeros(halo, dtype=np.uint32)
     halo_dir = np.zeros(halo, dtype=np.uint8)
     dir_list = np.zeros(9, dtype=np.uint8)
-    rc = lib.tile_program(f.s, f.k, ptr(off), r, L, nbhd, two_step, ptr(info), ptr(slot), ptr(X),
+    rc = lib.tile_program(f.s, f.k, ptr(off), r, L, nbhd, passes, ptr(info), ptr(slot), ptr(X),
                           ptr(Y), ptr(refs16), ptr(halo_off), ptr(halo_dir), ptr(dir_list))
+    if rc and passes > 1:
+        return None     # rings deeper than the box is wide: the library builds fewer passes
     assert rc == 0, rc
-    TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs, nhalo1 = (int(v) for v in info)
-    nrows = nslot + (nhalo1 if two_step else 0)
+    TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs, npass = (int(v) for v in info[:9])
+    ring_end = [int(v) for v in info[9:14]]
+    nrows = nslot + ring_end[npass - 1]
     return dict(TW=TW, TH=TH, rpw=rpw, wpr=wpr, cells=ncell, slots=nslot, nhalo=nhalo,
-                nhalo1=nhalo1, slot=slot[:ncell].astype(np.int64), X=X[:ncell].astype(np.int64),
+                passes=npass, ring_end=ring_end, nhalo1=ring_end[1],
+                slot=slot[:ncell].astype(np.int64), X=X[:ncell].astype(np.int64),
                 Y=Y[:ncell].astype(np.int64), refs=(refs16[:nrows * 8] // 4).astype(np.int64),
                 halo_off=halo_off[:nhalo].astype(np.int64), halo_dir=halo_dir[:nhalo],
                 dir_list=dir_list[:ndirs])
@@ -130,13 +134,13 @@ def emulate_step(f, r, L, prog, state, adj, rule=oracle.B3S23):
     return out
 
 
-def emulate_two_steps(f, r, L, prog, state, adj, rule=oracle.B3S23, mask=True):
-    """Two steps of every tile through the two-step program, as one launch
-    runs them: the tile's words and both halo rings from the state, step 1
-    of the slots and of the first ring (a first-ring cell of a missing tile
-    stays dead), then step 2 of the tile from those."""
+def emulate_passes(f, r, L, prog, state, adj, rule=oracle.B3S23, mask=True):
+    """P = prog["passes"] steps of every tile through the program, as one
+    launch runs them: the tile's words and halo rings 1..P from the state,
+    then for t = 1 .. P-1 step t of the slots and of rings 1..P-t (a ring cell
+    of a missing tile stays dead), then step P of the tile from those."""
     W = oracle.compact_shape(f, r)[1]
-    TW, slots, n1 = prog["TW"], prog["slots"], prog["nhalo1"]
+    TW, slots, P = prog["TW"], prog["slots"], prog["passes"]
     bases = tile_bases(f, r, prog)
     loff = (np.arange(prog["cells"]) // TW) * W + np.arange(prog["cells"]) % TW
     nw = slots + prog["nhalo"] + 1
@@ -155,11 +159,14 @@ def emulate_two_steps(f, r, L, prog, state, adj, rule=oracle.B3S23, mask=True):
         own = words[:, rows]
         return np.where(own == 1, (rule[1] >> count) & 1, (rule[0] >> count) & 1)
 
-    y = np.zeros_like(x)
-    y[:, prog["slot"]] = rule_rows(x, prog["slot"])
-    ring = np.arange(slots, slots + n1)
-    y[:, ring] = rule_rows(x, ring) & (exists[:, :n1] if mask else 1)
-    nxt = rule_rows(y, prog["slot"])
+    for t in range(1, P):
+        n = prog["ring_end"][P - t]
+        y = np.zeros_like(x)
+        y[:, prog["slot"]] = rule_rows(x, prog["slot"])
+        ring = np.arange(slots, slots + n)
+        y[:, ring] = rule_rows(x, ring) & (exists[:, :n] if mask else 1)
+        x = y
+    nxt = rule_rows(x, prog["slot"])
     out = np.zeros_like(state)
     out[bases[:, None] + loff[None, :]] = nxt
     return out
@@ -204,12 +211,17 @@ TWO_STEP_RULES = [oracle.B3S23, ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),   # 
                   ((1 << 0) | (1 << 3), (1 << 2) | (1 << 3))]                 # B03/S23: birth at 0
 
 
+@pytest.mark.parametrize("passes", [2, 4])
 @pytest.mark.parametrize("f,r,L,nbhd", CASES,
                          ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CASES])
-def test_two_step_program_equals_two_oracle_steps(lib, f, r, L, nbhd):
-    prog = program(lib, f, r, L, nbhd, two_step=1)
+def test_multi_step_program_equals_oracle_steps(lib, f, r, L, nbhd, passes):
+    prog = program(lib, f, r, L, nbhd, passes=passes)
     one = program(lib, f, r, L, nbhd)
-    # the first ring, its order and the slots' references are the one-step program's
+    if prog is None:
+        assert f.s ** L < passes    # the only reason the builder refuses more passes
+        return
+    assert prog["passes"] == passes
+    # ring 1, its order and the slots' references are the one-step program's
     assert prog["nhalo1"] == one["nhalo"] and prog["nhalo"] >= prog["nhalo1"]
     assert np.array_equal(prog["halo_off"][:prog["nhalo1"]], one["halo_off"])
     zero1, zero2 = one["slots"] + one["nhalo"], prog["slots"] + prog["nhalo"]
@@ -221,19 +233,22 @@ def test_two_step_program_equals_two_oracle_steps(lib, f, r, L, nbhd):
     adj = library_adjacency(lib, f, r, L, prog)
     for rule in TWO_STEP_RULES:
         want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
-            m, oracle.compact_to_box(f, r, state), 2, rule, nbhd))
-        assert np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule), want), rule
+            m, oracle.compact_to_box(f, r, state), passes, rule, nbhd))
+        assert np.array_equal(emulate_passes(f, r, L, prog, state, adj, rule), want), rule
 
 
-def test_two_step_emulation_catches_a_dropped_existence_mask(lib):
-    # Without the mask a first-ring cell of a missing tile can be born (rule
-    # B03 births at 0 neighbours) and feed step 2: the result must then differ.
+def test_multi_step_emulation_catches_a_dropped_existence_mask(lib):
+    # Without the mask a ring cell of a missing tile can be born (rule B03
+    # births at 0 neighbours) and feed the next step: the result must differ.
     f, r, L = I.TRIANGLE, 8, 3
-    prog = program(lib, f, r, L, oracle.MOORE, two_step=1)
-    adj = library_adjacency(lib, f, r, L, prog)
-    state = I.bernoulli_bytes(7, f.k ** r, 0.45)
-    rule = TWO_STEP_RULES[2]
-    want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
-        oracle.member_grid(f, r), oracle.compact_to_box(f, r, state), 2, rule, oracle.MOORE))
-    assert np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule), want)
-    assert not np.array_equal(emulate_two_steps(f, r, L, prog, state, adj, rule, mask=False), want)
+    for passes in (2, 4):
+        prog = program(lib, f, r, L, oracle.MOORE, passes=passes)
+        adj = library_adjacency(lib, f, r, L, prog)
+        state = I.bernoulli_bytes(7, f.k ** r, 0.45)
+        rule = TWO_STEP_RULES[2]
+        want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(
+            oracle.member_grid(f, r), oracle.compact_to_box(f, r, state), passes, rule,
+            oracle.MOORE))
+        assert np.array_equal(emulate_passes(f, r, L, prog, state, adj, rule), want)
+        assert not np.array_equal(emulate_passes(f, r, L, prog, state, adj, rule, mask=False),
+                                  want)

@@ -48,14 +48,15 @@ int tile_sizes(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t 
   return SQUEEZE_OK;
 }
 
-// The level-L program: info = (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs,
-// nhalo1); per local cell its slot and local expanded position; per slot (and,
-// for a two-step program, per first-ring halo word after them) 8 byte offsets
-// into the word array (slots, then halo words, then a zero word); per halo
-// word its offset from the adjacent tile's base and its direction index into
+// The level-L program for up to `passes` steps per launch (1, 2 or 4): info =
+// (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs, passes, ring_end[0..4]); per
+// local cell its slot and local expanded position; per slot (and per halo word
+// of rings 1 .. passes-1 after them) 8 byte offsets into the word array
+// (slots, then halo words ring by ring, then a zero word); per halo word its
+// offset from the adjacent tile's base and its direction index into
 // dir_list.  refs16 needs (slots + halo) * 8 entries.
 int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L,
-                 uint32_t nbhd, uint32_t two_step, uint32_t *info, uint32_t *slot, uint32_t *X,
+                 uint32_t nbhd, uint32_t passes, uint32_t *info, uint32_t *slot, uint32_t *X,
                  uint32_t *Y, uint16_t *refs16, uint32_t *halo_off, uint8_t *halo_dir,
                  uint8_t *dir_list) {
   FracDev f;
@@ -82,13 +83,15 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   B.cells_cap = z.cells;
   B.slots_cap = z.slots;
   B.halo_cap = z.halo;
-  B.two_step = two_step;
+  B.passes = passes;
   TileSpec sp;
   const int rc = sq_tile_build(f, L, B, sp);
   if (rc) return rc;
   const uint32_t wpr = sp.TW == 64 ? 2u : 1u;
-  const uint32_t v[9] = {sp.TW, sp.TH, sp.rpw, wpr, sp.cells, sp.slots, sp.nhalo, sp.ndirs,
-                         sp.nhalo1};
+  const uint32_t v[14] = {sp.TW,          sp.TH,          sp.rpw,         wpr,
+                          sp.cells,       sp.slots,       sp.nhalo,       sp.ndirs,
+                          sp.passes,      sp.ring_end[0], sp.ring_end[1], sp.ring_end[2],
+                          sp.ring_end[3], sp.ring_end[4]};
   memcpy(info, v, sizeof(v));
   for (uint32_t c = 0; c < sp.cells; ++c) {
     slot[c] = tile_slot_of(c, sp.TW, sp.rpw, wpr);
