@@ -2,7 +2,7 @@
 
 One bench step = one run of the workload: 100 synchronous B3/S23 steps over
 the 3,486,784,401-cell compact state (Bernoulli(0.5), seed 3), as launches of
-the bit-sliced tile kernel that each advance up to four steps (24 of four
+the bit-sliced tile kernel that each advance up to eight steps (12 of eight
 and 2 of two; the intermediate steps stay in shared memory).  The state (2 x 3.49 GB) is far larger than
 L2, so no flush is needed between launches.
 
@@ -41,7 +41,9 @@ from paper_2201_00613_gb300 import inputs as I  # noqa: E402
 WORKLOAD = I.TRIANGLE_R20
 COMPARE = I.TRIANGLE_R16
 METRIC = "cell-updates/s"
-STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2201_00613_gb300", "csrc", "step_tiled.cu")
+# the hot kernel's source: its device code and the host code that builds its program
+STEP_KERNEL_SRC = [os.path.join(ROOT, "paper_2201_00613_gb300", "csrc", f)
+                   for f in ("tile2d.cuh", "bitslice.cuh", "step_tiled.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 CPU_SAMPLE_LEVEL = 14   # oracle sample: the level-14 top-left sub-replica of the r = 20 box
 CPU_SAMPLE_STEPS = 800   # about 15 s of work on 16 cores
@@ -70,9 +72,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def file_sha(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def file_sha(paths):
+    """sha256 (16 hex digits) of the concatenation of the files."""
+    h = hashlib.sha256()
+    for path in ([paths] if isinstance(paths, str) else paths):
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def traffic_per_launch():
@@ -352,7 +358,7 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1))
     clocks = clk.summary()
     status = sq.squeeze_device_status(h.h)
-    _, launches_per_step, _, _ = sq.squeeze_last_step_info(h.h)
+    _, launches_per_step, _ = sq.squeeze_last_step_info(h.h)
     launches = args.steps * launches_per_step
     steps_per_launch = w.n_steps / launches_per_step
     ms_per_step = ms / args.steps
@@ -418,8 +424,13 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
                          "steps_per_launch": steps_per_launch,
-                         "state_bytes_moved_per_launch": 2 * cells,
-                         "dram_gbs": (traffic if traffic else 2 * cells) / launch_s / 1e9,
+                         "state_bytes_per_launch": 2 * cells,
+                         "state_gbs": 2 * cells / launch_s / 1e9,
+                         "state_frac": 2 * cells / launch_s / 1e9 / peak,
+                         "dram_gbs": traffic / launch_s / 1e9 if traffic else None,
+                         "note": "algorithmic bytes: 2 per cell-update (the state read and "
+                                 "written once per step); a launch advances steps_per_launch "
+                                 "steps per pass of the state over HBM (state_gbs)",
                          "avg_launch_ms": launch_s * 1e3},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": cells,
                     "d2h_bytes_per_step": cells, "api": "squeeze_step_host",

@@ -159,23 +159,30 @@ int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t s
  * kernel.  A level whose tiled program would not fit is UNSUPPORTED for
  * TILED (AUTO falls back to the per-cell ALU kernel only when no tile level
  * fits at all).  squeeze_last_step_info() tells which kernel AUTO chose.
- * The tiled kernel advances up to four steps per launch where its program
+ * The tiled kernel advances up to eight steps per launch where its program
  * allows (the intermediate states stay in shared memory), so d_buf1 holds no
  * particular step afterwards; the result is the same bit for bit. */
 int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                  int kind, void *stream);
 
+/* squeeze_set_max_steps_per_launch -- the most steps one launch of the tiled
+ * kernel may advance: 1, 2, 4 or 8, or 0 for the default (the most whose
+ * kernel keeps the CTAs per SM of the one-step kernel; its shared memory grows
+ * with the halo rings each further step needs).  The result of squeeze_step
+ * does not depend on it.  INVALID_ARG for other values. */
+int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps);
+
 /* squeeze_last_step_info -- what the handle's last accepted squeeze_step
  * call ran: *kind = SQUEEZE_STEP_TILED, SQUEEZE_MAP_ALU or SQUEEZE_MAP_TC_BF16
  * (0 before the first step), so that a caller of AUTO can see a fall-back to
  * the per-cell ALU kernel (misaligned buffers; about 300x slower than the
- * tiled kernel); *launches = kernel launches it enqueued; *two_step and
- * *four_step = how many of them advanced two and four steps (the tiled kernel
- * runs n steps as four-, two- and one-step launches whose count has the
- * parity of n: n = 100 is 24 four-step and 2 two-step launches).  Any pointer
- * may be NULL.  INVALID_ARG for a null handle. */
+ * tiled kernel); *launches = kernel launches it enqueued; by_steps[i] (four
+ * entries) = how many of them advanced 2^i steps (the tiled kernel runs n
+ * steps as launches of 8, 4, 2 and 1 steps whose count has the parity of n:
+ * n = 100 is 12 launches of 8 steps and 2 of 2).  Any pointer may be NULL.
+ * INVALID_ARG for a null handle. */
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
-                           uint64_t *two_step, uint64_t *four_step);
+                           uint64_t *by_steps);
 
 /* squeeze_step_host -- the same run from and to HOST memory: copies h_in
  * (k^r bytes, ideally pinned) into d_buf0, runs n_steps, copies the result to

@@ -128,10 +128,11 @@ _SIGS = {
     "squeeze_3d_tiled_level": ([ctypes.c_void_p], ctypes.c_int),
     "squeeze_device_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "squeeze_set_wait_limit": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "squeeze_set_max_steps_per_launch": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "squeeze_set_fault_injection": ([ctypes.c_void_p, ctypes.c_uint32], ctypes.c_int),
     "squeeze_last_step_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
-                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
-                                ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+                               ctypes.c_int),
     "squeeze_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "squeeze_last_cuda_error": ([], ctypes.c_char_p),
 }
@@ -459,6 +460,10 @@ def squeeze_device_status(h) -> int:
     return int(v.value)
 
 
+def squeeze_set_max_steps_per_launch(h, steps: int) -> None:
+    _check(_load().squeeze_set_max_steps_per_launch(h, steps), "squeeze_set_max_steps_per_launch")
+
+
 def squeeze_set_wait_limit(h, ns: int) -> None:
     _check(_load().squeeze_set_wait_limit(h, ns), "squeeze_set_wait_limit")
 
@@ -468,14 +473,13 @@ def squeeze_set_fault_injection(h, flags: int) -> None:
 
 
 def squeeze_last_step_info(h) -> tuple:
-    """(kind, launches, two-step launches, four-step launches) of the handle's
+    """(kind, launches, [launches of 1, 2, 4 and 8 steps]) of the handle's
     last squeeze_step."""
     kind, launches = ctypes.c_int(), ctypes.c_uint64()
-    two, four = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(_load().squeeze_last_step_info(h, ctypes.byref(kind), ctypes.byref(launches),
-                                          ctypes.byref(two), ctypes.byref(four)),
+    by = (ctypes.c_uint64 * 4)()
+    _check(_load().squeeze_last_step_info(h, ctypes.byref(kind), ctypes.byref(launches), by),
            "squeeze_last_step_info")
-    return int(kind.value), int(launches.value), int(two.value), int(four.value)
+    return int(kind.value), int(launches.value), [int(v) for v in by]
 
 
 def squeeze_status_string(code: int) -> str:

@@ -24,6 +24,9 @@
 
 using namespace sq;
 
+// Steps per launch of the batched kernel at most (it is instantiated for 1, 2 and 4).
+constexpr uint32_t kBatchPasses = 4;
+
 // The items of one tile-row instantiation and their launch.
 struct BatchPlan {
   int kind;                 // 27, 25, 8, 16, 64 or 0 (see sq_tile_kind)
@@ -136,7 +139,7 @@ int setup(squeeze_batch *b) {
     BatchPlan p{};
     p.kind = kind;
     p.life = true;
-    p.passes = 4;
+    p.passes = kBatchPasses;
     bool first = true;
     int own_threads = 0;
     std::vector<uint32_t> idx;
@@ -206,13 +209,19 @@ int setup(squeeze_batch *b) {
 // can, with a launch count of n_steps' parity (each launch swaps the
 // buffers; the state after an even number of steps belongs in buffer 0).
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
-  uint32_t passes = 4;
+  uint32_t passes = kBatchPasses;
   for (const BatchPlan &p : b->plans) passes = p.passes < passes ? p.passes : passes;
-  uint64_t quads, doubles, singles;
-  sq_launch_plan(n_steps, passes, quads, doubles, singles);
-  for (uint64_t t = 0; t < quads + doubles + singles; ++t) {
+  uint64_t counts[4];
+  sq_launch_plan(n_steps, passes, counts);
+  const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
+  for (uint64_t t = 0, i = 3, used = 0; t < total; ++t) {
+    while (used == counts[i]) {   // largest launches first
+      --i;
+      used = 0;
+    }
+    ++used;
     const uint32_t parity = (uint32_t)((b->parity + t) & 1u);
-    const uint32_t steps = t < quads ? 4u : (t < quads + doubles ? 2u : 1u);
+    const uint32_t steps = 1u << i;
     for (const BatchPlan &p : b->plans) {
       int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
                                p.grid, p.threads, p.life, p.kind, steps, parity, st);

@@ -229,16 +229,22 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     if (rc) return rc;
   }
   h->last_kind = kind;
-  // The tiled kernel runs up to four steps per launch where its program
-  // allows (sq_launch_plan: four-, two- and one-step launches whose count has
+  // The tiled kernel runs up to eight steps per launch where its program
+  // allows (sq_launch_plan: launches of 8, 4, 2 and 1 steps whose count has
   // the parity of n_steps, since every launch swaps the buffers and the
   // result belongs in d_buf[n_steps & 1]).
-  uint64_t quads = 0, doubles = 0, singles = n_steps;
-  if (kind == SQUEEZE_STEP_TILED) sq_launch_plan(n_steps, sq_tiled_passes(h), quads, doubles, singles);
+  uint64_t counts[4] = {n_steps, 0, 0, 0};
+  if (kind == SQUEEZE_STEP_TILED) sq_launch_plan(n_steps, sq_tiled_passes(h), counts);
+  const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
   uint8_t *a = d_buf0, *b = d_buf1;
-  for (uint64_t t = 0; t < quads + doubles + singles; ++t) {
+  for (uint64_t t = 0, i = 3, used = 0; t < total; ++t) {
+    while (used == counts[i]) {   // largest launches first
+      --i;
+      used = 0;
+    }
+    ++used;
+    const uint32_t steps = 1u << i;
     int rc;
-    const uint32_t steps = t < quads ? 4u : (t < quads + doubles ? 2u : 1u);
     switch (kind) {
       case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, steps, st); break;
       case SQUEEZE_MAP_TC_BF16: rc = sq_launch_step_tc(h, a, b, st); break;
@@ -249,9 +255,8 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     a = b;
     b = tmp;
   }
-  h->last_launches = quads + doubles + singles;
-  h->last_two_step = doubles;
-  h->last_four_step = quads;
+  h->last_launches = total;
+  for (int i = 0; i < 4; ++i) h->last_counts[i] = counts[i];
   return SQUEEZE_OK;
 }
 
@@ -334,12 +339,25 @@ int squeeze_bb_to_compact(const squeeze_handle *h, const uint8_t *d_grid, uint8_
 }
 
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
-                           uint64_t *two_step_launches, uint64_t *four_step_launches) {
+                           uint64_t *by_steps) {
   if (check_handle(h)) return SQUEEZE_ERR_INVALID_ARG;
   if (kind) *kind = h->last_kind;
   if (launches) *launches = h->last_launches;
-  if (two_step_launches) *two_step_launches = h->last_two_step;
-  if (four_step_launches) *four_step_launches = h->last_four_step;
+  if (by_steps)
+    for (int i = 0; i < 4; ++i) by_steps[i] = h->last_counts[i];
+  return SQUEEZE_OK;
+}
+
+int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps) {
+  if (check_handle(h) || (steps != 0 && steps != 1 && steps != 2 && steps != 4 && steps != 8))
+    return SQUEEZE_ERR_INVALID_ARG;
+  if (h->tiled && steps != h->max_passes) {   // rebuilt on the next step
+    cudaError_t e = cudaDeviceSynchronize();
+    sq_tiled_free(h->tiled);
+    h->tiled = nullptr;
+    if (e != cudaSuccess) return sq_cuda_fail(e);
+  }
+  h->max_passes = steps;
   return SQUEEZE_OK;
 }
 

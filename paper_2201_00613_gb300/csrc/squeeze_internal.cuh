@@ -16,6 +16,7 @@ namespace sq {
 constexpr uint8_t kHole = 0xFF;   // H_nu entry of a digit pair that is not a replica
 constexpr int kMaxS = 16;          // s <= 16, so H_nu has at most 256 entries
 constexpr int kMaxK = 255;
+constexpr int kMaxPasses = 8;     // steps one launch of the tiled kernel can advance
 
 // Exact unsigned 32-bit division by a runtime divisor d >= 1 with one
 // multiply-high (Granlund & Montgomery, "Division by invariant integers using
@@ -211,8 +212,8 @@ struct TiledDev {
   const uint8_t *halo_dir;   // nhalo direction indices
   const uint32_t *adj;       // ndirs x tiles adjacent tile indices (~0: none)
   int *status;
-  uint32_t ring_end[5];        // halo words of rings 1..k: [0, ring_end[k])
-  uint32_t ring_start[3][10];  // words of ring k + 2 in direction j
+  uint32_t ring_end[kMaxPasses + 1];        // halo words of rings 1..k: [0, ring_end[k])
+  uint32_t ring_start[kMaxPasses - 1][10];  // words of ring k + 2 in direction j
   uint64_t wait_ns;          // a bulk-copy wait gives up after this many ns
   uint32_t fault;            // SQUEEZE_FAULT_* (test hook), normally 0
   uint32_t pad_;
@@ -236,16 +237,17 @@ struct TileLayout {
 // tables live.
 struct TileSpec {
   uint32_t L, TW, TH, rpw, cells, slots, nhalo, ndirs, dir_mask;
-  uint32_t passes;     // steps one launch of the program can advance: 1, 2 or 4
-  uint32_t ring_end[5];      // halo words of rings 1..k: [0, ring_end[k]) (ring_end[passes] = nhalo)
+  uint32_t passes;     // steps one launch of the program can advance: 1, 2, 4 or 8
+  uint32_t ring_end[kMaxPasses + 1];  // halo words of rings 1..k: [0, ring_end[k]) (ring_end[passes] = nhalo)
   uint8_t dir_list[9];
   uint32_t halo_start[10];   // first-ring words of direction j: [halo_start[j], halo_start[j+1])
-  uint32_t ring_start[3][10];  // words of ring k + 2 in direction j: [ring_start[k][j], ring_start[k][j+1])
+  uint32_t ring_start[kMaxPasses - 1][10];  // words of ring k + 2 in direction j: [ring_start[k][j], ring_start[k][j+1])
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint64_t groups;
   size_t smem;
   int threads;
-  int grid[3][2];      // persistent grid per steps-per-launch (1, 2, 4) and rule (generic, B3/S23)
+  int grid[4][2];      // persistent grid per steps-per-launch (1, 2, 4, 8) and rule (generic, B3/S23)
+  int occ[4][2];       // CTAs per SM of those kernels
 };
 
 // Capacities needed to build the program of one tile level.
@@ -265,7 +267,7 @@ struct TileBuild {
   uint32_t *halo_off;
   uint8_t *halo_dir;
   uint64_t box_cap, cells_cap, slots_cap, halo_cap;
-  // Steps per launch the program is built for (1, 2 or 4): for P > 1 the halo
+  // Steps per launch the program is built for (1, 2, 4 or 8): for P > 1 the halo
   // rings 2..P are built too, and references for rings 1..P-1 (refs and
   // refs16 then need (slots + halo_cap) * 8 entries).
   uint32_t passes;
@@ -304,8 +306,8 @@ struct squeeze_handle {
   uint32_t fault;            // fault-injection flags (tests only)
   int last_kind;             // kind the last squeeze_step ran (0 before the first)
   uint64_t last_launches;    // kernel launches of that call
-  uint64_t last_two_step;    // of which two steps per launch
-  uint64_t last_four_step;   // and four steps per launch
+  uint64_t last_counts[4];   // of which 1, 2, 4 and 8 steps per launch
+  uint32_t max_passes;       // steps per launch at most (0: the default choice)
 };
 
 // Error plumbing and descriptor validation (handle.cu).
@@ -328,16 +330,15 @@ int sq_launch_init(const squeeze_handle *h, uint8_t *state, uint64_t seed, uint3
 int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                        cudaStream_t st);
 int sq_tiled_prepare(squeeze_handle *h);
-// One launch of the handle's tiled program: steps = 1, 2 or 4, at most the
+// One launch of the handle's tiled program: steps = 1, 2, 4 or 8, at most the
 // passes the program was built for (sq_tiled_passes).
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                          uint32_t steps, cudaStream_t st);
 uint32_t sq_tiled_passes(const squeeze_handle *h);
-// Launches of n steps at up to `passes` steps each (4, 2 and 1), with a launch
-// count of n's parity (every launch swaps the buffers; the result belongs in
-// buffer n & 1).
-void sq_launch_plan(uint64_t n, uint32_t passes, uint64_t &quads, uint64_t &doubles,
-                    uint64_t &singles);
+// Launches of n steps at up to `passes` steps each: counts[i] launches of
+// 2^i steps (i = 0..3), with a launch count of n's parity (every launch swaps
+// the buffers; the result belongs in buffer n & 1).
+void sq_launch_plan(uint64_t n, uint32_t passes, uint64_t *counts);
 void sq_tiled_free(TiledProgram *p);
 int sq_tiled_default_level(const squeeze_handle *h);
 int sq_tiled_default_level_for(const sq::FracDev &f);
@@ -352,7 +353,7 @@ sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint3
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
 int sq_tile_build_adjacency(const sq::FracDev &f, const sq::TiledDev &d, uint32_t *adj,
                             cudaStream_t st);
-// One launch of the tiled kernel: steps = 1, 2 or 4 (at most the program's passes).
+// One launch of the tiled kernel: steps = 1, 2, 4 or 8 (at most the program's passes).
 int sq_tile_launch(const sq::TiledDev &d, const sq::TileSpec &sp, const uint8_t *in,
                    uint8_t *out, uint32_t steps, cudaStream_t st);
 // The handle's prepared tiled program (sq_tiled_prepare first).

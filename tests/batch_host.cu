@@ -12,8 +12,8 @@ int sq_tiled_describe(const squeeze_handle *, sq::TiledDev *, sq::TileSpec *) {
 sq::TileLayout sq_tile_layout(uint32_t, uint32_t, uint32_t, uint32_t) { return sq::TileLayout{}; }
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &) { return a; }
 int sq_tile_kind(const sq::TileSpec &) { return 0; }
-void sq_launch_plan(uint64_t, uint32_t, uint64_t &quads, uint64_t &doubles, uint64_t &singles) {
-  quads = doubles = singles = 0;
+void sq_launch_plan(uint64_t, uint32_t, uint64_t *counts) {
+  for (int i = 0; i < 4; ++i) counts[i] = 0;
 }
 int sq_batch_occupancy(bool, int, uint32_t, int, uint32_t) { return 0; }
 int sq_batch_launch(const sq::TiledDev *, uint8_t *const *, uint8_t *const *, const sq::BatchWork *,

@@ -438,9 +438,9 @@ TWO_STEP_RULES = [(1 << 3, (1 << 2) | (1 << 3)),                    # B3/S23
                                  (I.VICSEK, 6), (I.FULL2, 7), (I.TRIANGLE, 4)],
                          ids=["triangle9", "triangle_paper8", "carpet5", "vicsek6", "full2-7",
                               "triangle4"])
-@pytest.mark.parametrize("steps", [4, 6, 7, 12])
+@pytest.mark.parametrize("steps", [4, 6, 7, 12, 16, 21])
 def test_multi_step_launches_match_the_oracle(f, r, steps):
-    """The tiled kernel runs four or two steps in one launch (the intermediate
+    """The tiled kernel runs eight, four or two steps in one launch (the intermediate
     steps of the tile and of its halo rings in shared memory); every rule,
     including one with births at zero neighbours (which a missing adjacent
     tile must not feed), must give the oracle's states."""
@@ -451,23 +451,23 @@ def test_multi_step_launches_match_the_oracle(f, r, steps):
         for rule in TWO_STEP_RULES:
             sq.squeeze_set_rule(h.h, *rule)
             got = run_steps(h, c0, steps, sq.SQUEEZE_STEP_TILED)
-            kind, launches, two, four = sq.squeeze_last_step_info(h.h)
-            assert kind == sq.SQUEEZE_STEP_TILED and two + four >= 1
-            assert launches % 2 == steps % 2
-            assert 4 * four + 2 * two + (launches - two - four) == steps
+            kind, launches, by = sq.squeeze_last_step_info(h.h)
+            assert kind == sq.SQUEEZE_STEP_TILED and sum(by[1:]) >= 1
+            assert launches == sum(by) and launches % 2 == steps % 2
+            assert sum(c << i for i, c in enumerate(by)) == steps
             want = oracle.box_to_compact(f, r, oracle.box_run_nbhd(m, box0, steps, rule,
                                                                    oracle.MOORE))
             assert np.array_equal(got, want), rule
         assert sq.squeeze_device_status(h.h) == sq.SQUEEZE_OK
 
 
-@pytest.mark.parametrize("steps", [1, 2, 3, 4, 5, 6, 8, 10])
+@pytest.mark.parametrize("steps", [1, 2, 3, 4, 5, 6, 8, 10, 16, 17, 24, 100])
 def test_launch_plan_puts_the_result_in_the_right_buffer(steps):
     f, r = I.TRIANGLE, 10
     with sq.Handle(f, r) as h:
         c0 = I.bernoulli_bytes(5, h.cells, 0.5)
         got = run_steps(h, c0, steps, sq.SQUEEZE_STEP_TILED)
-        _, launches, two, four = sq.squeeze_last_step_info(h.h)
-        assert launches % 2 == steps % 2
-        assert 4 * four + 2 * two + (launches - two - four) == steps
+        _, launches, by = sq.squeeze_last_step_info(h.h)
+        assert launches == sum(by) and launches % 2 == steps % 2
+        assert sum(c << i for i, c in enumerate(by)) == steps
         assert np.array_equal(got, oracle.run_compact(f, r, c0, steps))

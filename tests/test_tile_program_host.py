@@ -55,7 +55,7 @@ def program(lib, f, r, L, nbhd, passes=1):
     caps = np.zeros(3, dtype=np.uint64)
     assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
     cells, slots, halo = (int(v) for v in caps)
-    info = np.zeros(14, dtype=np.uint32)
+    info = np.zeros(18, dtype=np.uint32)
     slot = np.zeros(cells, dtype=np.uint32)
     X = np.zeros(cells, dtype=np.uint32)
     Y = np.zeros(cells, dtype=np.uint32)
@@ -69,7 +69,7 @@ def program(lib, f, r, L, nbhd, passes=1):
         return None     # rings deeper than the box is wide: the library builds fewer passes
     assert rc == 0, rc
     TW, TH, rpw, wpr, ncell, nslot, nhalo, ndirs, npass = (int(v) for v in info[:9])
-    ring_end = [int(v) for v in info[9:14]]
+    ring_end = [int(v) for v in info[9:18]]
     nrows = nslot + ring_end[npass - 1]
     return dict(TW=TW, TH=TH, rpw=rpw, wpr=wpr, cells=ncell, slots=nslot, nhalo=nhalo,
                 passes=npass, ring_end=ring_end, nhalo1=ring_end[1],
@@ -211,7 +211,7 @@ TWO_STEP_RULES = [oracle.B3S23, ((1 << 3) | (1 << 6), (1 << 2) | (1 << 3)),   # 
                   ((1 << 0) | (1 << 3), (1 << 2) | (1 << 3))]                 # B03/S23: birth at 0
 
 
-@pytest.mark.parametrize("passes", [2, 4])
+@pytest.mark.parametrize("passes", [2, 4, 8])
 @pytest.mark.parametrize("f,r,L,nbhd", CASES,
                          ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CASES])
 def test_multi_step_program_equals_oracle_steps(lib, f, r, L, nbhd, passes):
@@ -241,7 +241,7 @@ def test_multi_step_emulation_catches_a_dropped_existence_mask(lib):
     # Without the mask a ring cell of a missing tile can be born (rule B03
     # births at 0 neighbours) and feed the next step: the result must differ.
     f, r, L = I.TRIANGLE, 8, 3
-    for passes in (2, 4):
+    for passes in (2, 4, 8):
         prog = program(lib, f, r, L, oracle.MOORE, passes=passes)
         adj = library_adjacency(lib, f, r, L, prog)
         state = I.bernoulli_bytes(7, f.k ** r, 0.45)

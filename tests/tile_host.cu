@@ -48,8 +48,8 @@ int tile_sizes(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t 
   return SQUEEZE_OK;
 }
 
-// The level-L program for up to `passes` steps per launch (1, 2 or 4): info =
-// (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs, passes, ring_end[0..4]); per
+// The level-L program for up to `passes` steps per launch (1, 2, 4 or 8): info
+// = (TW, TH, rpw, wpr, cells, slots, nhalo, ndirs, passes, ring_end[0..8]); per
 // local cell its slot and local expanded position; per slot (and per halo word
 // of rings 1 .. passes-1 after them) 8 byte offsets into the word array
 // (slots, then halo words ring by ring, then a zero word); per halo word its
@@ -88,11 +88,10 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   const int rc = sq_tile_build(f, L, B, sp);
   if (rc) return rc;
   const uint32_t wpr = sp.TW == 64 ? 2u : 1u;
-  const uint32_t v[14] = {sp.TW,          sp.TH,          sp.rpw,         wpr,
-                          sp.cells,       sp.slots,       sp.nhalo,       sp.ndirs,
-                          sp.passes,      sp.ring_end[0], sp.ring_end[1], sp.ring_end[2],
-                          sp.ring_end[3], sp.ring_end[4]};
+  const uint32_t v[9] = {sp.TW, sp.TH, sp.rpw, wpr, sp.cells, sp.slots, sp.nhalo, sp.ndirs,
+                         sp.passes};
   memcpy(info, v, sizeof(v));
+  memcpy(info + 9, sp.ring_end, sizeof(sp.ring_end));   // kMaxPasses + 1 entries
   for (uint32_t c = 0; c < sp.cells; ++c) {
     slot[c] = tile_slot_of(c, sp.TW, sp.rpw, wpr);
     X[c] = vX[c];
