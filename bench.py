@@ -592,7 +592,7 @@ def bb_compare(sq, torch, dev, stream, steps=20):
            "compact_l2": "one step per launch, L2 flushed before every launch",
            "compact_hbm_frac": compact_frac,
            "compact_resident_cell_updates_per_s": resident,
-           "compact_resident": "200 steps in one call (two steps per launch, state in L2)",
+           "compact_resident": "200 steps in one call (the default steps per launch, state in L2)",
            "bb_cell_updates_per_s": bb, "bb_box_gbs": bb_gbs, "bb_hbm_frac": bb_frac,
            "lambda_approach_cell_updates_per_s": lam,
            "speedup_compact_over_bb": compact / bb,

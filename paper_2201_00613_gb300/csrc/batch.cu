@@ -9,8 +9,8 @@
 // shared memory.  Each launch's CTAs walk a host-built schedule of (instance,
 // group range) entries, cut so that every CTA gets about the same number of
 // group slots (a group costs about the same whether its 32 tile lanes are
-// full or not).  Launches advance two steps where the items' programs allow
-// (the intermediate step stays in shared memory).  The launches of n_steps
+// full or not).  Launches advance up to four steps where the items' programs
+// allow (the intermediate steps stay in shared memory).  The launches of n_steps
 // steps are captured once into a CUDA graph (buffers ping-ponging) and
 // replayed on later calls.
 #include <stdio.h>
