@@ -102,10 +102,44 @@ void build_schedule(const std::vector<uint64_t> &cells, const std::vector<uint64
       };
       uint64_t g0 = first_at(lo), g1 = first_at(hi);
       if (c == grid - 1) g1 = groups[j];
-      if (g0 < g1) work.push_back(BatchWork{(uint32_t)j, 0u, g0, g1});
+      if (g0 < g1) work.push_back(BatchWork{(uint32_t)j, 1u, g0, g1});
     }
   }
   start[grid] = (uint32_t)work.size();
+}
+
+// Consecutive CTAs whose only entry is a run of one instance, each run
+// starting where the previous one ends, share those groups strided instead:
+// the q-th of m CTAs takes gA + q, gA + q + m, ... below gB.  The CTAs then
+// step a band of neighbouring groups at a time, so the halo chunks read from
+// the tiles above and below are still in L2 (used for 64-wide rows, which
+// lose nothing by not handing row ends over).  Each CTA keeps its number of
+// groups within one.
+void stride_schedule(std::vector<BatchWork> &work, const std::vector<uint32_t> &start) {
+  const size_t grid = start.size() - 1;
+  size_t c = 0;
+  while (c < grid) {
+    if (start[c + 1] - start[c] != 1) {
+      ++c;
+      continue;
+    }
+    size_t e = c;
+    while (e + 1 < grid && start[e + 2] - start[e + 1] == 1 &&
+           work[start[e + 1]].instance == work[start[c]].instance &&
+           work[start[e + 1]].g_first == work[start[e]].g_end)
+      ++e;
+    const size_t m = e - c + 1;
+    if (m > 1) {
+      const uint64_t gA = work[start[c]].g_first, gB = work[start[e]].g_end;
+      for (size_t q = 0; q < m; ++q) {
+        BatchWork &w = work[start[c + q]];
+        w.g_first = gA + q;
+        w.g_end = gB;
+        w.g_stride = (uint32_t)m;
+      }
+    }
+    c = e + 1;
+  }
 }
 
 int setup(squeeze_batch *b) {
@@ -148,7 +182,7 @@ int setup(squeeze_batch *b) {
       if (sq_tile_kind(specs[i]) != kind) continue;
       const TileSpec &sp = specs[i];
       const squeeze_handle *h = b->items[i].h;
-      TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
+      TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp));
       p.lay = first ? l : sq_tile_layout_max(p.lay, l);
       first = false;
       p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
@@ -177,6 +211,7 @@ int setup(squeeze_batch *b) {
     std::vector<BatchWork> work;
     std::vector<uint32_t> start;
     build_schedule(weight, groups, p.grid, work, start);
+    if (kind == 64) stride_schedule(work, start);
     for (BatchWork &w : work) w.instance = idx[w.instance];
     b->plans.push_back(p);
     works.push_back(work);

@@ -216,6 +216,12 @@ struct TiledDev {
   uint32_t ring_start[kMaxPasses - 1][10];  // words of ring k + 2 in direction j
   uint64_t wait_ns;          // a bulk-copy wait gives up after this many ns
   uint32_t fault;            // SQUEEZE_FAULT_* (test hook), normally 0
+  // Halo by 16-byte chunks (64-wide rows only; 0: halo bytes one by one).
+  // halo_off is followed by the chunk table: nchunks chunk offsets inside a
+  // tile, nchunks + 1 cell ranges, then nhalo cells (halo word | byte << 16);
+  // direction j owns chunks [chunk_start[j], chunk_start[j + 1]).
+  uint32_t nchunks;
+  uint32_t chunk_start[10];
   uint32_t pad_;
 };
 
@@ -243,6 +249,8 @@ struct TileSpec {
   uint32_t halo_start[10];   // first-ring words of direction j: [halo_start[j], halo_start[j+1])
   uint32_t ring_start[kMaxPasses - 1][10];  // words of ring k + 2 in direction j: [ring_start[k][j], ring_start[k][j+1])
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
+  uint32_t nchunks;          // chunk table of the halo (64-wide rows), 0 if none
+  uint32_t chunk_start[10];  // chunks of direction j: [chunk_start[j], chunk_start[j+1])
   uint64_t groups;
   size_t smem;
   int threads;
@@ -271,14 +279,17 @@ struct TileBuild {
   // rings 2..P are built too, and references for rings 1..P-1 (refs and
   // refs16 then need (slots + halo_cap) * 8 entries).
   uint32_t passes;
+  // Optional (64-wide rows): the halo's chunk table, 3 * halo_cap + 1 words
+  // (layout as in TiledDev); null builds a program without one.
+  uint32_t *chunks;
 };
 
 // One entry of a batched launch's schedule: CTA c processes entries
-// [sched_start[c], sched_start[c + 1]), each a contiguous range of groups of
-// one instance.
+// [sched_start[c], sched_start[c + 1]), each the groups g_first, g_first +
+// g_stride, ... below g_end of one instance.
 struct BatchWork {
   uint32_t instance;
-  uint32_t pad;
+  uint32_t g_stride;
   uint64_t g_first, g_end;
 };
 
@@ -349,7 +360,10 @@ int sq_tile_launch_config(sq::TileSpec &sp, int device);
 sq::TiledDev sq_tiled_dev(const sq::FracDev &f, const sq::Rule &rule, const sq::TileSpec &sp,
                           const uint16_t *refs, const uint32_t *halo_off,
                           const uint8_t *halo_dir, const uint32_t *adj, int *status);
-sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch);
+sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch,
+                              uint32_t table_words = 0);
+// Words of a program's halo chunk table (0 when it has none).
+uint32_t sq_tile_table_words(const sq::TileSpec &sp);
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
 int sq_tile_build_adjacency(const sq::FracDev &f, const sq::TiledDev &d, uint32_t *adj,
                             cudaStream_t st);

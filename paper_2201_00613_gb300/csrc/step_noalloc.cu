@@ -44,6 +44,7 @@ struct HostWork {
   uint16_t refs16[kSlotsCap * 8];
   uint32_t halo_off[kHaloCap];
   uint8_t halo_dir[kHaloCap];
+  uint32_t chunks[3 * kHaloCap + 1];   // halo chunk table of 64-wide rows
 };
 
 HostWork g_work;         // guarded by g_mutex
@@ -91,7 +92,8 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
     if (z.box > kBoxCap || z.cells > kCellsCap || z.slots > kSlotsCap) continue;
     TileBuild B = {g_work.inv,   g_work.X,      g_work.Y,     g_work.refs,   g_work.keys,
                    g_work.sorted, g_work.order, g_work.rank,  g_work.refs16, g_work.halo_off,
-                   g_work.halo_dir, kBoxCap,    kCellsCap,    kSlotsCap,     kHaloCap};
+                   g_work.halo_dir, kBoxCap,    kCellsCap,    kSlotsCap,     kHaloCap,
+                   1u,            g_work.chunks};
     rc = sq_tile_build(f, (uint32_t)L, B, sp);
     if (rc == SQUEEZE_OK && sp.smem <= sq_tiled_smem_cap()) break;
     rc = SQUEEZE_ERR_UNSUPPORTED;
@@ -101,12 +103,13 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
     return SQUEEZE_ERR_UNSUPPORTED;
   }
 
-  // Scratch layout: status word | neighbour program | halo offsets | halo
-  // directions | adjacency table.
+  // Scratch layout: status word | neighbour program | halo offsets and chunk
+  // table | halo directions | adjacency table.
   const uint64_t tiles = (uint64_t)sp.tiles_x * sp.tiles_y;
+  const uint32_t table_words = sq_tile_table_words(sp);
   const size_t off_refs = 256;
   const size_t off_hoff = align16(off_refs + (size_t)sp.slots * 16);
-  const size_t off_hdir = align16(off_hoff + (size_t)sp.nhalo * 4);
+  const size_t off_hdir = align16(off_hoff + ((size_t)sp.nhalo + table_words) * 4);
   const size_t off_adj = align16(off_hdir + sp.nhalo);
   const uint64_t need = off_adj + (uint64_t)sp.ndirs * tiles * 4;
   if (need > kNoallocScratchBytes) {
@@ -132,6 +135,9 @@ extern "C" int squeeze_step_noalloc(uint32_t s, uint32_t k, const uint8_t *offse
   SQ_CUDA(cudaMemcpyAsync(d_refs, g_work.refs16, (size_t)sp.slots * 16, cudaMemcpyHostToDevice, st));
   if (sp.nhalo) {
     SQ_CUDA(cudaMemcpyAsync(d_hoff, g_work.halo_off, (size_t)sp.nhalo * 4, cudaMemcpyHostToDevice, st));
+    if (table_words)
+      SQ_CUDA(cudaMemcpyAsync(d_hoff + sp.nhalo, g_work.chunks, (size_t)table_words * 4,
+                              cudaMemcpyHostToDevice, st));
     SQ_CUDA(cudaMemcpyAsync(d_hdir, g_work.halo_dir, sp.nhalo, cudaMemcpyHostToDevice, st));
   }
   Rule rule{birth, survive};

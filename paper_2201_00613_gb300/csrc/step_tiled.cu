@@ -22,7 +22,9 @@
 // merged unpack return the bytes to the staging rows, and TMA bulk stores
 // write them back.  Rows 8 or 16 cells wide share a word (4 or 2 rows per
 // word); rows 64 cells wide take two words.  Only halo bytes are read with
-// single-byte loads.
+// single-byte loads; for 64-wide rows (whose tiles start on 64-byte
+// boundaries) the halo comes in 16-byte chunks of the adjacent tiles, one load
+// serving every halo cell of the chunk.
 //
 // Bit order of a packed row word: bit 8b + j holds tile-row byte 4j + b (the
 // order the pack produces for free); the neighbour program is built in that
@@ -89,10 +91,11 @@ static uint32_t layout_total(const TileLayout &l) {
 }
 
 // Word buffer: slots, halo words, the zero word and 9 per-direction masks.
-TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch) {
+TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch,
+                          uint32_t table_words) {
   TileLayout l;
   l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1 + 9) * 4 + 15) & ~(size_t)15);
-  l.hoff_bytes = (uint32_t)(((size_t)nhalo * 4 + 15) & ~(size_t)15);
+  l.hoff_bytes = (uint32_t)((((size_t)nhalo + table_words) * 4 + 15) & ~(size_t)15);
   l.hdir_bytes = (uint32_t)(((size_t)nhalo + 15) & ~(size_t)15);
   l.rowa_bytes = (uint32_t)(((size_t)2 * TH + 15) & ~(size_t)15);
   l.carry_bytes = 16u * TH;
@@ -102,6 +105,10 @@ TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t 
   l.stage_bytes = (uint32_t)((size_t)TH * pitch + 16);
   l.smem = layout_total(l);
   return l;
+}
+
+uint32_t sq_tile_table_words(const TileSpec &sp) {
+  return sp.nchunks ? 2u * sp.nchunks + 1u + sp.nhalo : 0u;
 }
 
 TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
@@ -207,6 +214,8 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   for (int i = 0; i <= kMaxPasses; ++i) d.ring_end[i] = sp.ring_end[i];
   for (int k = 0; k < kMaxPasses - 1; ++k)
     for (int i = 0; i < 10; ++i) d.ring_start[k][i] = sp.ring_start[k][i];
+  d.nchunks = sp.nchunks;
+  for (int i = 0; i < 10; ++i) d.chunk_start[i] = sp.chunk_start[i];
   return d;
 }
 
@@ -277,6 +286,40 @@ void sq_tile_build_sizes(const FracDev &f, uint32_t L, TileBuildSizes &z) {
   z.cells = TW * TH;
   z.slots = TH * (TW == 64 ? 64 : 32);
   z.halo = 8 * z.cells;
+}
+
+// The halo's chunk table for 64-wide rows.  A tile starts on a multiple of 64
+// bytes and W is a multiple of 64, so the halo cell at offset o of an adjacent
+// tile lies in the 16-byte chunk o & ~15 of it, at byte o & 15.  Per
+// direction: its distinct chunks in increasing order, and per chunk its cells
+// in increasing halo-word order (so ring by ring).  out = chunk offsets |
+// nchunks + 1 cell ranges | nhalo cells (halo word | byte << 16).
+static void build_chunks(uint32_t nhalo, const uint32_t *halo_off, const uint8_t *halo_dir,
+                         TileSpec &sp, uint32_t *out) {
+  std::vector<uint32_t> coff, cstart, cells;
+  for (uint32_t j = 0; j <= sp.ndirs; ++j) {
+    sp.chunk_start[j] = (uint32_t)coff.size();
+    if (j == sp.ndirs) break;
+    std::vector<uint32_t> mine;   // chunk offsets of direction j
+    for (uint32_t h = 0; h < nhalo; ++h)
+      if (halo_dir[h] == j) mine.push_back(halo_off[h] & ~15u);
+    std::sort(mine.begin(), mine.end());
+    mine.erase(std::unique(mine.begin(), mine.end()), mine.end());
+    for (uint32_t c : mine) {
+      coff.push_back(c);
+      cstart.push_back((uint32_t)cells.size());
+      for (uint32_t h = 0; h < nhalo; ++h)
+        if (halo_dir[h] == j && (halo_off[h] & ~15u) == c)
+          cells.push_back(h | ((halo_off[h] & 15u) << 16));
+    }
+  }
+  for (uint32_t j = sp.ndirs + 1; j < 10; ++j) sp.chunk_start[j] = (uint32_t)coff.size();
+  cstart.push_back((uint32_t)cells.size());
+  sp.nchunks = (uint32_t)coff.size();
+  uint32_t *o = out;
+  for (uint32_t v : coff) *o++ = v;
+  for (uint32_t v : cstart) *o++ = v;
+  for (uint32_t v : cells) *o++ = v;
 }
 
 // Host construction of the level-L neighbour program (see the file comment):
@@ -432,7 +475,8 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.groups_per_band = (sp.tiles_x + 31) / 32;
   sp.groups = (uint64_t)sp.groups_per_band * sp.tiles_y;
   sp.pitch = pitch_for(TW);
-  sp.smem = smem_for(slots, nhalo, TH, sp.pitch);
+  if (TW == 64 && B.chunks && nhalo) build_chunks(nhalo, B.halo_off, B.halo_dir, sp, B.chunks);
+  sp.smem = sq_tile_layout(slots, nhalo, TH, sp.pitch, sq_tile_table_words(sp)).smem;
   if (sp.groups >= (1ull << 32) || sp.smem > kTiledSmemLimit) return SQUEEZE_ERR_UNSUPPORTED;
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
   // Shared slot words: two slot rows per warp, 4..8 warps.
@@ -486,9 +530,10 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return SQUEEZE_ERR_INVALID_ARG;
   if ((steps != 1 && steps != 2 && steps != 4 && steps != 8) || steps > sp.passes)
     return SQUEEZE_ERR_INVALID_ARG;
+  if (sp.TW == 64 && sp.nhalo && !sp.nchunks) return SQUEEZE_ERR_INVALID_ARG;  // no chunk table
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
-  TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch);
+  TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp));
   void *args[] = {&dd, &lay, &in, &out};
   const int grid = sp.grid[steps_index(steps)][life ? 1 : 0];
   SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw, steps), dim3(grid),
@@ -511,11 +556,11 @@ int sq_tiled_prepare(squeeze_handle *h) {
       rank(z.halo);
   std::vector<uint64_t> keys(z.halo), sorted(z.halo);
   std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
-  std::vector<uint32_t> halo_off(z.halo);
+  std::vector<uint32_t> halo_off(z.halo), chunks(3 * z.halo + 1);
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
-                 z.box, z.cells, z.slots, z.halo, kTiledPasses};
+                 z.box, z.cells, z.slots, z.halo, kTiledPasses, chunks.data()};
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
   // Steps per launch: by default the most (8, 4, 2) whose program builds and
@@ -545,16 +590,19 @@ int sq_tiled_prepare(squeeze_handle *h) {
     return rc;
   }
   const TileSpec &sp = p->spec;
-  uint32_t nhalo = sp.nhalo;
+  uint32_t nhalo = sp.nhalo, tw = sq_tile_table_words(sp);
   // slots, then the rings with references (1 .. passes - 1)
   const size_t ref_bytes = (size_t)(sp.slots + sp.ring_end[sp.passes - 1]) * 16;
   cudaError_t e = cudaMalloc(&p->d_refs, ref_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, (nhalo ? nhalo : 1) * 4);
+  // halo offsets, then the chunk table (if any)
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_off, ((size_t)nhalo + tw + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_halo_dir, (nhalo ? nhalo : 1));
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_refs, refs16.data(), ref_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
     e = cudaMemcpy(p->d_halo_off, halo_off.data(), nhalo * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && tw)
+    e = cudaMemcpy(p->d_halo_off + nhalo, chunks.data(), (size_t)tw * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nhalo)
     e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
   uint64_t tiles = (uint64_t)sp.tiles_x * sp.tiles_y;

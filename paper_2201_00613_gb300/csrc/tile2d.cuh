@@ -312,6 +312,62 @@ __device__ __forceinline__ void gather_halo(const TiledDev &p, uint32_t TW, uint
   }
 }
 
+// Halo by chunks (64-wide rows, TiledDev::nchunks > 0).  ctab is the chunk
+// table in shared memory: nchunks chunk offsets, nchunks + 1 cell ranges,
+// then the cells (halo word | byte << 16).  Lane = tile: each lane loads the
+// same 16-byte chunk of its own adjacent tile (base), so one load serves every
+// halo cell of that chunk, then each cell's byte becomes one bit of its word.
+constexpr int kChunkBatch = 4;   // chunk loads in flight per warp
+
+template <int kB>
+__device__ __forceinline__ void load_chunks(const TiledDev &p, uint64_t base,
+                                            const uint32_t *ctab, uint32_t c, uint32_t c1,
+                                            const uint8_t *in, uint4 *v) {
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    v[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (c + i < c1 && base != ~0ull) {
+      const uint64_t a = base + ctab[c + i];
+      if (a + 16u <= p.total) v[i] = __ldg(reinterpret_cast<const uint4 *>(in + a));
+      else flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+    }
+  }
+}
+
+// Halo words of the cells of chunks c .. min(c + kB, c1) - 1 held in v; cells
+// of halo words >= hlimit (rings this launch does not use) are skipped.
+template <int kB>
+__device__ __forceinline__ void ballot_chunks(const TiledDev &p, const uint32_t *ctab,
+                                              uint32_t c, uint32_t c1, const uint4 *v,
+                                              uint32_t *words, uint32_t hlimit, unsigned lane) {
+  const uint32_t *cstart = ctab + p.nchunks, *cells = cstart + p.nchunks + 1;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    if (c + i < c1) {
+      const uint32_t e1 = cstart[c + i + 1];
+      for (uint32_t e = cstart[c + i]; e < e1; ++e) {
+        const uint32_t ent = cells[e], h = ent & 0xFFFFu, byte = ent >> 16;
+        if (h >= hlimit) break;   // cells are in increasing word order
+        const uint32_t w = (byte & 8u) ? ((byte & 4u) ? v[i].w : v[i].z)
+                                       : ((byte & 4u) ? v[i].y : v[i].x);
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, (w >> ((byte & 3u) * 8u)) & 1u);
+        if (lane == 0) words[h] = word;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void gather_chunks(const TiledDev &p, uint64_t base,
+                                              const uint32_t *ctab, uint32_t c0, uint32_t c1,
+                                              uint32_t *words, uint32_t hlimit,
+                                              const uint8_t *in, unsigned lane) {
+  for (uint32_t c = c0; c < c1; c += kChunkBatch) {
+    uint4 v[kChunkBatch];
+    load_chunks<kChunkBatch>(p, base, ctab, c, c1, in, v);
+    ballot_chunks<kChunkBatch>(p, ctab, c, c1, v, words, hlimit, lane);
+  }
+}
+
 // Pack tile row ly of the staging buffer into a word (lane = tile; bit 8b + j
 // <- byte 4j + b of the row); 0 for lanes past the group.
 template <int kTW>
@@ -558,7 +614,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   // A CTA that gave up on an earlier instance of a batch loads nothing more:
   // this instance's output is not valid either, so its status says so.
   if (tid == 0 && cta_aborted()) flag(p.status, SQUEEZE_ERR_DEVICE_TIMEOUT);
-  for (uint32_t i = tid; i < nhalo; i += nthreads) hoff[i] = p.halo_off[i];
+  // 64-wide rows gather the halo by chunks (their programs always carry the
+  // chunk table); the table follows the halo offsets in global and in shared
+  // memory.
+  constexpr bool kChunked = kTW == 64;
+  const uint32_t ntab = nhalo + (kChunked && p.nchunks ? 2u * p.nchunks + 1u + nhalo : 0u);
+  const uint32_t *ctab = hoff + nhalo;
+  for (uint32_t i = tid; i < ntab; i += nthreads) hoff[i] = p.halo_off[i];
   if constexpr (kT > 1)
     for (uint32_t i = tid; i < p.ring_end[kT - 1]; i += nthreads) hdir[i] = p.halo_dir[i];
   if (tid == 0) {
@@ -610,7 +672,16 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     // and directions j >= nw, are gathered in place.
     uint32_t hb[kHaloAhead];
     uint32_t h_pre = 0, t_next = ~0u;
-    if (warp < p.ndirs) {
+    const uint32_t hlimit = p.ring_end[kT];   // halo words of the rings this launch uses
+    if (kChunked && warp < p.ndirs) {
+      // chunk mode: direction `warp` is gathered after the pack (loading
+      // chunks ahead of it costs registers and measured no faster)
+      if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
+      if constexpr (kT > 1) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, t_cur != ~0u);
+        if (lane == 0) emask[warp] = m;
+      }
+    } else if (!kChunked && warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp], h1 = p.halo_start[warp + 1];
       h_pre = min(h1 - h0, (uint32_t)kHaloAhead);
       const uint64_t base = tile_base(p, TW, t_cur);
@@ -635,13 +706,20 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     }
     for (uint32_t j = warp + nw; j < p.ndirs; j += nw) {
       const uint32_t t = adjacent_of(p, G, j, lane);
-      gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff, win + slots,
-                              in, lane);
-      if constexpr (kT > 1) {
+      if constexpr (kChunked) {
+        gather_chunks(p, tile_base(p, TW, t), ctab, p.chunk_start[j], p.chunk_start[j + 1],
+                      win + slots, hlimit, in, lane);
+      } else {
+        gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff,
+                                win + slots, in, lane);
+        if constexpr (kT > 1) {
 #pragma unroll
-        for (int k = 0; k < kT - 1; ++k)
-          gather_halo<kHaloBatch>(p, TW, t, p.ring_start[k][j], p.ring_start[k][j + 1], hoff,
-                                  win + slots, in, lane);
+          for (int k = 0; k < kT - 1; ++k)
+            gather_halo<kHaloBatch>(p, TW, t, p.ring_start[k][j], p.ring_start[k][j + 1], hoff,
+                                    win + slots, in, lane);
+        }
+      }
+      if constexpr (kT > 1) {
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, t != ~0u);
         if (lane == 0) emask[j] = m;
       }
@@ -701,7 +779,11 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       for (int k = 0; k < kR; ++k)
         if (vrow(u0, k) < VR) win[vrow(u0, k) * 32u + lane] = acc[k];
     }
-    if (warp < p.ndirs) {
+    if (kChunked && warp < p.ndirs) {
+      gather_chunks(p, tile_base(p, TW, t_cur), ctab, p.chunk_start[warp],
+                    p.chunk_start[warp + 1], win + slots, hlimit, in, lane);
+      t_cur = t_next;
+    } else if (!kChunked && warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp];
 #pragma unroll
       for (int i = 0; i < kHaloAhead; ++i) {
@@ -866,8 +948,12 @@ __device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLay
   }
 }
 
-// kT steps (1 or 2) of one instance; CTA c of the persistent grid takes the
-// contiguous run of groups [c G / grid, (c + 1) G / grid).
+// kT steps (1, 2, 4 or 8) of one instance; CTA c of the persistent grid takes
+// the contiguous run of groups [c G / grid, (c + 1) G / grid), except for
+// 64-wide rows: there CTA c takes groups c, c + grid, c + 2 grid, ..., so that
+// the CTAs work on a band of neighbouring groups at a time and the halo chunks
+// they read from the tiles above and below are still in L2 (those rows start
+// on 16-byte boundaries, so nothing is lost by not handing row ends over).
 template <bool kLife, int kTW, int kT>
 __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, TileLayout lay, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
@@ -876,19 +962,25 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   make_transpose(threadIdx.x & 31u, keep, rot);
   init_barriers(smem, lay);
   uint32_t it = 0;
-  const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
-  const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
-  run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
+  if constexpr (kTW == 64) {
+    run_groups<kLife, kTW, kT>(p, lay, in, out, blockIdx.x, p.groups, gridDim.x, smem, keep, rot,
+                               it);
+  } else {
+    const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
+    const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
+    run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
+  }
   bulk_wait_all();
   settle_abort();
 }
 
-// kT steps (1 or 2) of many instances (each with its own fractal, level and
-// buffers) that share one tile-row instantiation, in a single persistent
+// kT steps (1, 2, 4 or 8) of many instances (each with its own fractal, level
+// and buffers) that share one tile-row instantiation, in a single persistent
 // launch.  parity selects the launch's input: buffer 0 or buffer 1.  CTA c
-// walks its schedule entries, each a contiguous run of groups of one
-// instance; the instance's description is copied to shared memory for the
-// run (its fields are read throughout the group loop).
+// walks its schedule entries, each a run of groups of one instance (g_first,
+// g_first + g_stride, ... below g_end); the instance's description is copied
+// to shared memory for the run (its fields are read throughout the group
+// loop).
 template <bool kLife, int kTW, int kT>
 __global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
@@ -910,7 +1002,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     __syncthreads();  // s_dev complete: run_groups reads its sizes before its own first barrier
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
-    run_groups<kLife, kTW, kT>(s_dev, lay, in, out, w.g_first, w.g_end, 1, smem, keep, rot, it);
+    run_groups<kLife, kTW, kT>(s_dev, lay, in, out, w.g_first, w.g_end, w.g_stride, smem, keep, rot,
+                               it);
   }
   bulk_wait_all();
   settle_abort();

@@ -38,14 +38,15 @@ def lib(tmp_path_factory):
     return L
 
 
-def schedule(lib, cells, groups, grid):
+def schedule(lib, cells, groups, grid, strided=False):
     cells = np.ascontiguousarray(cells, dtype=np.uint64)
     groups = np.ascontiguousarray(groups, dtype=np.uint64)
     cap = int(groups.sum()) + len(cells) * grid + 1
-    work = np.zeros((cap, 3), dtype=np.uint64)
+    work = np.zeros((cap, 4), dtype=np.uint64)
     start = np.zeros(grid + 1, dtype=np.uint32)
     n = lib.batch_schedule(cells.ctypes.data_as(P), groups.ctypes.data_as(P), len(cells), grid,
-                           work.ctypes.data_as(P), ctypes.c_uint64(cap), start.ctypes.data_as(P))
+                           int(strided), work.ctypes.data_as(P), ctypes.c_uint64(cap),
+                           start.ctypes.data_as(P))
     assert n >= 0
     return work[:n].astype(np.int64), start.astype(np.int64)
 
@@ -53,20 +54,22 @@ def schedule(lib, cells, groups, grid):
 def check(cells, groups, grid, work, start):
     cells, groups = np.asarray(cells, dtype=np.int64), np.asarray(groups, dtype=np.int64)
     assert start[0] == 0 and start[-1] == len(work) and np.all(np.diff(start) >= 0)
-    # exact cover, in (instance, group) order
+    # exact cover; contiguous runs come in (instance, group) order
     covered = [np.zeros(g, dtype=np.int64) for g in groups]
     prev = (-1, -1)
-    for inst, g0, g1 in work:
-        assert 0 <= g0 < g1 <= groups[inst]
-        assert (inst, g0) > prev
-        prev = (inst, g1 - 1)
-        covered[inst][g0:g1] += 1
+    for inst, g0, g1, step in work:
+        assert 0 <= g0 < g1 <= groups[inst] and step >= 1
+        if np.all(work[:, 3] == 1):
+            assert (inst, g0) > prev
+            prev = (inst, g1 - 1)
+        covered[inst][g0:g1:step] += 1
     assert all(np.all(c == 1) for c in covered)
     # balance: each CTA's cells are within one group of total / grid
     per_group = cells / groups
     total = cells.sum()
     for c in range(grid):
-        load = sum((g1 - g0) * per_group[inst] for inst, g0, g1 in work[start[c]:start[c + 1]])
+        load = sum(len(range(g0, g1, step)) * per_group[inst]
+                   for inst, g0, g1, step in work[start[c]:start[c + 1]])
         assert abs(load - total / grid) <= 2 * per_group.max() + 1e-6, (c, load, total / grid)
 
 
@@ -79,6 +82,9 @@ def test_random_mixes(lib, seed):
     grid = int(rng.choice([1, 7, 152, 304, 608]))
     work, start = schedule(lib, cells, groups, grid)
     check(cells, groups, grid, work, start)
+    assert np.all(work[:, 3] == 1)
+    work, start = schedule(lib, cells, groups, grid, strided=True)
+    check(cells, groups, grid, work, start)
 
 
 def test_benchmark_mix_shape(lib):
@@ -88,8 +94,11 @@ def test_benchmark_mix_shape(lib):
     cells = [i.fractal.cells(i.r) for i in mix]
     groups = [max(1, -(-c // tile[i.fractal.name] // 32)) for c, i in zip(cells, mix)]
     for grid in (304, 608):
-        work, start = schedule(lib, cells, groups, grid)
-        check(cells, groups, grid, work, start)
+        for strided in (False, True):
+            work, start = schedule(lib, cells, groups, grid, strided)
+            check(cells, groups, grid, work, start)
+    # the large carpets are shared by runs of CTAs, which the strided form interleaves
+    assert np.any(work[:, 3] > 1)
 
 
 @pytest.mark.parametrize("cells,groups,grid", [
@@ -99,5 +108,13 @@ def test_benchmark_mix_shape(lib):
     ([6561] * 300, [1] * 300, 152),     # many one-group instances
 ], ids=["few-groups", "one-group-each", "one-instance", "many-small"])
 def test_edge_cases(lib, cells, groups, grid):
-    work, start = schedule(lib, cells, groups, grid)
-    check(cells, groups, grid, work, start)
+    for strided in (False, True):
+        work, start = schedule(lib, cells, groups, grid, strided)
+        check(cells, groups, grid, work, start)
+
+
+def test_strided_runs_interleave_one_instance(lib):
+    # one instance of 1000 groups over 7 CTAs: CTA q takes q, q + 7, ...
+    work, start = schedule(lib, [10 ** 6], [1000], 7, strided=True)
+    assert len(work) == 7 and np.all(np.diff(start) == 1)
+    assert [tuple(w) for w in work] == [(0, q, 1000, 7) for q in range(7)]

@@ -252,3 +252,61 @@ def test_multi_step_emulation_catches_a_dropped_existence_mask(lib):
         assert np.array_equal(emulate_passes(f, r, L, prog, state, adj, rule), want)
         assert not np.array_equal(emulate_passes(f, r, L, prog, state, adj, rule, mask=False),
                                   want)
+
+
+CHUNK_CASES = [(I.CARPET, 5, 3, oracle.MOORE), (I.CARPET, 6, 3, VON_NEUMANN),
+               (I.CARPET, 6, 3, ONE_SIDED), (I.FULL2, 7, 5, oracle.MOORE),
+               (I.TRIANGLE, 8, 6, oracle.MOORE)]
+
+
+def chunk_table(lib, f, r, L, nbhd, passes):
+    off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
+    caps = np.zeros(3, dtype=np.uint64)
+    assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
+    halo = int(caps[2])
+    info = np.zeros(11, dtype=np.uint32)
+    table = np.zeros(3 * halo + 1, dtype=np.uint32)
+    hoff = np.zeros(halo, dtype=np.uint32)
+    hdir = np.zeros(halo, dtype=np.uint8)
+    rc = lib.tile_chunks(f.s, f.k, ptr(off), r, L, nbhd, passes, ptr(info), ptr(table), ptr(hoff),
+                         ptr(hdir))
+    return rc, info, table, hoff, hdir
+
+
+@pytest.mark.parametrize("passes", [1, 2, 4, 8])
+@pytest.mark.parametrize("f,r,L,nbhd", CHUNK_CASES,
+                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CHUNK_CASES])
+def test_halo_chunk_table_serves_every_halo_cell(lib, f, r, L, nbhd, passes):
+    """64-wide rows gather the halo by 16-byte chunks of the adjacent tile: the
+    table must hold every halo word exactly once, in the chunk and at the byte
+    of its offset, under its own direction; other widths carry no table."""
+    prog = program(lib, f, r, L, nbhd, passes=passes)
+    if prog is None:
+        return
+    rc, info, table, hoff, hdir = chunk_table(lib, f, r, L, nbhd, passes)
+    assert rc == 0
+    nhalo, ndirs, W = prog["nhalo"], len(prog["dir_list"]), f.k ** ((r + 1) // 2)
+    assert np.array_equal(hoff[:nhalo], prog["halo_off"])
+    nch, cs = int(info[0]), info[1:11].astype(np.int64)
+    if prog["TW"] != 64:
+        assert nch == 0
+        return
+    assert nch > 0 and cs[0] == 0 and cs[ndirs] == nch and np.all(np.diff(cs) >= 0)
+    assert np.all(cs[ndirs:] == nch)
+    coff = table[:nch].astype(np.int64)
+    cstart = table[nch:2 * nch + 1].astype(np.int64)
+    cells = table[2 * nch + 1:2 * nch + 1 + nhalo].astype(np.int64)
+    assert cstart[0] == 0 and cstart[-1] == nhalo and np.all(np.diff(cstart) > 0)
+    assert np.all(coff % 16 == 0)
+    assert np.all(coff // W < prog["TH"]) and np.all(coff % W + 16 <= prog["TW"])
+    seen = np.zeros(nhalo, dtype=np.int64)
+    for j in range(ndirs):
+        assert np.all(np.diff(coff[cs[j]:cs[j + 1]]) > 0)   # distinct, increasing
+        for c in range(cs[j], cs[j + 1]):
+            ent = cells[cstart[c]:cstart[c + 1]]
+            h, byte = ent & 0xFFFF, ent >> 16
+            assert np.all(np.diff(h) > 0)                    # ring by ring
+            assert np.all(hdir[h] == j)
+            assert np.all(coff[c] + byte == prog["halo_off"][h])
+            seen[h] += 1
+    assert np.all(seen == 1)

@@ -84,6 +84,8 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   B.slots_cap = z.slots;
   B.halo_cap = z.halo;
   B.passes = passes;
+  std::vector<uint32_t> chunks(3 * z.halo + 1);
+  B.chunks = chunks.data();
   TileSpec sp;
   const int rc = sq_tile_build(f, L, B, sp);
   if (rc) return rc;
@@ -98,6 +100,33 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
     Y[c] = vY[c];
   }
   memcpy(dir_list, sp.dir_list, 9);
+  return SQUEEZE_OK;
+}
+
+// The halo chunk table of the level-L program (built for 64-wide rows only):
+// info = (nchunks, chunk_start[0..9]); table = nchunks chunk offsets, nchunks
+// + 1 cell ranges, nhalo cells (halo word | byte << 16), 3 * halo + 1 words at
+// most; halo_off and halo_dir as in tile_program.
+int tile_chunks(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L,
+                uint32_t nbhd, uint32_t passes, uint32_t *info, uint32_t *table,
+                uint32_t *halo_off, uint8_t *halo_dir) {
+  FracDev f;
+  if (!fill(s, k, off, r, nbhd, f)) return SQUEEZE_ERR_INVALID_ARG;
+  TileBuildSizes z;
+  sq_tile_build_sizes(f, L, z);
+  std::vector<int32_t> inv(z.box);
+  std::vector<uint32_t> vX(z.cells), vY(z.cells), refs((z.slots + z.halo) * 8), order(z.halo),
+      rank(z.halo);
+  std::vector<uint64_t> key(z.halo), sorted(z.halo);
+  std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
+  TileBuild B = {inv.data(), vX.data(),  vY.data(),  refs.data(), key.data(),  sorted.data(),
+                 order.data(), rank.data(), refs16.data(), halo_off, halo_dir, z.box,
+                 z.cells,      z.slots,     z.halo,        passes,   table};
+  TileSpec sp;
+  const int rc = sq_tile_build(f, L, B, sp);
+  if (rc) return rc;
+  info[0] = sp.nchunks;
+  memcpy(info + 1, sp.chunk_start, sizeof(sp.chunk_start));
   return SQUEEZE_OK;
 }
 
