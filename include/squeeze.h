@@ -167,8 +167,8 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
 
 /* squeeze_set_max_steps_per_launch -- the most steps one launch of the tiled
  * kernel may advance: 1, 2, 4 or 8, or 0 for the default (the most whose
- * kernel keeps the CTAs per SM of the one-step kernel; its shared memory grows
- * with the halo rings each further step needs).  The result of squeeze_step
+ * kernel keeps the CTAs per SM of the one-step kernel, or 4 if that has more;
+ * its shared memory grows with the halo rings each further step needs).  The result of squeeze_step
  * does not depend on it.  INVALID_ARG for other values. */
 int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps);
 
@@ -179,7 +179,10 @@ int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps);
  * tiled kernel); *launches = kernel launches it enqueued; by_steps[i] (four
  * entries) = how many of them advanced 2^i steps (the tiled kernel runs n
  * steps as launches of 8, 4, 2 and 1 steps whose count has the parity of n:
- * n = 100 is 12 launches of 8 steps and 2 of 2).  Any pointer may be NULL.
+ * n = 100 is 12 launches of 8 steps and 2 of 2).  For fractals whose tiles
+ * have 64-wide rows (the carpet) *launches also counts one launch that writes
+ * the border records of the input (the halo the first step reads), which
+ * advances no step.  Any pointer may be NULL.
  * INVALID_ARG for a null handle. */
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
                            uint64_t *by_steps);

@@ -182,7 +182,7 @@ int setup(squeeze_batch *b) {
       if (sq_tile_kind(specs[i]) != kind) continue;
       const TileSpec &sp = specs[i];
       const squeeze_handle *h = b->items[i].h;
-      TileLayout l = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp));
+      TileLayout l = sq_tile_layout_of(sp);
       p.lay = first ? l : sq_tile_layout_max(p.lay, l);
       first = false;
       p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
@@ -249,6 +249,14 @@ int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
   uint64_t counts[4];
   sq_launch_plan(n_steps, passes, counts);
   const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
+  // 64-wide rows read their halo from border records: first those of the
+  // input (one records-only launch of that instantiation)
+  for (const BatchPlan &p : b->plans) {
+    if (p.kind != 64 || !total) continue;
+    int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay, p.grid,
+                             p.threads, p.life, p.kind, 1, (uint32_t)(b->parity & 1u), 1, st);
+    if (rc) return rc;
+  }
   for (uint64_t t = 0, i = 3, used = 0; t < total; ++t) {
     while (used == counts[i]) {   // largest launches first
       --i;
@@ -259,7 +267,7 @@ int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
     const uint32_t steps = 1u << i;
     for (const BatchPlan &p : b->plans) {
       int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
-                               p.grid, p.threads, p.life, p.kind, steps, parity, st);
+                               p.grid, p.threads, p.life, p.kind, steps, parity, 0, st);
       if (rc) return rc;
     }
   }

@@ -43,9 +43,9 @@ int sq_batch_occupancy(bool life, int kind, uint32_t steps, int threads, uint32_
 int sq_batch_launch(const TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const BatchWork *d_work, const uint32_t *d_sched, const TileLayout &lay,
                     int grid, int threads, bool life, int kind, uint32_t steps, uint32_t parity,
-                    cudaStream_t st) {
+                    uint32_t mode, cudaStream_t st) {
   TileLayout l = lay;
-  void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity};
+  void *args[] = {&d_devs, &d_buf0, &d_buf1, &d_work, &d_sched, &l, &parity, &mode};
   SQ_CUDA(cudaLaunchKernel(batch_kernel_for(life, kind, steps), dim3(grid), dim3(threads), args,
                            l.smem, st));
   SQ_CUDA(cudaGetLastError());

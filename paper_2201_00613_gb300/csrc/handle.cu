@@ -236,6 +236,12 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
   uint64_t counts[4] = {n_steps, 0, 0, 0};
   if (kind == SQUEEZE_STEP_TILED) sq_launch_plan(n_steps, sq_tiled_passes(h), counts);
   const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
+  // 64-wide rows: the border records of the input first (one extra launch)
+  int extra = 0;
+  if (kind == SQUEEZE_STEP_TILED && total) {
+    const int rc = sq_tiled_begin(h, d_buf0, st, &extra);
+    if (rc) return rc;
+  }
   uint8_t *a = d_buf0, *b = d_buf1;
   for (uint64_t t = 0, i = 3, used = 0; t < total; ++t) {
     while (used == counts[i]) {   // largest launches first
@@ -255,7 +261,7 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     a = b;
     b = tmp;
   }
-  h->last_launches = total;
+  h->last_launches = total + (uint64_t)extra;
   for (int i = 0; i < 4; ++i) h->last_counts[i] = counts[i];
   return SQUEEZE_OK;
 }

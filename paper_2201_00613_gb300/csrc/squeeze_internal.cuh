@@ -222,6 +222,18 @@ struct TiledDev {
   // direction j owns chunks [chunk_start[j], chunk_start[j + 1]).
   uint32_t nchunks;
   uint32_t chunk_start[10];
+  // Border records (64-wide rows): each launch also writes, per tile, the
+  // states of its cells that adjacent tiles read as halo, rec_words words per
+  // tile, segment j (words [rec_seg[j], rec_seg[j+1])) holding what the tile
+  // adjacent in direction j of it reads, bit i of word w = halo cell 32 w + i
+  // of that segment.  The table after the chunk table maps each record bit to
+  // (exporting slot | halo word << 16).  rec[0]: records of the input state
+  // (null: gather by chunks), rec[1]: records of the output state; mode 1
+  // writes the input's records to rec[1] and nothing else.
+  uint32_t rec_words;
+  uint32_t rec_seg[10];
+  uint32_t *rec[2];
+  uint32_t mode;
   uint32_t pad_;
 };
 
@@ -235,6 +247,7 @@ struct TileLayout {
   uint32_t hdir_bytes;       // halo direction indices (one byte per halo word)
   uint32_t rowa_bytes;       // per-row alignment offsets (two sets)
   uint32_t carry_bytes;      // per-row 16-byte chunk handed to the next group
+  uint32_t z_bytes;          // final-step words of the last two groups (border records)
   uint32_t stage_bytes;      // one staging buffer (two are used)
   uint32_t smem;             // total dynamic shared memory
 };
@@ -251,6 +264,8 @@ struct TileSpec {
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint32_t nchunks;          // chunk table of the halo (64-wide rows), 0 if none
   uint32_t chunk_start[10];  // chunks of direction j: [chunk_start[j], chunk_start[j+1])
+  uint32_t rec_words;        // border record words per tile (64-wide rows), 0 if none
+  uint32_t rec_seg[10];      // record words read by direction j: [rec_seg[j], rec_seg[j+1])
   uint64_t groups;
   size_t smem;
   int threads;
@@ -279,8 +294,9 @@ struct TileBuild {
   // rings 2..P are built too, and references for rings 1..P-1 (refs and
   // refs16 then need (slots + halo_cap) * 8 entries).
   uint32_t passes;
-  // Optional (64-wide rows): the halo's chunk table, 3 * halo_cap + 1 words
-  // (layout as in TiledDev); null builds a program without one.
+  // Optional (64-wide rows): the halo's chunk table and border-record table,
+  // at most 4 * halo_cap + 289 words (layout as in TiledDev); null builds a
+  // program without them.
   uint32_t *chunks;
 };
 
@@ -345,6 +361,9 @@ int sq_tiled_prepare(squeeze_handle *h);
 // passes the program was built for (sq_tiled_passes).
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                          uint32_t steps, cudaStream_t st);
+// Border records of a squeeze_step call's input (before its tiled launches;
+// *launches = 1 if a records-only launch was made).
+int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, int *launches);
 uint32_t sq_tiled_passes(const squeeze_handle *h);
 // Launches of n steps at up to `passes` steps each: counts[i] launches of
 // 2^i steps (i = 0..3), with a launch count of n's parity (every launch swaps
@@ -361,7 +380,9 @@ sq::TiledDev sq_tiled_dev(const sq::FracDev &f, const sq::Rule &rule, const sq::
                           const uint16_t *refs, const uint32_t *halo_off,
                           const uint8_t *halo_dir, const uint32_t *adj, int *status);
 sq::TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch,
-                              uint32_t table_words = 0);
+                              uint32_t table_words = 0, uint32_t z_words = 0);
+// Shared-memory layout of a program (its tables and record buffers included).
+sq::TileLayout sq_tile_layout_of(const sq::TileSpec &sp);
 // Words of a program's halo chunk table (0 when it has none).
 uint32_t sq_tile_table_words(const sq::TileSpec &sp);
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &b);
@@ -381,7 +402,7 @@ int sq_batch_occupancy(bool life, int kind, uint32_t steps, int threads, uint32_
 int sq_batch_launch(const sq::TiledDev *d_devs, uint8_t *const *d_buf0, uint8_t *const *d_buf1,
                     const sq::BatchWork *d_work, const uint32_t *d_sched,
                     const sq::TileLayout &lay, int grid, int threads, bool life, int kind,
-                    uint32_t steps, uint32_t parity, cudaStream_t st);
+                    uint32_t steps, uint32_t parity, uint32_t mode, cudaStream_t st);
 bool sq_tiled_level_fits(const squeeze_handle *h, uint32_t level);
 int sq_launch_step_tc(const squeeze_handle *h, const uint8_t *in, uint8_t *out, cudaStream_t st);
 int sq_launch_map_tc(const squeeze_handle *h, int direction, const void *in, void *out,

@@ -44,6 +44,11 @@ struct TiledProgram {
   uint32_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
   uint8_t *d_halo_dir;      // nhalo indices into dir_list
   uint32_t *d_adj;          // ndirs x tiles: adjacent tile index, or ~0 (hole / off the box)
+  // Border records (64-wide rows): tiles x rec_words words each, one per state
+  // buffer of a squeeze_step call; rec_cur is the one of the next launch's
+  // input (the launches of a call alternate, like the buffers).
+  uint32_t *d_rec[2];
+  int rec_cur;
 };
 
 namespace sq {
@@ -87,18 +92,19 @@ using namespace sq;
 
 static uint32_t layout_total(const TileLayout &l) {
   return 2 * l.win_bytes + l.hoff_bytes + l.hdir_bytes + 16 + l.rowa_bytes + l.carry_bytes +
-         2 * l.stage_bytes;
+         l.z_bytes + 2 * l.stage_bytes;
 }
 
 // Word buffer: slots, halo words, the zero word and 9 per-direction masks.
 TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t pitch,
-                          uint32_t table_words) {
+                          uint32_t table_words, uint32_t z_words) {
   TileLayout l;
   l.win_bytes = (uint32_t)((((size_t)slots + nhalo + 1 + 9) * 4 + 15) & ~(size_t)15);
   l.hoff_bytes = (uint32_t)((((size_t)nhalo + table_words) * 4 + 15) & ~(size_t)15);
   l.hdir_bytes = (uint32_t)(((size_t)nhalo + 15) & ~(size_t)15);
   l.rowa_bytes = (uint32_t)(((size_t)2 * TH + 15) & ~(size_t)15);
   l.carry_bytes = 16u * TH;
+  l.z_bytes = (uint32_t)(((size_t)z_words * 4 + 15) & ~(size_t)15);
   // + slack: the last lane's whole-word reads and writes of the last row run up
   // to 8 bytes past it (a 27-wide row: 9 words from a 4-byte boundary below a
   // row start at most 15 bytes into the pitch, and 32 * 27 + 15 <= pitch)
@@ -108,7 +114,12 @@ TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t 
 }
 
 uint32_t sq_tile_table_words(const TileSpec &sp) {
-  return sp.nchunks ? 2u * sp.nchunks + 1u + sp.nhalo : 0u;
+  return (sp.nchunks ? 2u * sp.nchunks + 1u + sp.nhalo : 0u) + 32u * sp.rec_words;
+}
+
+TileLayout sq_tile_layout_of(const TileSpec &sp) {
+  return sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp),
+                        sp.rec_words ? 2u * sp.slots : 0u);
 }
 
 TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
@@ -118,6 +129,7 @@ TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
   l.hdir_bytes = a.hdir_bytes > b.hdir_bytes ? a.hdir_bytes : b.hdir_bytes;
   l.rowa_bytes = a.rowa_bytes > b.rowa_bytes ? a.rowa_bytes : b.rowa_bytes;
   l.carry_bytes = a.carry_bytes > b.carry_bytes ? a.carry_bytes : b.carry_bytes;
+  l.z_bytes = a.z_bytes > b.z_bytes ? a.z_bytes : b.z_bytes;
   l.stage_bytes = a.stage_bytes > b.stage_bytes ? a.stage_bytes : b.stage_bytes;
   l.smem = layout_total(l);
   return l;
@@ -216,6 +228,10 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
     for (int i = 0; i < 10; ++i) d.ring_start[k][i] = sp.ring_start[k][i];
   d.nchunks = sp.nchunks;
   for (int i = 0; i < 10; ++i) d.chunk_start[i] = sp.chunk_start[i];
+  d.rec_words = sp.rec_words;
+  for (int i = 0; i < 10; ++i) d.rec_seg[i] = sp.rec_seg[i];
+  d.rec[0] = d.rec[1] = nullptr;
+  d.mode = 0;
   return d;
 }
 
@@ -225,6 +241,8 @@ void sq_tiled_free(TiledProgram *p) {
   cudaFree(p->d_halo_off);
   cudaFree(p->d_halo_dir);
   cudaFree(p->d_adj);
+  cudaFree(p->d_rec[0]);
+  cudaFree(p->d_rec[1]);
   delete p;
 }
 
@@ -320,6 +338,32 @@ static void build_chunks(uint32_t nhalo, const uint32_t *halo_off, const uint8_t
   for (uint32_t v : coff) *o++ = v;
   for (uint32_t v : cstart) *o++ = v;
   for (uint32_t v : cells) *o++ = v;
+}
+
+// The border-record table for 64-wide rows.  Segment j of a tile's record
+// holds, in halo-word order, the states of the tile's cells that the tile
+// adjacent to it in direction j reads as its direction-j halo (the halo words
+// h with halo_dir[h] == j, all rings): ceil(n_j / 32) words from rec_seg[j].
+// out[32 w + i] for record bit i of word w = exporting slot (the slot word of
+// local cell ly * 64 + lx, with halo_off = ly * W + lx) | halo word << 16;
+// 0xFFFFFFFF pads a segment's last word.
+static void build_records(uint64_t W, uint32_t nhalo, const uint32_t *halo_off,
+                          const uint8_t *halo_dir, TileSpec &sp, uint32_t *out) {
+  uint32_t words = 0;
+  for (uint32_t j = 0; j < sp.ndirs; ++j) {
+    sp.rec_seg[j] = words;
+    uint32_t n = 0;
+    for (uint32_t h = 0; h < nhalo; ++h)
+      if (halo_dir[h] == j) {
+        const uint32_t lc = (uint32_t)(halo_off[h] / W) * 64u + (uint32_t)(halo_off[h] % W);
+        out[32u * words + n++] = tile_slot_of(lc, 64u, 1u, 2u) | (h << 16);
+      }
+    const uint32_t used = (n + 31u) / 32u;
+    for (uint32_t i = n; i < 32u * used; ++i) out[32u * words + i] = 0xFFFFFFFFu;
+    words += used;
+  }
+  for (uint32_t j = sp.ndirs; j < 10; ++j) sp.rec_seg[j] = words;
+  sp.rec_words = words;
 }
 
 // Host construction of the level-L neighbour program (see the file comment):
@@ -475,8 +519,12 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.groups_per_band = (sp.tiles_x + 31) / 32;
   sp.groups = (uint64_t)sp.groups_per_band * sp.tiles_y;
   sp.pitch = pitch_for(TW);
-  if (TW == 64 && B.chunks && nhalo) build_chunks(nhalo, B.halo_off, B.halo_dir, sp, B.chunks);
-  sp.smem = sq_tile_layout(slots, nhalo, TH, sp.pitch, sq_tile_table_words(sp)).smem;
+  if (TW == 64 && B.chunks && nhalo) {
+    build_chunks(nhalo, B.halo_off, B.halo_dir, sp, B.chunks);
+    build_records(f.W, nhalo, B.halo_off, B.halo_dir, sp,
+                  B.chunks + 2u * sp.nchunks + 1u + nhalo);
+  }
+  sp.smem = sq_tile_layout_of(sp).smem;
   if (sp.groups >= (1ull << 32) || sp.smem > kTiledSmemLimit) return SQUEEZE_ERR_UNSUPPORTED;
   // Whole warps, one tile row per warp per pass: pick 6..12 warps to balance TH rows.
   // Shared slot words: two slot rows per warp, 4..8 warps.
@@ -533,7 +581,7 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   if (sp.TW == 64 && sp.nhalo && !sp.nchunks) return SQUEEZE_ERR_INVALID_ARG;  // no chunk table
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
-  TileLayout lay = sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp));
+  TileLayout lay = sq_tile_layout_of(sp);
   void *args[] = {&dd, &lay, &in, &out};
   const int grid = sp.grid[steps_index(steps)][life ? 1 : 0];
   SQ_CUDA(cudaLaunchKernel(tiled_kernel_for(life, sp.TW, sp.rpw, steps), dim3(grid),
@@ -556,7 +604,7 @@ int sq_tiled_prepare(squeeze_handle *h) {
       rank(z.halo);
   std::vector<uint64_t> keys(z.halo), sorted(z.halo);
   std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
-  std::vector<uint32_t> halo_off(z.halo), chunks(3 * z.halo + 1);
+  std::vector<uint32_t> halo_off(z.halo), chunks(4 * z.halo + 289);
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
@@ -564,16 +612,17 @@ int sq_tiled_prepare(squeeze_handle *h) {
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
   // Steps per launch: by default the most (8, 4, 2) whose program builds and
-  // whose kernel keeps the CTAs per SM of the one-step kernel (its shared
-  // memory grows with the halo rings); with squeeze_set_max_steps_per_launch
-  // the most up to that limit that build.
+  // whose kernel keeps the CTAs per SM of the one-step kernel, or 4 if that
+  // has more (its shared memory grows with the halo rings; 4 CTAs per SM is
+  // what the default tile level is sized for); with
+  // squeeze_set_max_steps_per_launch the most up to that limit that build.
   int rc = SQUEEZE_ERR_UNSUPPORTED, occ1 = 0;
   {
     B.passes = 1;
     TileSpec one;
     rc = sq_tile_build(f, L, B, one);
     if (rc == SQUEEZE_OK) rc = sq_tile_launch_config(one, h->device);
-    if (rc == SQUEEZE_OK) occ1 = one.occ[0][1];
+    if (rc == SQUEEZE_OK) occ1 = one.occ[0][1] < 4 ? one.occ[0][1] : 4;
   }
   for (uint32_t passes = h->max_passes ? h->max_passes : kTiledPasses; rc == SQUEEZE_OK; passes /= 2) {
     B.passes = passes;
@@ -607,6 +656,8 @@ int sq_tiled_prepare(squeeze_handle *h) {
     e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
   uint64_t tiles = (uint64_t)sp.tiles_x * sp.tiles_y;
   if (e == cudaSuccess && sp.ndirs) e = cudaMalloc(&p->d_adj, (size_t)sp.ndirs * tiles * 4);
+  for (int i = 0; i < 2 && e == cudaSuccess && sp.rec_words; ++i)
+    e = cudaMalloc(&p->d_rec[i], (size_t)sp.rec_words * tiles * 4);
   if (e != cudaSuccess) {
     sq_tiled_free(p);
     return sq_cuda_fail(e);
@@ -629,13 +680,36 @@ int sq_tiled_prepare(squeeze_handle *h) {
 
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                          uint32_t steps, cudaStream_t st) {
-  const TiledProgram *p = h->tiled;
+  TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
   if (h->wait_ns) d.wait_ns = h->wait_ns;
   d.fault = h->fault;
-  return sq_tile_launch(d, p->spec, in, out, steps, st);
+  if (p->spec.rec_words) {   // records of the input, and of the output for the next launch
+    d.rec[0] = p->d_rec[p->rec_cur];
+    d.rec[1] = p->d_rec[p->rec_cur ^ 1];
+  }
+  const int rc = sq_tile_launch(d, p->spec, in, out, steps, st);
+  if (rc == SQUEEZE_OK) p->rec_cur ^= 1;
+  return rc;
+}
+
+// Before the launches of a squeeze_step call: the border records of its input
+// (one records-only launch; nothing for programs without records).
+int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, int *launches) {
+  TiledProgram *p = h->tiled;
+  *launches = 0;
+  if (!p || !p->spec.rec_words) return SQUEEZE_OK;
+  TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
+                            p->d_adj, h->d_status);
+  if (h->wait_ns) d.wait_ns = h->wait_ns;
+  d.fault = h->fault;
+  d.rec[1] = p->d_rec[0];
+  d.mode = 1;
+  p->rec_cur = 0;
+  *launches = 1;
+  return sq_tile_launch(d, p->spec, in, const_cast<uint8_t *>(in), 1, st);
 }
 
 uint32_t sq_tiled_passes(const squeeze_handle *h) { return h->tiled ? h->tiled->spec.passes : 1u; }
@@ -664,6 +738,8 @@ int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   *d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
                     h->d_status);
+  d->rec[0] = p->d_rec[0];   // records of buffer 0 and of buffer 1
+  d->rec[1] = p->d_rec[1];
   if (h->wait_ns) d->wait_ns = h->wait_ns;
   d->fault = h->fault;
   *sp = p->spec;

@@ -407,27 +407,93 @@ __device__ __forceinline__ uint32_t pack_aligned(const uint32_t *stage32, uint32
   return acc;
 }
 
-// Pack one 32-byte half of a 64-byte tile row (16-byte aligned): 8 words.
-__device__ __forceinline__ uint32_t pack_half64(const uint32_t *stage32, uint32_t o) {
-  const uint4 lo = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2));
-  const uint4 hi = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2) + 4);
-  const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-  uint32_t acc = 0, acc1 = 0;
-#pragma unroll
-  for (int j = 0; j < 8; j += 2) {
-    acc |= (w[j] & 0x01010101u) << j;
-    acc1 |= (w[j + 1] & 0x01010101u) << (j + 1);
+// ---- border records (64-wide rows) -----------------------------------------
+//
+// rtab: the record table in shared memory (per record bit: exporting slot |
+// halo word << 16, or ~0 for padding).  A tile's record word w holds at bit i
+// the state of the cell of record bit 32 w + i, so one 32 x 32 transpose turns
+// the group's words into the 32 tiles' record words and back.
+
+// The records of the group's tiles from its words (bit l of words[s] = slot
+// s of tile l); warp-strided over record words, lane l stores its tile's.
+__device__ __forceinline__ void build_records(const TiledDev &p, const uint32_t *words,
+                                              const Group &G, const uint32_t *rtab,
+                                              uint32_t *rec_out, unsigned lane, unsigned warp,
+                                              unsigned nw, const uint32_t *keep,
+                                              const uint32_t *rot) {
+  const uint32_t R = p.rec_words;
+  const uint64_t t0 = (uint64_t)G.ty * p.tiles_x + G.tx0;
+  for (uint32_t w = warp; w < R; w += nw) {
+    const uint32_t e = rtab[32u * w + lane];
+    uint32_t x = e == 0xFFFFFFFFu ? 0u : words[e & 0xFFFFu];
+    transpose32_n<1>(&x, keep, rot);
+    if (lane < G.ntiles) rec_out[(t0 + lane) * R + w] = x;
   }
-  return acc | acc1;
 }
 
-// The inverse of pack_half64.
-__device__ __forceinline__ void unpack_half64(uint32_t *stage32w, uint32_t o, uint32_t y) {
-  uint32_t u[8];
+// Halo words of direction j from the records of the lanes' adjacent tiles t
+// (~0: none, all dead): lane l loads record word w of its tile, and after the
+// transpose lane i holds the word of record bit 32 w + i, whose halo word the
+// table names.  Words of rings past hlimit are skipped.
+__device__ __forceinline__ void gather_records(const TiledDev &p, uint32_t t, uint32_t j,
+                                               const uint32_t *rtab, const uint32_t *rec_in,
+                                               uint32_t *words, uint32_t hlimit, unsigned lane,
+                                               const uint32_t *keep, const uint32_t *rot) {
+  const uint32_t R = p.rec_words, w1 = p.rec_seg[j + 1];
+  if (t != ~0u && t >= p.tiles) {
+    flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
+    t = ~0u;
+  }
+  for (uint32_t w = p.rec_seg[j]; w < w1; w += 4) {
+    uint32_t x[4];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) u[t] = (y >> t) & 0x01010101u;
-  *reinterpret_cast<uint4 *>(stage32w + (o >> 2)) = make_uint4(u[0], u[1], u[2], u[3]);
-  *reinterpret_cast<uint4 *>(stage32w + (o >> 2) + 4) = make_uint4(u[4], u[5], u[6], u[7]);
+    for (int i = 0; i < 4; ++i)
+      x[i] = (w + i < w1 && t != ~0u) ? __ldg(rec_in + (uint64_t)t * R + w + i) : 0u;
+    transpose32_n<4>(x, keep, rot);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (w + i < w1) {
+        const uint32_t e = rtab[32u * (w + i) + lane], h = e >> 16;
+        if (e != 0xFFFFFFFFu && h < hlimit) words[h] = x[i];
+      }
+    }
+  }
+}
+
+// Pack a 64-byte tile row at o (16-byte aligned; lane = tile, the lanes' rows
+// 64 bytes apart) into two words, one per 32-byte half: bit 8b + j of a half's
+// word <- byte 4j + b of the half.  Lane l reads the row's four 16-byte chunks
+// starting at chunk rot = (l >> 1) & 3, so the 8 lanes of each phase of a
+// 16-byte shared load touch 8 different bank groups (reading chunk c in every
+// lane would put lanes l, l + 2, l + 4, l + 6 on the same banks).
+__device__ __forceinline__ void pack_row64(const uint32_t *stage32, uint32_t o, uint32_t rot,
+                                           uint32_t &lo, uint32_t &hi) {
+  uint32_t a0 = 0, a1 = 0;
+#pragma unroll
+  for (uint32_t c = 0; c < 4; ++c) {
+    const uint32_t q = (c + rot) & 3u;   // chunk of the row read at this step
+    const uint4 v = *reinterpret_cast<const uint4 *>(stage32 + (o >> 2) + q * 4u);
+    const uint32_t j = (q & 1u) * 4u;    // its first word within its half
+    const uint32_t m = ((v.x & 0x01010101u) << j) | ((v.y & 0x01010101u) << (j + 1u)) |
+                       ((v.z & 0x01010101u) << (j + 2u)) | ((v.w & 0x01010101u) << (j + 3u));
+    a0 |= (q >> 1) ? 0u : m;
+    a1 |= (q >> 1) ? m : 0u;
+  }
+  lo = a0;
+  hi = a1;
+}
+
+// The inverse of pack_row64, with the same chunk rotation.
+__device__ __forceinline__ void unpack_row64(uint32_t *stage32w, uint32_t o, uint32_t rot,
+                                             uint32_t lo, uint32_t hi) {
+#pragma unroll
+  for (uint32_t c = 0; c < 4; ++c) {
+    const uint32_t q = (c + rot) & 3u;
+    const uint32_t y = (q >> 1) ? hi : lo, j = (q & 1u) * 4u;
+    *reinterpret_cast<uint4 *>(stage32w + (o >> 2) + q * 4u) =
+        make_uint4((y >> j) & 0x01010101u, (y >> (j + 1u)) & 0x01010101u,
+                   (y >> (j + 2u)) & 0x01010101u, (y >> (j + 3u)) & 0x01010101u);
+  }
 }
 
 // The inverse of pack_aligned: the low kTW / 4 bit planes of y, as whole words.
@@ -498,7 +564,8 @@ __device__ __forceinline__ void unpack_row(uint32_t *stage32w, uint8_t *stage, u
 // Shared-memory carve-up of the tiled kernel (offsets in bytes; every region
 // starts at a multiple of 16): two word buffers, halo offsets, halo
 // directions, 2 mbarriers, two sets of row offsets, the row-end carry chunks,
-// two staging buffers.
+// the final-step words of two groups (border records only), two staging
+// buffers.
 struct SmemPtrs {
   unsigned char *win0;
   uint32_t *hoff;
@@ -506,6 +573,7 @@ struct SmemPtrs {
   uint64_t *mbar;
   uint8_t *rowa;
   uint8_t *carry;
+  uint32_t *z;      // final-step words of the last two groups (border records)
   uint8_t *stage0;
 };
 
@@ -524,6 +592,8 @@ __device__ __forceinline__ SmemPtrs carve(unsigned char *smem, const TileLayout 
   off += lay.rowa_bytes;
   q.carry = smem + off;
   off += lay.carry_bytes;
+  q.z = reinterpret_cast<uint32_t *>(smem + off);
+  off += lay.z_bytes;
   q.stage0 = smem + off;
   return q;
 }
@@ -579,7 +649,9 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
                                            uint8_t *__restrict__ out, uint64_t g_first,
                                            uint64_t g_end, uint64_t g_stride,
                                            unsigned char *smem, const uint32_t *keep,
-                                           const uint32_t *rot, uint32_t &it) {
+                                           const uint32_t *rot, uint32_t &it,
+                                           const uint32_t *rec_in, uint32_t *rec_out,
+                                           bool rec_only) {
   // Tile rows per slot word (kTW = 8, 16: the rows of 4 or 2 tile rows share
   // one word), slot rows in flight per warp, and tile rows per write-back batch.
   // (kTW = 64: each tile row is two slot words, its left and right halves; a
@@ -620,7 +692,15 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   constexpr bool kChunked = kTW == 64;
   const uint32_t ntab = nhalo + (kChunked && p.nchunks ? 2u * p.nchunks + 1u + nhalo : 0u);
   const uint32_t *ctab = hoff + nhalo;
-  for (uint32_t i = tid; i < ntab; i += nthreads) hoff[i] = p.halo_off[i];
+  // Border records (64-wide rows with a record table): read the input's
+  // records for the halo (rec_in; else gather by chunks), write the output's
+  // (rec_out); rec_only: write the input's records to rec_out and nothing else.
+  const uint32_t rtab_words = kChunked && p.rec_words ? 32u * p.rec_words : 0u;
+  const uint32_t *rtab = ctab + (kChunked && p.nchunks ? 2u * p.nchunks + 1u + nhalo : 0u);
+  const bool use_rec = rtab_words != 0u && rec_in != nullptr;
+  const bool produce = rtab_words != 0u && rec_out != nullptr && !rec_only;
+  uint32_t *zbuf = q.z;
+  for (uint32_t i = tid; i < ntab + rtab_words; i += nthreads) hoff[i] = p.halo_off[i];
   if constexpr (kT > 1)
     for (uint32_t i = tid; i < p.ring_end[kT - 1]; i += nthreads) hdir[i] = p.halo_dir[i];
   if (tid == 0) {
@@ -707,8 +787,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     for (uint32_t j = warp + nw; j < p.ndirs; j += nw) {
       const uint32_t t = adjacent_of(p, G, j, lane);
       if constexpr (kChunked) {
-        gather_chunks(p, tile_base(p, TW, t), ctab, p.chunk_start[j], p.chunk_start[j + 1],
-                      win + slots, hlimit, in, lane);
+        if (rec_only) {
+        } else if (use_rec) {
+          gather_records(p, t, j, rtab, rec_in, win + slots, hlimit, lane, keep, rot);
+        } else {
+          gather_chunks(p, tile_base(p, TW, t), ctab, p.chunk_start[j], p.chunk_start[j + 1],
+                        win + slots, hlimit, in, lane);
+        }
       } else {
         gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff,
                                 win + slots, in, lane);
@@ -746,12 +831,17 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       for (int k = 0; k < kR; ++k) {
         const uint32_t vr = vrow(u0, k);
         if constexpr (kWPR > 1) {
-          acc[k] = 0;
-          if (vr < VR) {
-            const uint32_t ly = vr / kWPR, a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
-            if (lane == 0 && (vr % kWPR) == 0) rowa[b * p.TH + ly] = (uint8_t)a;
-            if (lane < ntiles)
-              acc[k] = pack_half64(stage32, ly * p.pitch + a + lane * 64u + (vr % kWPR) * 32u);
+          // entries k, k + 1 are the two halves of one tile row (a row starts on
+          // a 64-byte boundary: its alignment offset a is 0)
+          if (k % 2 == 0) {
+            acc[k] = acc[k + 1] = 0;
+            if (vr < VR) {
+              const uint32_t ly = vr / kWPR, a = ((uint32_t)G.row0 + ly * (uint32_t)W) & 15u;
+              if (lane == 0) rowa[b * p.TH + ly] = (uint8_t)a;
+              if (lane < ntiles)
+                pack_row64(stage32, ly * p.pitch + a + lane * 64u, (lane >> 1) & 3u, acc[k],
+                           acc[k + 1]);
+            }
           }
         } else if constexpr (kRPW == 1) {
           const uint32_t ly = vr;
@@ -780,8 +870,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
         if (vrow(u0, k) < VR) win[vrow(u0, k) * 32u + lane] = acc[k];
     }
     if (kChunked && warp < p.ndirs) {
-      gather_chunks(p, tile_base(p, TW, t_cur), ctab, p.chunk_start[warp],
-                    p.chunk_start[warp + 1], win + slots, hlimit, in, lane);
+      if (rec_only) {
+      } else if (use_rec) {
+        gather_records(p, t_cur, warp, rtab, rec_in, win + slots, hlimit, lane, keep, rot);
+      } else {
+        gather_chunks(p, tile_base(p, TW, t_cur), ctab, p.chunk_start[warp],
+                      p.chunk_start[warp + 1], win + slots, hlimit, in, lane);
+      }
       t_cur = t_next;
     } else if (!kChunked && warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp];
@@ -803,6 +898,18 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     if (warp == 0 && g + g_stride < g_end && !cta_aborted() && !withhold)
       issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
+    if constexpr (kChunked) {
+      if (rec_only) {   // the input's records from its packed words; no step
+        build_records(p, win, G, rtab, rec_out, lane, warp, nw, keep, rot);
+        continue;
+      }
+      // The previous group's records: its final-step words are complete, since
+      // every warp has passed this barrier (and nothing rewrites them before
+      // the next one).
+      if (produce && g != g_first)
+        build_records(p, zbuf + ((it - 1u) & 1u) * slots, group_at(p, TW, g - g_stride), rtab,
+                      rec_out, lane, warp, nw, keep, rot);
+    }
 
     // kT > 1: steps 1 .. kT-1 of the own slot rows and of the halo rings that
     // the later steps still need, alternating between X and Y.
@@ -836,6 +943,11 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 #pragma unroll
       for (int k = 0; k < kR; ++k)
         y[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, rbase, vrow(u0, k) * 32u + lane) : 0u;
+      if (kChunked && produce) {   // keep the final words for this group's records
+#pragma unroll
+        for (int k = 0; k < kR; ++k)
+          if (vrow(u0, k) < VR) zbuf[(it & 1u) * slots + vrow(u0, k) * 32u + lane] = y[k];
+      }
       transpose32_n<kR>(y, keep, rot);
       // Row offsets first: a shared load after the unpack's stores would wait for them.
       uint32_t arow[kR];
@@ -848,10 +960,9 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       for (int k = 0; k < kR; ++k) {
         const uint32_t vr = vrow(u0, k);
         if constexpr (kWPR > 1) {
-          if (vr < VR && lane < ntiles) {
-            const uint32_t ly = vr / kWPR;
-            unpack_half64(stage32w, ly * p.pitch + arow[k] + lane * 64u + (vr % kWPR) * 32u, y[k]);
-          }
+          if (k % 2 == 0 && vr < VR && lane < ntiles)
+            unpack_row64(stage32w, vr / kWPR * p.pitch + arow[k] + lane * 64u, (lane >> 1) & 3u,
+                         y[k], y[k + 1]);
         } else if constexpr (kRPW == 1) {
           const uint32_t ly = vr;
           if (ly < p.TH)
@@ -934,6 +1045,15 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       if (lane < kRR) bulk_commit();
     }
   }
+  if constexpr (kChunked) {
+    // the last group's records (after a barrier: its final words are complete)
+    if (produce && g_first < g_end) {
+      __syncthreads();
+      const uint64_t last = g_first + (g_end - 1u - g_first) / g_stride * g_stride;
+      build_records(p, zbuf + ((it - 1u) & 1u) * slots, group_at(p, TW, last), rtab, rec_out, lane,
+                    warp, nw, keep, rot);
+    }
+  }
 }
 
 
@@ -964,11 +1084,12 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   uint32_t it = 0;
   if constexpr (kTW == 64) {
     run_groups<kLife, kTW, kT>(p, lay, in, out, blockIdx.x, p.groups, gridDim.x, smem, keep, rot,
-                               it);
+                               it, p.rec[0], p.rec[1], p.mode == 1u);
   } else {
     const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
     const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
-    run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it);
+    run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it, nullptr, nullptr,
+                               false);
   }
   bulk_wait_all();
   settle_abort();
@@ -976,7 +1097,9 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
 
 // kT steps (1, 2, 4 or 8) of many instances (each with its own fractal, level
 // and buffers) that share one tile-row instantiation, in a single persistent
-// launch.  parity selects the launch's input: buffer 0 or buffer 1.  CTA c
+// launch.  parity selects the launch's input: buffer 0 or buffer 1 (and the
+// border records of that buffer, for 64-wide rows); mode 1 writes only the
+// input's records (before the first step of a run).  CTA c
 // walks its schedule entries, each a run of groups of one instance (g_first,
 // g_first + g_stride, ... below g_end); the instance's description is copied
 // to shared memory for the run (its fields are read throughout the group
@@ -985,7 +1108,7 @@ template <bool kLife, int kTW, int kT>
 __global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     const TiledDev *__restrict__ devs, uint8_t *const *__restrict__ buf0,
     uint8_t *const *__restrict__ buf1, const BatchWork *__restrict__ work,
-    const uint32_t *__restrict__ sched_start, TileLayout lay, uint32_t parity) {
+    const uint32_t *__restrict__ sched_start, TileLayout lay, uint32_t parity, uint32_t mode) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(16) TiledDev s_dev;
   static_assert(sizeof(TiledDev) % 4 == 0, "TiledDev is copied as words");
@@ -1003,7 +1126,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
     run_groups<kLife, kTW, kT>(s_dev, lay, in, out, w.g_first, w.g_end, w.g_stride, smem, keep, rot,
-                               it);
+                               it, mode ? nullptr : s_dev.rec[parity],
+                               s_dev.rec[mode ? parity : parity ^ 1u], mode == 1u);
   }
   bulk_wait_all();
   settle_abort();

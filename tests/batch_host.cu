@@ -11,6 +11,7 @@ int sq_tiled_describe(const squeeze_handle *, sq::TiledDev *, sq::TileSpec *) {
 }
 sq::TileLayout sq_tile_layout(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return sq::TileLayout{}; }
 uint32_t sq_tile_table_words(const sq::TileSpec &) { return 0; }
+sq::TileLayout sq_tile_layout_of(const sq::TileSpec &) { return sq::TileLayout{}; }
 sq::TileLayout sq_tile_layout_max(const sq::TileLayout &a, const sq::TileLayout &) { return a; }
 int sq_tile_kind(const sq::TileSpec &) { return 0; }
 void sq_launch_plan(uint64_t, uint32_t, uint64_t *counts) {
@@ -19,7 +20,7 @@ void sq_launch_plan(uint64_t, uint32_t, uint64_t *counts) {
 int sq_batch_occupancy(bool, int, uint32_t, int, uint32_t) { return 0; }
 int sq_batch_launch(const sq::TiledDev *, uint8_t *const *, uint8_t *const *, const sq::BatchWork *,
                     const uint32_t *, const sq::TileLayout &, int, int, bool, int, uint32_t,
-                    uint32_t, cudaStream_t) {
+                    uint32_t, uint32_t, cudaStream_t) {
   return SQUEEZE_ERR_UNSUPPORTED;
 }
 

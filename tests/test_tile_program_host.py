@@ -264,8 +264,8 @@ def chunk_table(lib, f, r, L, nbhd, passes):
     caps = np.zeros(3, dtype=np.uint64)
     assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
     halo = int(caps[2])
-    info = np.zeros(11, dtype=np.uint32)
-    table = np.zeros(3 * halo + 1, dtype=np.uint32)
+    info = np.zeros(22, dtype=np.uint32)
+    table = np.zeros(4 * halo + 289, dtype=np.uint32)
     hoff = np.zeros(halo, dtype=np.uint32)
     hdir = np.zeros(halo, dtype=np.uint8)
     rc = lib.tile_chunks(f.s, f.k, ptr(off), r, L, nbhd, passes, ptr(info), ptr(table), ptr(hoff),
@@ -289,7 +289,7 @@ def test_halo_chunk_table_serves_every_halo_cell(lib, f, r, L, nbhd, passes):
     assert np.array_equal(hoff[:nhalo], prog["halo_off"])
     nch, cs = int(info[0]), info[1:11].astype(np.int64)
     if prog["TW"] != 64:
-        assert nch == 0
+        assert nch == 0 and info[11] == 0
         return
     assert nch > 0 and cs[0] == 0 and cs[ndirs] == nch and np.all(np.diff(cs) >= 0)
     assert np.all(cs[ndirs:] == nch)
@@ -310,3 +310,51 @@ def test_halo_chunk_table_serves_every_halo_cell(lib, f, r, L, nbhd, passes):
             assert np.all(coff[c] + byte == prog["halo_off"][h])
             seen[h] += 1
     assert np.all(seen == 1)
+
+
+@pytest.mark.parametrize("passes", [1, 4, 8])
+@pytest.mark.parametrize("f,r,L,nbhd", CHUNK_CASES[:4],
+                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CHUNK_CASES[:4]])
+def test_border_records_carry_every_halo_word(lib, f, r, L, nbhd, passes):
+    """64-wide rows read their halo from the adjacent tiles' border records:
+    emulate a launch writing every tile's record from its packed words (the
+    record table's slots) and the next reading them (its halo words), and
+    compare each halo word with the direct gather through halo_off."""
+    prog = program(lib, f, r, L, nbhd, passes=passes)
+    if prog is None:
+        return
+    rc, info, table, hoff, hdir = chunk_table(lib, f, r, L, nbhd, passes)
+    assert rc == 0
+    nhalo, ndirs, nch = prog["nhalo"], len(prog["dir_list"]), int(info[0])
+    R, seg = int(info[11]), info[12:22].astype(np.int64)
+    assert R > 0 and seg[0] == 0 and seg[ndirs] == R and np.all(seg[ndirs:] == R)
+    rtab = table[2 * nch + 1 + nhalo:2 * nch + 1 + nhalo + 32 * R].astype(np.int64)
+    pad = rtab == 0xFFFFFFFF
+    slot_of, h_of = rtab & 0xFFFF, rtab >> 16
+    # every halo word once, in its own direction's segment, ring by ring
+    assert sorted(h_of[~pad].tolist()) == list(range(nhalo))
+    for j in range(ndirs):
+        hs = h_of[32 * seg[j]:32 * seg[j + 1]][~pad[32 * seg[j]:32 * seg[j + 1]]]
+        assert np.all(hdir[hs] == j) and np.all(np.diff(hs) > 0)
+        assert seg[j + 1] - seg[j] == -(-len(hs) // 32)
+    # emulation over every tile of a random state
+    W, TW, TH = f.k ** ((r + 1) // 2), prog["TW"], prog["TH"]
+    tiles_x, tiles_y = W // TW, f.k ** (r // 2) // TH
+    state = I.bernoulli_bytes(41 + r, f.k ** r, 0.5).reshape(-1, W)
+    tiles = state.reshape(tiles_y, TH, tiles_x, TW).transpose(0, 2, 1, 3).reshape(-1, TH * TW)
+    words = np.zeros((len(tiles), prog["slots"]), dtype=np.int64)   # slot word per tile
+    words[:, prog["slot"]] = tiles[:, :prog["cells"]] & 1
+    rec = np.where(pad, 0, words[:, np.where(pad, 0, slot_of)])   # record bits per tile
+    adj = library_adjacency(lib, f, r, L, prog)     # base of the adjacent tile, or -1
+    for j in range(ndirs):
+        base = adj[:, j]
+        ok = base >= 0
+        b = np.where(ok, base, 0)
+        t = (b // (TH * W)) * tiles_x + (b % W) // TW
+        for pos in range(32 * seg[j], 32 * seg[j + 1]):
+            if pad[pos]:
+                continue
+            h = h_of[pos]
+            got = np.where(ok, rec[t, pos], 0)
+            want = np.where(ok, state.reshape(-1)[b + prog["halo_off"][h]] & 1, 0)
+            assert np.array_equal(got, want), (j, h)
