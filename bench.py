@@ -15,8 +15,8 @@ memory; the same-GPU bounding-box comparison at level 16; the integer-ALU
 maps and per-cell step against their tensor-core (tcgen05) forms at level 20;
 the block-level layouts at level 16; the von Neumann tiled step and fp32 heat
 diffusion; the 256-instance batched mix (autotuned, 50 steps under a CUDA
-graph) and the 10,000-request loop (Poisson arrivals at 80 % of the batched
-mix's measured throughput, p50/p99 latency); the CPU oracle on a bounded
+graph) and the 10,000-request loop (Poisson arrivals at 80 % of the loop's
+own saturated throughput, p50/p99 latency); the CPU oracle on a bounded
 sample, on the level-10 workload and on the level-16 box; SM clocks sampled
 during the timed region.
 
@@ -420,7 +420,7 @@ def main():
     if not args.no_serve:
         mix = batch_mix_leg(sq, torch, dev, peaks()[0])
         if args.requests > 0 and world == 1:
-            loop = request_loop_leg(args.requests, mix["cell_updates_per_s"], mix["shape"]["levels"])
+            loop = request_loop_leg(args.requests, mix["shape"]["levels"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -504,22 +504,29 @@ def batch_mix_leg(sq, torch, dev, peak_gbs, steps=50):
                 "ctas_per_step": launches[0], "tuning_seconds": tune_s, "status": -status}
 
 
-def request_loop_leg(n, capacity, levels):
+def request_loop_leg(n, levels, calibration=1500):
     """`n` requests (seed 6): type uniform over the mix, level uniform up to
     triangle 18 / carpet 9 / Vicsek 12, steps uniform 10-500, Poisson arrivals
-    at a rate that offers 80 % of the batched mix's measured throughput;
-    continuous batching with admission by free HBM (64 slots, rounds of at
-    most 25 steps)."""
+    at a rate that offers 80 % of the loop's own saturated throughput
+    (measured first on `calibration` requests of seed 7 that all arrive at
+    once); continuous batching with admission by free HBM (64 slots, rounds of
+    at most 25 steps)."""
     from paper_2201_00613_gb300.serve import RequestLoop
     proto = I.request_stream(seed=6, count=2000, rate_per_s=1.0)
     mean_work = statistics.mean(r.instance.fractal.cells(r.instance.r) * r.n_steps for r in proto)
+    loop = RequestLoop(max_slots=64, chunk=25, levels=levels)
+    sat = loop.run(I.request_stream(seed=7, count=calibration, rate_per_s=1e9))
+    loop.close()
+    capacity = sat["cell_updates_per_s"]
     rate = 0.8 * capacity / mean_work
     reqs = I.request_stream(seed=6, count=n, rate_per_s=rate)
     loop = RequestLoop(max_slots=64, chunk=25, levels=levels)
     out = loop.run(reqs)
     loop.close()
-    out.update({"offered_rate_per_s": rate, "offered_load": "80 % of the batched mix",
-                "mean_work_cell_updates": mean_work})
+    out.update({"offered_rate_per_s": rate,
+                "offered_load": "80 % of the loop's saturated throughput",
+                "saturated_cell_updates_per_s": capacity,
+                "saturated_requests": calibration, "mean_work_cell_updates": mean_work})
     return out
 
 

@@ -26,7 +26,13 @@
  *     reported by squeeze_device_status().
  *   - The handle owns small per-fractal tables and, once the tiled step has
  *     run, its neighbour program and adjacency table (4 bytes per tile and
- *     direction) in device memory, freed by squeeze_destroy().
+ *     direction) in device memory, freed by squeeze_destroy().  For tiles
+ *     with 64-wide rows (the carpet) squeeze_step also keeps two border-record
+ *     buffers of 4 bytes per 32 halo cells of a tile (1/8 of a state for the
+ *     carpet); a batch keeps its own per item.
+ *   - Calls that use one handle must be ordered on the GPU (one stream, or
+ *     streams ordered by events): its status word and record buffers are
+ *     shared by its calls.
  *
  * Compact layout (Sec. 3.1): level mu odd unrolls along x, even along y, so
  * the compact rectangle has W = k^ceil(r/2) columns and H = k^floor(r/2)

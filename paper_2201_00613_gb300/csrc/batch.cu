@@ -47,6 +47,7 @@ struct squeeze_batch {
   int device;
   TiledDev *d_devs;
   uint8_t **d_buf0, **d_buf1;
+  uint32_t *d_rec;          // border records of the items with 64-wide rows, two per item
   cudaStream_t capture;     // stream the graphs are captured on
   std::map<uint64_t, cudaGraphExec_t> graphs;  // (n_steps, parity) -> executable graph
 };
@@ -68,7 +69,9 @@ void release(squeeze_batch *b) {
   cudaFree(b->d_devs);
   cudaFree(b->d_buf0);
   cudaFree(b->d_buf1);
+  cudaFree(b->d_rec);
   if (b->capture) cudaStreamDestroy(b->capture);
+  b->d_rec = nullptr;
   b->d_devs = nullptr;
   b->d_buf0 = b->d_buf1 = nullptr;
   b->capture = nullptr;
@@ -218,6 +221,21 @@ int setup(squeeze_batch *b) {
     starts.push_back(start);
   }
 
+  // Border records (64-wide rows): two buffers per item, of this batch alone
+  // (items may share a handle, each with its own states).
+  size_t rec_total = 0;
+  for (uint32_t i = 0; i < count; ++i)
+    rec_total += 2ull * specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
+  if (rec_total) {
+    SQ_CUDA(cudaMalloc(&b->d_rec, rec_total * 4));
+    size_t off = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+      const size_t n = (size_t)specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
+      devs[i].rec[0] = n ? b->d_rec + off : nullptr;          // records of buffer 0
+      devs[i].rec[1] = n ? b->d_rec + off + n : nullptr;      // and of buffer 1
+      off += 2 * n;
+    }
+  }
   SQ_CUDA(cudaMalloc(&b->d_devs, sizeof(TiledDev) * count));
   SQ_CUDA(cudaMalloc(&b->d_buf0, sizeof(uint8_t *) * count));
   SQ_CUDA(cudaMalloc(&b->d_buf1, sizeof(uint8_t *) * count));

@@ -656,8 +656,6 @@ int sq_tiled_prepare(squeeze_handle *h) {
     e = cudaMemcpy(p->d_halo_dir, halo_dir.data(), nhalo, cudaMemcpyHostToDevice);
   uint64_t tiles = (uint64_t)sp.tiles_x * sp.tiles_y;
   if (e == cudaSuccess && sp.ndirs) e = cudaMalloc(&p->d_adj, (size_t)sp.ndirs * tiles * 4);
-  for (int i = 0; i < 2 && e == cudaSuccess && sp.rec_words; ++i)
-    e = cudaMalloc(&p->d_rec[i], (size_t)sp.rec_words * tiles * 4);
   if (e != cudaSuccess) {
     sq_tiled_free(p);
     return sq_cuda_fail(e);
@@ -701,6 +699,10 @@ int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, 
   TiledProgram *p = h->tiled;
   *launches = 0;
   if (!p || !p->spec.rec_words) return SQUEEZE_OK;
+  // the record buffers, on the first squeeze_step (a batch keeps its own)
+  const size_t rec_bytes = (size_t)p->spec.rec_words * p->spec.tiles_x * p->spec.tiles_y * 4;
+  for (int i = 0; i < 2; ++i)
+    if (!p->d_rec[i]) SQ_CUDA(cudaMalloc(&p->d_rec[i], rec_bytes));
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
   if (h->wait_ns) d.wait_ns = h->wait_ns;
@@ -738,8 +740,6 @@ int sq_tiled_describe(const squeeze_handle *h, TiledDev *d, TileSpec *sp) {
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   *d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir, p->d_adj,
                     h->d_status);
-  d->rec[0] = p->d_rec[0];   // records of buffer 0 and of buffer 1
-  d->rec[1] = p->d_rec[1];
   if (h->wait_ns) d->wait_ns = h->wait_ns;
   d->fault = h->fault;
   *sp = p->spec;

@@ -140,3 +140,34 @@ def test_autotuner_picks_a_valid_shape(tmp_path, monkeypatch):
         torch.cuda.synchronize()
         for i, inst in enumerate(mix):
             assert torch.equal(mb.state(i), solo(inst, 3)), inst
+
+
+@pytest.mark.parametrize("steps", [1, 6, 9])
+def test_items_sharing_a_handle_keep_their_own_states(steps):
+    """Several items of one batch on the same handle (the request loop shares a
+    handle per fractal and level): each keeps its own states and border
+    records, so each must equal its own solo run."""
+    shapes = [(I.CARPET, 6), (I.CARPET, 6), (I.CARPET, 6), (I.TRIANGLE, 9), (I.TRIANGLE, 9)]
+    handles = {}
+    bufs, items, insts = [], [], []
+    try:
+        for i, (f, r) in enumerate(shapes):
+            h = handles.setdefault((f.name, r), sq.Handle(f, r))
+            inst = I.Instance(f, r, 700 + i)
+            a = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+            b = torch.empty_like(a)
+            sq.squeeze_init_bernoulli(h.h, a, inst.seed, I.p_q24(inst.p))
+            bufs.append((a, b))
+            items.append((h.h, a, b))
+            insts.append(inst)
+        batch = sq.squeeze_batch_create(items)
+        sq.squeeze_batch_run(batch, steps)
+        torch.cuda.synchronize()
+        for (a, b), inst in zip(bufs, insts):
+            assert torch.equal(b if steps % 2 else a, solo(inst, steps)), inst
+        sq.squeeze_batch_destroy(batch)
+        for h in handles.values():
+            assert sq.squeeze_device_status(h.h) == sq.SQUEEZE_OK
+    finally:
+        for h in handles.values():
+            h.close()
