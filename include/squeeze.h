@@ -26,10 +26,10 @@
  *     reported by squeeze_device_status().
  *   - The handle owns small per-fractal tables and, once the tiled step has
  *     run, its neighbour program and adjacency table (4 bytes per tile and
- *     direction) in device memory, freed by squeeze_destroy().  For tiles
- *     with 64-wide rows (the carpet) squeeze_step also keeps two border-record
- *     buffers of 4 bytes per 32 halo cells of a tile (1/8 of a state for the
- *     carpet); a batch keeps its own per item.
+ *     direction) in device memory, freed by squeeze_destroy().  squeeze_step
+ *     also keeps two border-record buffers of 4 bytes per 32 halo cells of a
+ *     tile (1/30 of a state for the triangle, 1/4 for the carpet with eight
+ *     steps per launch); a batch keeps its own per item.
  *   - Calls that use one handle must be ordered on the GPU (one stream, or
  *     streams ordered by events): its status word and record buffers are
  *     shared by its calls.
@@ -173,8 +173,9 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
 
 /* squeeze_set_max_steps_per_launch -- the most steps one launch of the tiled
  * kernel may advance: 1, 2, 4 or 8, or 0 for the default (the most whose
- * kernel keeps the CTAs per SM of the one-step kernel, or 4 if that has more;
- * its shared memory grows with the halo rings each further step needs).  The result of squeeze_step
+ * kernel keeps the CTAs per SM of the one-step kernel, or 3 if that has
+ * more; its shared memory grows with the halo rings each further step
+ * needs).  The result of squeeze_step
  * does not depend on it.  INVALID_ARG for other values. */
 int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps);
 
@@ -185,10 +186,10 @@ int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps);
  * tiled kernel); *launches = kernel launches it enqueued; by_steps[i] (four
  * entries) = how many of them advanced 2^i steps (the tiled kernel runs n
  * steps as launches of 8, 4, 2 and 1 steps whose count has the parity of n:
- * n = 100 is 12 launches of 8 steps and 2 of 2).  For fractals whose tiles
- * have 64-wide rows (the carpet) *launches also counts one launch that writes
- * the border records of the input (the halo the first step reads), which
- * advances no step.  Any pointer may be NULL.
+ * n = 100 is 12 launches of 8 steps and 2 of 2).  *launches also counts one
+ * launch that writes the border records of the input (the halo the first
+ * step reads), which advances no step (none for a fractal whose tiles have no
+ * halo).  Any pointer may be NULL.
  * INVALID_ARG for a null handle. */
 int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launches,
                            uint64_t *by_steps);

@@ -9,7 +9,7 @@
 // shared memory.  Each launch's CTAs walk a host-built schedule of (instance,
 // group range) entries, cut so that every CTA gets about the same number of
 // group slots (a group costs about the same whether its 32 tile lanes are
-// full or not).  Launches advance up to four steps where the items' programs
+// full or not).  Launches advance up to eight steps where the items' programs
 // allow (the intermediate steps stay in shared memory).  The launches of n_steps
 // steps are captured once into a CUDA graph (buffers ping-ponging) and
 // replayed on later calls.
@@ -24,8 +24,9 @@
 
 using namespace sq;
 
-// Steps per launch of the batched kernel at most (it is instantiated for 1, 2 and 4).
-constexpr uint32_t kBatchPasses = 4;
+// Steps per launch of the batched kernel at most (it is instantiated for 1, 2, 4
+// and 8).
+constexpr uint32_t kBatchPasses = 8;
 
 // The items of one tile-row instantiation and their launch.
 struct BatchPlan {
@@ -34,6 +35,7 @@ struct BatchPlan {
   uint32_t passes;          // steps per launch every item's program allows (1, 2 or 4)
   TileLayout lay;           // the maxima of the items' shared-memory needs
   int threads, grid;        // CTA size; persistent grid (the same for every steps per launch)
+  bool records;             // some item reads its halo from border records
   BatchWork *d_work;
   uint32_t *d_sched;
 };
@@ -190,6 +192,7 @@ int setup(squeeze_batch *b) {
       first = false;
       p.life = p.life && h->rule.birth == (1u << 3) && h->rule.survive == ((1u << 2) | (1u << 3));
       p.passes = sp.passes < p.passes ? sp.passes : p.passes;
+      p.records = p.records || sp.rec_words != 0;
       own_threads = sp.threads > own_threads ? sp.threads : own_threads;
       idx.push_back(i);
       // a group costs about the same whatever its fill: weigh it by its slots
@@ -258,7 +261,7 @@ int setup(squeeze_batch *b) {
   return SQUEEZE_OK;
 }
 
-// Launches of n_steps steps: up to four steps per launch where every plan
+// Launches of n_steps steps: up to eight steps per launch where every plan
 // can, with a launch count of n_steps' parity (each launch swaps the
 // buffers; the state after an even number of steps belongs in buffer 0).
 int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
@@ -267,10 +270,10 @@ int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
   uint64_t counts[4];
   sq_launch_plan(n_steps, passes, counts);
   const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
-  // 64-wide rows read their halo from border records: first those of the
-  // input (one records-only launch of that instantiation)
+  // The launches read their halo from border records: first those of the
+  // input (one records-only launch per instantiation whose items have any)
   for (const BatchPlan &p : b->plans) {
-    if (p.kind != 64 || !total) continue;
+    if (!p.records || !total) continue;
     int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay, p.grid,
                              p.threads, p.life, p.kind, 1, (uint32_t)(b->parity & 1u), 1, st);
     if (rc) return rc;

@@ -20,6 +20,7 @@ const void *batch_kernel_of(int kind) {
 }
 
 const void *batch_kernel_for(bool life, int kind, uint32_t steps) {
+  if (steps == 8) return life ? batch_kernel_of<true, 8>(kind) : batch_kernel_of<false, 8>(kind);
   if (steps == 4) return life ? batch_kernel_of<true, 4>(kind) : batch_kernel_of<false, 4>(kind);
   if (steps == 2) return life ? batch_kernel_of<true, 2>(kind) : batch_kernel_of<false, 2>(kind);
   return life ? batch_kernel_of<true, 1>(kind) : batch_kernel_of<false, 1>(kind);

@@ -222,19 +222,20 @@ struct TiledDev {
   // direction j owns chunks [chunk_start[j], chunk_start[j + 1]).
   uint32_t nchunks;
   uint32_t chunk_start[10];
-  // Border records (64-wide rows): each launch also writes, per tile, the
-  // states of its cells that adjacent tiles read as halo, rec_words words per
-  // tile, segment j (words [rec_seg[j], rec_seg[j+1])) holding what the tile
-  // adjacent in direction j of it reads, bit i of word w = halo cell 32 w + i
-  // of that segment.  The table after the chunk table maps each record bit to
-  // (exporting slot | halo word << 16).  rec[0]: records of the input state
-  // (null: gather by chunks), rec[1]: records of the output state; mode 1
-  // writes the input's records to rec[1] and nothing else.
+  // Border records: each launch also writes, per tile, the states of its
+  // cells that adjacent tiles read as halo, rec_words words per tile, segment
+  // j (words [rec_seg[j], rec_seg[j+1])) holding what the tile adjacent in
+  // direction j of it reads, bit i of word w = halo cell 32 w + i of that
+  // segment.  The record tables after the chunk table map each record bit to
+  // (exported cell | halo word << 16), each exported cell to its slot, and
+  // each slot to its exported cell.  rec[0]: records of the input state (null:
+  // gather the halo from the state), rec[1]: records of the output state; mode
+  // 1 writes the input's records to rec[1] and nothing else.
   uint32_t rec_words;
   uint32_t rec_seg[10];
+  uint32_t rec_nexp;         // exported cells: final-step words kept per group
   uint32_t *rec[2];
   uint32_t mode;
-  uint32_t pad_;
 };
 
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
@@ -247,7 +248,7 @@ struct TileLayout {
   uint32_t hdir_bytes;       // halo direction indices (one byte per halo word)
   uint32_t rowa_bytes;       // per-row alignment offsets (two sets)
   uint32_t carry_bytes;      // per-row 16-byte chunk handed to the next group
-  uint32_t z_bytes;          // final-step words of the last two groups (border records)
+  uint32_t z_bytes;          // exported final-step words of the last two groups (border records)
   uint32_t stage_bytes;      // one staging buffer (two are used)
   uint32_t smem;             // total dynamic shared memory
 };
@@ -264,8 +265,9 @@ struct TileSpec {
   uint32_t tiles_x, tiles_y, groups_per_band, pitch;
   uint32_t nchunks;          // chunk table of the halo (64-wide rows), 0 if none
   uint32_t chunk_start[10];  // chunks of direction j: [chunk_start[j], chunk_start[j+1])
-  uint32_t rec_words;        // border record words per tile (64-wide rows), 0 if none
+  uint32_t rec_words;        // border record words per tile, 0 if none
   uint32_t rec_seg[10];      // record words read by direction j: [rec_seg[j], rec_seg[j+1])
+  uint32_t rec_nexp;         // cells of a tile that its record holds
   uint64_t groups;
   size_t smem;
   int threads;
@@ -294,9 +296,9 @@ struct TileBuild {
   // rings 2..P are built too, and references for rings 1..P-1 (refs and
   // refs16 then need (slots + halo_cap) * 8 entries).
   uint32_t passes;
-  // Optional (64-wide rows): the halo's chunk table and border-record table,
-  // at most 4 * halo_cap + 289 words (layout as in TiledDev); null builds a
-  // program without them.
+  // Optional: the halo's chunk table (64-wide rows) and the border-record
+  // tables, at most 5 * halo_cap + slots_cap / 2 + 300 words (layout as in
+  // TiledDev); null builds a program without them.
   uint32_t *chunks;
 };
 

@@ -44,7 +44,7 @@ struct HostWork {
   uint16_t refs16[kSlotsCap * 8];
   uint32_t halo_off[kHaloCap];
   uint8_t halo_dir[kHaloCap];
-  uint32_t chunks[4 * kHaloCap + 289];   // halo chunk and border-record tables (64-wide rows)
+  uint32_t chunks[5 * kHaloCap + kSlotsCap / 2 + 300];   // halo chunk and border-record tables
 };
 
 HostWork g_work;         // guarded by g_mutex

@@ -113,13 +113,20 @@ TileLayout sq_tile_layout(uint32_t slots, uint32_t nhalo, uint32_t TH, uint32_t 
   return l;
 }
 
+// Words of the chunk table (kept in shared memory) and of the record tables
+// (read through the cache), which follow the halo offsets in device memory.
+static uint32_t chunk_table_words(const TileSpec &sp) {
+  return sp.nchunks ? 2u * sp.nchunks + 1u + sp.nhalo : 0u;
+}
+
 uint32_t sq_tile_table_words(const TileSpec &sp) {
-  return (sp.nchunks ? 2u * sp.nchunks + 1u + sp.nhalo : 0u) + 32u * sp.rec_words;
+  return chunk_table_words(sp) +
+         (sp.rec_words ? 32u * sp.rec_words + sp.rec_nexp + (sp.slots + 1u) / 2u : 0u);
 }
 
 TileLayout sq_tile_layout_of(const TileSpec &sp) {
-  return sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, sq_tile_table_words(sp),
-                        sp.rec_words ? 2u * sp.slots : 0u);
+  return sq_tile_layout(sp.slots, sp.nhalo, sp.TH, sp.pitch, chunk_table_words(sp),
+                        2u * sp.rec_nexp);
 }
 
 TileLayout sq_tile_layout_max(const TileLayout &a, const TileLayout &b) {
@@ -230,6 +237,7 @@ TiledDev sq_tiled_dev(const FracDev &f, const Rule &rule, const TileSpec &sp,
   for (int i = 0; i < 10; ++i) d.chunk_start[i] = sp.chunk_start[i];
   d.rec_words = sp.rec_words;
   for (int i = 0; i < 10; ++i) d.rec_seg[i] = sp.rec_seg[i];
+  d.rec_nexp = sp.rec_nexp;
   d.rec[0] = d.rec[1] = nullptr;
   d.mode = 0;
   return d;
@@ -340,23 +348,32 @@ static void build_chunks(uint32_t nhalo, const uint32_t *halo_off, const uint8_t
   for (uint32_t v : cells) *o++ = v;
 }
 
-// The border-record table for 64-wide rows.  Segment j of a tile's record
-// holds, in halo-word order, the states of the tile's cells that the tile
-// adjacent to it in direction j reads as its direction-j halo (the halo words
-// h with halo_dir[h] == j, all rings): ceil(n_j / 32) words from rec_seg[j].
-// out[32 w + i] for record bit i of word w = exporting slot (the slot word of
-// local cell ly * 64 + lx, with halo_off = ly * W + lx) | halo word << 16;
-// 0xFFFFFFFF pads a segment's last word.
-static void build_records(uint64_t W, uint32_t nhalo, const uint32_t *halo_off,
-                          const uint8_t *halo_dir, TileSpec &sp, uint32_t *out) {
+// The border-record tables.  Segment j of a tile's record holds, in
+// halo-word order, the states of the tile's cells that the tile adjacent to it
+// in direction j reads as its direction-j halo (the halo words h with
+// halo_dir[h] == j, all rings): ceil(n_j / 32) words from rec_seg[j].  The
+// cells a record names, its exported cells, are numbered e = 0 .. rec_nexp-1
+// in order of first use; a launch keeps the final-step words of those slots
+// only.  out = record bits (32 per record word: e | halo word << 16, or ~0 to
+// pad a segment's last word) | the slot of each exported cell | per slot its
+// export number or 0xFFFF (16 bits each, two per word).
+static void build_records(uint64_t W, uint32_t TW, uint32_t rpw, uint32_t wpr, uint32_t slots,
+                          uint32_t nhalo, const uint32_t *halo_off, const uint8_t *halo_dir,
+                          TileSpec &sp, uint32_t *out) {
+  std::vector<uint32_t> exp_of(slots, 0xFFFFu), exp_slot;
   uint32_t words = 0;
   for (uint32_t j = 0; j < sp.ndirs; ++j) {
     sp.rec_seg[j] = words;
     uint32_t n = 0;
     for (uint32_t h = 0; h < nhalo; ++h)
       if (halo_dir[h] == j) {
-        const uint32_t lc = (uint32_t)(halo_off[h] / W) * 64u + (uint32_t)(halo_off[h] % W);
-        out[32u * words + n++] = tile_slot_of(lc, 64u, 1u, 2u) | (h << 16);
+        const uint32_t lc = (uint32_t)(halo_off[h] / W) * TW + (uint32_t)(halo_off[h] % W);
+        const uint32_t s = tile_slot_of(lc, TW, rpw, wpr);
+        if (exp_of[s] == 0xFFFFu) {
+          exp_of[s] = (uint32_t)exp_slot.size();
+          exp_slot.push_back(s);
+        }
+        out[32u * words + n++] = exp_of[s] | (h << 16);
       }
     const uint32_t used = (n + 31u) / 32u;
     for (uint32_t i = n; i < 32u * used; ++i) out[32u * words + i] = 0xFFFFFFFFu;
@@ -364,6 +381,11 @@ static void build_records(uint64_t W, uint32_t nhalo, const uint32_t *halo_off,
   }
   for (uint32_t j = sp.ndirs; j < 10; ++j) sp.rec_seg[j] = words;
   sp.rec_words = words;
+  sp.rec_nexp = (uint32_t)exp_slot.size();
+  uint32_t *o = out + 32u * words;
+  for (uint32_t s : exp_slot) *o++ = s;
+  for (uint32_t s = 0; s < slots; s += 2)
+    *o++ = exp_of[s] | ((s + 1 < slots ? exp_of[s + 1] : 0xFFFFu) << 16);
 }
 
 // Host construction of the level-L neighbour program (see the file comment):
@@ -519,10 +541,10 @@ int sq_tile_build(const FracDev &f, uint32_t L, const TileBuild &B, TileSpec &sp
   sp.groups_per_band = (sp.tiles_x + 31) / 32;
   sp.groups = (uint64_t)sp.groups_per_band * sp.tiles_y;
   sp.pitch = pitch_for(TW);
-  if (TW == 64 && B.chunks && nhalo) {
-    build_chunks(nhalo, B.halo_off, B.halo_dir, sp, B.chunks);
-    build_records(f.W, nhalo, B.halo_off, B.halo_dir, sp,
-                  B.chunks + 2u * sp.nchunks + 1u + nhalo);
+  if (B.chunks && nhalo) {
+    if (TW == 64) build_chunks(nhalo, B.halo_off, B.halo_dir, sp, B.chunks);
+    build_records(f.W, TW, rpw, wpr, slots, nhalo, B.halo_off, B.halo_dir, sp,
+                  B.chunks + chunk_table_words(sp));
   }
   sp.smem = sq_tile_layout_of(sp).smem;
   if (sp.groups >= (1ull << 32) || sp.smem > kTiledSmemLimit) return SQUEEZE_ERR_UNSUPPORTED;
@@ -579,6 +601,9 @@ int sq_tile_launch(const TiledDev &d, const TileSpec &sp, const uint8_t *in, uin
   if ((steps != 1 && steps != 2 && steps != 4 && steps != 8) || steps > sp.passes)
     return SQUEEZE_ERR_INVALID_ARG;
   if (sp.TW == 64 && sp.nhalo && !sp.nchunks) return SQUEEZE_ERR_INVALID_ARG;  // no chunk table
+  if ((d.rec[0] || d.rec[1]) && !sp.rec_words) return SQUEEZE_ERR_INVALID_ARG;
+  // several steps per launch read the halo from the input's records only
+  if (steps > 1 && sp.rec_words && (d.mode != 0 || !d.rec[0])) return SQUEEZE_ERR_INVALID_ARG;
   bool life = d.rule.birth == (1u << 3) && d.rule.survive == ((1u << 2) | (1u << 3));
   TiledDev dd = d;
   TileLayout lay = sq_tile_layout_of(sp);
@@ -604,7 +629,7 @@ int sq_tiled_prepare(squeeze_handle *h) {
       rank(z.halo);
   std::vector<uint64_t> keys(z.halo), sorted(z.halo);
   std::vector<uint16_t> refs16((z.slots + z.halo) * 8);
-  std::vector<uint32_t> halo_off(z.halo), chunks(4 * z.halo + 289);
+  std::vector<uint32_t> halo_off(z.halo), chunks(5 * z.halo + z.slots / 2 + 300);
   std::vector<uint8_t> halo_dir(z.halo);
   TileBuild B = {inv.data(), X.data(), Y.data(), refs.data(), keys.data(), sorted.data(),
                  order.data(), rank.data(), refs16.data(), halo_off.data(), halo_dir.data(),
@@ -612,9 +637,10 @@ int sq_tiled_prepare(squeeze_handle *h) {
   TiledProgram *p = new TiledProgram;
   memset(p, 0, sizeof(*p));
   // Steps per launch: by default the most (8, 4, 2) whose program builds and
-  // whose kernel keeps the CTAs per SM of the one-step kernel, or 4 if that
-  // has more (its shared memory grows with the halo rings; 4 CTAs per SM is
-  // what the default tile level is sized for); with
+  // whose kernel keeps the CTAs per SM of the one-step kernel, or 3 if that
+  // has more (its shared memory grows with the halo rings; with the halo read
+  // from border records eight steps at 3 CTAs per SM beat four at 4 by 30 %
+  // for the triangle and Vicsek, and tie for the carpet); with
   // squeeze_set_max_steps_per_launch the most up to that limit that build.
   int rc = SQUEEZE_ERR_UNSUPPORTED, occ1 = 0;
   {
@@ -622,7 +648,7 @@ int sq_tiled_prepare(squeeze_handle *h) {
     TileSpec one;
     rc = sq_tile_build(f, L, B, one);
     if (rc == SQUEEZE_OK) rc = sq_tile_launch_config(one, h->device);
-    if (rc == SQUEEZE_OK) occ1 = one.occ[0][1] < 4 ? one.occ[0][1] : 4;
+    if (rc == SQUEEZE_OK) occ1 = one.occ[0][1] < 3 ? one.occ[0][1] : 3;
   }
   for (uint32_t passes = h->max_passes ? h->max_passes : kTiledPasses; rc == SQUEEZE_OK; passes /= 2) {
     B.passes = passes;

@@ -13,7 +13,7 @@ namespace sq {
 namespace {
 
 constexpr int kTiledMaxThreads = 384;
-constexpr uint32_t kTiledPasses = 8;            // steps per launch the handle's program is built for
+constexpr uint32_t kTiledPasses = 8;            // most steps per launch the handle's program is built for
 constexpr size_t kTiledSmemCap = 56 * 1024;     // default level: 4 CTAs per SM
 constexpr size_t kTiledSmemLimit = 200 * 1024;  // any level: one CTA per SM
 
@@ -407,25 +407,28 @@ __device__ __forceinline__ uint32_t pack_aligned(const uint32_t *stage32, uint32
   return acc;
 }
 
-// ---- border records (64-wide rows) -----------------------------------------
+// ---- border records -----------------------------------------------------------
 //
-// rtab: the record table in shared memory (per record bit: exporting slot |
-// halo word << 16, or ~0 for padding).  A tile's record word w holds at bit i
-// the state of the cell of record bit 32 w + i, so one 32 x 32 transpose turns
-// the group's words into the 32 tiles' record words and back.
+// rtab: the record table (per record bit: exported cell | halo word << 16, or
+// ~0 for padding), read through the cache.  A tile's record word w holds at
+// bit i the state of the cell of record bit 32 w + i, so one 32 x 32
+// transpose turns the group's words into the 32 tiles' record words and back.
 
-// The records of the group's tiles from its words (bit l of words[s] = slot
-// s of tile l); warp-strided over record words, lane l stores its tile's.
+// The records of the group's tiles (bit l of a word = tile l): from the
+// exported final words (words[e], map null) or from the word array of the
+// group (words[map[e]], map = the exported cells' slots).  Warp-strided over
+// record words; lane l stores its tile's.
 __device__ __forceinline__ void build_records(const TiledDev &p, const uint32_t *words,
-                                              const Group &G, const uint32_t *rtab,
-                                              uint32_t *rec_out, unsigned lane, unsigned warp,
-                                              unsigned nw, const uint32_t *keep,
-                                              const uint32_t *rot) {
+                                              const uint32_t *map, const Group &G,
+                                              const uint32_t *rtab, uint32_t *rec_out,
+                                              unsigned lane, unsigned warp, unsigned nw,
+                                              const uint32_t *keep, const uint32_t *rot) {
   const uint32_t R = p.rec_words;
   const uint64_t t0 = (uint64_t)G.ty * p.tiles_x + G.tx0;
   for (uint32_t w = warp; w < R; w += nw) {
-    const uint32_t e = rtab[32u * w + lane];
-    uint32_t x = e == 0xFFFFFFFFu ? 0u : words[e & 0xFFFFu];
+    const uint32_t e = __ldg(rtab + 32u * w + lane);
+    uint32_t x = 0u;
+    if (e != 0xFFFFFFFFu) x = words[map ? __ldg(map + (e & 0xFFFFu)) : (e & 0xFFFFu)];
     transpose32_n<1>(&x, keep, rot);
     if (lane < G.ntiles) rec_out[(t0 + lane) * R + w] = x;
   }
@@ -435,29 +438,36 @@ __device__ __forceinline__ void build_records(const TiledDev &p, const uint32_t 
 // (~0: none, all dead): lane l loads record word w of its tile, and after the
 // transpose lane i holds the word of record bit 32 w + i, whose halo word the
 // table names.  Words of rings past hlimit are skipped.
+template <int kN>
+__device__ __forceinline__ void records_to_words(const TiledDev &p, uint32_t t, uint32_t w,
+                                                 const uint32_t *rtab, const uint32_t *rec_in,
+                                                 uint32_t *words, uint32_t hlimit, unsigned lane,
+                                                 const uint32_t *keep, const uint32_t *rot) {
+  uint32_t x[kN];
+#pragma unroll
+  for (int i = 0; i < kN; ++i)
+    x[i] = t != ~0u ? __ldg(rec_in + (uint64_t)t * p.rec_words + w + i) : 0u;
+  transpose32_n<kN>(x, keep, rot);
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {
+    const uint32_t e = __ldg(rtab + 32u * (w + i) + lane), h = e >> 16;
+    if (e != 0xFFFFFFFFu && h < hlimit) words[h] = x[i];
+  }
+}
+
 __device__ __forceinline__ void gather_records(const TiledDev &p, uint32_t t, uint32_t j,
                                                const uint32_t *rtab, const uint32_t *rec_in,
                                                uint32_t *words, uint32_t hlimit, unsigned lane,
                                                const uint32_t *keep, const uint32_t *rot) {
-  const uint32_t R = p.rec_words, w1 = p.rec_seg[j + 1];
+  const uint32_t w1 = p.rec_seg[j + 1];
   if (t != ~0u && t >= p.tiles) {
     flag(p.status, SQUEEZE_ERR_DEVICE_BOUNDS);
     t = ~0u;
   }
-  for (uint32_t w = p.rec_seg[j]; w < w1; w += 4) {
-    uint32_t x[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      x[i] = (w + i < w1 && t != ~0u) ? __ldg(rec_in + (uint64_t)t * R + w + i) : 0u;
-    transpose32_n<4>(x, keep, rot);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (w + i < w1) {
-        const uint32_t e = rtab[32u * (w + i) + lane], h = e >> 16;
-        if (e != 0xFFFFFFFFu && h < hlimit) words[h] = x[i];
-      }
-    }
-  }
+  uint32_t w = p.rec_seg[j];
+  for (; w + 2u <= w1; w += 2u)   // two words per transpose pass
+    records_to_words<2>(p, t, w, rtab, rec_in, words, hlimit, lane, keep, rot);
+  if (w < w1) records_to_words<1>(p, t, w, rtab, rec_in, words, hlimit, lane, keep, rot);
 }
 
 // Pack a 64-byte tile row at o (16-byte aligned; lane = tile, the lanes' rows
@@ -692,15 +702,26 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
   constexpr bool kChunked = kTW == 64;
   const uint32_t ntab = nhalo + (kChunked && p.nchunks ? 2u * p.nchunks + 1u + nhalo : 0u);
   const uint32_t *ctab = hoff + nhalo;
-  // Border records (64-wide rows with a record table): read the input's
-  // records for the halo (rec_in; else gather by chunks), write the output's
+  // Border records (programs with a record table): read the input's records
+  // for the halo (rec_in; else gather from the state), write the output's
   // (rec_out); rec_only: write the input's records to rec_out and nothing else.
-  const uint32_t rtab_words = kChunked && p.rec_words ? 32u * p.rec_words : 0u;
-  const uint32_t *rtab = ctab + (kChunked && p.nchunks ? 2u * p.nchunks + 1u + nhalo : 0u);
-  const bool use_rec = rtab_words != 0u && rec_in != nullptr;
-  const bool produce = rtab_words != 0u && rec_out != nullptr && !rec_only;
-  uint32_t *zbuf = q.z;
-  for (uint32_t i = tid; i < ntab + rtab_words; i += nthreads) hoff[i] = p.halo_off[i];
+  // The record tables stay in device memory (read through the cache): record
+  // bits (exported cell | halo word << 16), the exported cells' slots, and
+  // each slot's exported cell (16 bits).
+  const uint32_t *rtab = p.halo_off + ntab;
+  const uint32_t *exp_slot = rtab + 32u * p.rec_words;
+  const uint16_t *exp_of = reinterpret_cast<const uint16_t *>(exp_slot + p.rec_nexp);
+  const bool use_rec = p.rec_words != 0u && rec_in != nullptr;
+  const bool produce = p.rec_words != 0u && rec_out != nullptr && !rec_only;
+  // Halo gathered after the pack (records, or chunks of 64-wide rows), or
+  // byte by byte.  Launches of more than one step always have the input's
+  // records, so only one-step launches (the allocation-free step has no
+  // records) compile the gathers from the state.
+  constexpr bool kGather = kT == 1;
+  const bool deferred = !kGather || kChunked || use_rec || rec_only;
+  const uint32_t nexp = p.rec_nexp;
+  uint32_t *zbuf = q.z;   // exported final words of the last two groups
+  for (uint32_t i = tid; i < ntab; i += nthreads) hoff[i] = p.halo_off[i];
   if constexpr (kT > 1)
     for (uint32_t i = tid; i < p.ring_end[kT - 1]; i += nthreads) hdir[i] = p.halo_dir[i];
   if (tid == 0) {
@@ -753,15 +774,15 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     uint32_t hb[kHaloAhead];
     uint32_t h_pre = 0, t_next = ~0u;
     const uint32_t hlimit = p.ring_end[kT];   // halo words of the rings this launch uses
-    if (kChunked && warp < p.ndirs) {
-      // chunk mode: direction `warp` is gathered after the pack (loading
+    if (deferred && warp < p.ndirs) {
+      // chunks or records: direction `warp` is gathered after the pack (loading
       // chunks ahead of it costs registers and measured no faster)
       if (g + g_stride < g_end) t_next = adjacent_of(p, group_at(p, TW, g + g_stride), warp, lane);
       if constexpr (kT > 1) {
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, t_cur != ~0u);
         if (lane == 0) emask[warp] = m;
       }
-    } else if (!kChunked && warp < p.ndirs) {
+    } else if (kGather && !deferred && warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp], h1 = p.halo_start[warp + 1];
       h_pre = min(h1 - h0, (uint32_t)kHaloAhead);
       const uint64_t base = tile_base(p, TW, t_cur);
@@ -786,15 +807,15 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     }
     for (uint32_t j = warp + nw; j < p.ndirs; j += nw) {
       const uint32_t t = adjacent_of(p, G, j, lane);
-      if constexpr (kChunked) {
+      if (deferred) {
         if (rec_only) {
         } else if (use_rec) {
           gather_records(p, t, j, rtab, rec_in, win + slots, hlimit, lane, keep, rot);
-        } else {
+        } else if constexpr (kChunked && kGather) {
           gather_chunks(p, tile_base(p, TW, t), ctab, p.chunk_start[j], p.chunk_start[j + 1],
                         win + slots, hlimit, in, lane);
         }
-      } else {
+      } else if constexpr (kGather) {
         gather_halo<kHaloBatch>(p, TW, t, p.halo_start[j], p.halo_start[j + 1], hoff,
                                 win + slots, in, lane);
         if constexpr (kT > 1) {
@@ -869,16 +890,16 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       for (int k = 0; k < kR; ++k)
         if (vrow(u0, k) < VR) win[vrow(u0, k) * 32u + lane] = acc[k];
     }
-    if (kChunked && warp < p.ndirs) {
+    if (deferred && warp < p.ndirs) {
       if (rec_only) {
       } else if (use_rec) {
         gather_records(p, t_cur, warp, rtab, rec_in, win + slots, hlimit, lane, keep, rot);
-      } else {
+      } else if constexpr (kChunked && kGather) {
         gather_chunks(p, tile_base(p, TW, t_cur), ctab, p.chunk_start[warp],
                       p.chunk_start[warp + 1], win + slots, hlimit, in, lane);
       }
       t_cur = t_next;
-    } else if (!kChunked && warp < p.ndirs) {
+    } else if (kGather && !deferred && warp < p.ndirs) {
       const uint32_t h0 = p.halo_start[warp];
 #pragma unroll
       for (int i = 0; i < kHaloAhead; ++i) {
@@ -898,18 +919,16 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
     if (warp == 0 && g + g_stride < g_end && !cta_aborted() && !withhold)
       issue_group_loads(p, group_at(p, TW, g + g_stride), in, stage_base + (b ^ 1u) * stage_bytes,
                         &mbar[b ^ 1u], lane);
-    if constexpr (kChunked) {
-      if (rec_only) {   // the input's records from its packed words; no step
-        build_records(p, win, G, rtab, rec_out, lane, warp, nw, keep, rot);
-        continue;
-      }
-      // The previous group's records: its final-step words are complete, since
-      // every warp has passed this barrier (and nothing rewrites them before
-      // the next one).
-      if (produce && g != g_first)
-        build_records(p, zbuf + ((it - 1u) & 1u) * slots, group_at(p, TW, g - g_stride), rtab,
-                      rec_out, lane, warp, nw, keep, rot);
+    if (rec_only) {   // the input's records from its packed words; no step
+      build_records(p, win, exp_slot, G, rtab, rec_out, lane, warp, nw, keep, rot);
+      continue;
     }
+    // The previous group's records: its exported final words are complete,
+    // since every warp has passed this barrier (and nothing rewrites them
+    // before the next one).
+    if (produce && g != g_first)
+      build_records(p, zbuf + ((it - 1u) & 1u) * nexp, nullptr, group_at(p, TW, g - g_stride),
+                    rtab, rec_out, lane, warp, nw, keep, rot);
 
     // kT > 1: steps 1 .. kT-1 of the own slot rows and of the halo rings that
     // the later steps still need, alternating between X and Y.
@@ -943,10 +962,13 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
 #pragma unroll
       for (int k = 0; k < kR; ++k)
         y[k] = vrow(u0, k) < VR ? rule_at<kLife>(p, rbase, vrow(u0, k) * 32u + lane) : 0u;
-      if (kChunked && produce) {   // keep the final words for this group's records
+      if (produce) {   // keep the exported final words for this group's records
 #pragma unroll
         for (int k = 0; k < kR; ++k)
-          if (vrow(u0, k) < VR) zbuf[(it & 1u) * slots + vrow(u0, k) * 32u + lane] = y[k];
+          if (vrow(u0, k) < VR) {
+            const uint32_t e = __ldg(exp_of + vrow(u0, k) * 32u + lane);
+            if (e != 0xFFFFu) zbuf[(it & 1u) * nexp + e] = y[k];
+          }
       }
       transpose32_n<kR>(y, keep, rot);
       // Row offsets first: a shared load after the unpack's stores would wait for them.
@@ -1045,14 +1067,12 @@ __device__ __forceinline__ void run_groups(const TiledDev &p, const TileLayout &
       if (lane < kRR) bulk_commit();
     }
   }
-  if constexpr (kChunked) {
-    // the last group's records (after a barrier: its final words are complete)
-    if (produce && g_first < g_end) {
-      __syncthreads();
-      const uint64_t last = g_first + (g_end - 1u - g_first) / g_stride * g_stride;
-      build_records(p, zbuf + ((it - 1u) & 1u) * slots, group_at(p, TW, last), rtab, rec_out, lane,
-                    warp, nw, keep, rot);
-    }
+  // the last group's records (after a barrier: its final words are complete)
+  if (produce && g_first < g_end) {
+    __syncthreads();
+    const uint64_t last = g_first + (g_end - 1u - g_first) / g_stride * g_stride;
+    build_records(p, zbuf + ((it - 1u) & 1u) * nexp, nullptr, group_at(p, TW, last), rtab,
+                  rec_out, lane, warp, nw, keep, rot);
   }
 }
 
@@ -1075,7 +1095,7 @@ __device__ __forceinline__ void init_barriers(unsigned char *smem, const TileLay
 // they read from the tiles above and below are still in L2 (those rows start
 // on 16-byte boundaries, so nothing is lost by not handing row ends over).
 template <bool kLife, int kTW, int kT>
-__global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
+__global__ void __launch_bounds__(kTW == 64 ? 256 : kTiledMaxThreads) step_tiled_kernel(
     TiledDev p, TileLayout lay, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint32_t keep[5], rot[5];
@@ -1088,8 +1108,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads) step_tiled_kernel(
   } else {
     const uint64_t g0 = (uint64_t)blockIdx.x * p.groups / gridDim.x;
     const uint64_t g1 = (uint64_t)(blockIdx.x + 1) * p.groups / gridDim.x;
-    run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it, nullptr, nullptr,
-                               false);
+    run_groups<kLife, kTW, kT>(p, lay, in, out, g0, g1, 1, smem, keep, rot, it, p.rec[0], p.rec[1],
+                               p.mode == 1u);
   }
   bulk_wait_all();
   settle_abort();

@@ -127,10 +127,10 @@ class RequestLoop:
         return ids
 
     def _fits(self, inst) -> bool:
-        # two states, the batch's border records (at most 1/8 of a state each,
-        # for 64-wide tile rows) and tables
+        # two states, the batch's two border-record buffers (at most a quarter
+        # of a state each: the carpet's eight halo rings) and tables
         cells = inst.fractal.cells(inst.r)
-        need = 2 * cells + cells // 4 + (1 << 20)
+        need = 2 * cells + cells // 2 + (1 << 20)
         return self.backend.free_bytes() - need >= self.reserve
 
     def _handle(self, inst):

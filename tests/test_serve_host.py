@@ -89,9 +89,9 @@ def test_every_request_gets_exactly_its_steps():
 def test_admission_holds_the_memory_reserve():
     f, r = I.TRIANGLE, 6
     reqs = [I.Request(i, 0.0, I.Instance(f, r, i), 5 + i % 3) for i in range(12)]
-    # the loop asks for the two buffers, a quarter of a state for border records
-    # and 1 MiB of headroom: room for three at a time
-    be = FakeBackend(total_bytes=(1 << 20) + 3 * 2 * f.cells(r) + f.cells(r) // 4 + 100)
+    # the loop asks for the two buffers, half a state for border records and
+    # 1 MiB of headroom: room for three at a time
+    be = FakeBackend(total_bytes=(1 << 20) + 3 * 2 * f.cells(r) + f.cells(r) // 2 + 100)
     loop = RequestLoop(max_slots=16, chunk=4, reserve_bytes=0, backend=be)
     out = loop.run(reqs, max_seconds=30)
     assert out["requests"] == len(reqs)
@@ -108,7 +108,7 @@ def test_a_request_that_can_never_fit_is_rejected_and_the_loop_ends():
     reqs = [I.Request(0, 0.0, small, 3), I.Request(1, 0.0, big, 3), I.Request(2, 0.0, small, 2)]
     # room for a small request's buffers, never for the big one's (no max_seconds: the
     # loop must end by itself)
-    be = FakeBackend(total_bytes=(1 << 20) + 2 * f.cells(5) + f.cells(5) // 4 + 10)
+    be = FakeBackend(total_bytes=(1 << 20) + 2 * f.cells(5) + f.cells(5) // 2 + 10)
     loop = RequestLoop(max_slots=4, chunk=4, reserve_bytes=0, backend=be)
     out = loop.run(reqs)
     assert loop.rejected == [1]

@@ -263,9 +263,9 @@ def chunk_table(lib, f, r, L, nbhd, passes):
     off = np.ascontiguousarray(f.offsets_array(), dtype=np.uint8)
     caps = np.zeros(3, dtype=np.uint64)
     assert lib.tile_sizes(f.s, f.k, ptr(off), r, L, ptr(caps)) == 0
-    halo = int(caps[2])
-    info = np.zeros(22, dtype=np.uint32)
-    table = np.zeros(4 * halo + 289, dtype=np.uint32)
+    slots, halo = int(caps[1]), int(caps[2])
+    info = np.zeros(23, dtype=np.uint32)
+    table = np.zeros(5 * halo + slots // 2 + 300, dtype=np.uint32)
     hoff = np.zeros(halo, dtype=np.uint32)
     hdir = np.zeros(halo, dtype=np.uint8)
     rc = lib.tile_chunks(f.s, f.k, ptr(off), r, L, nbhd, passes, ptr(info), ptr(table), ptr(hoff),
@@ -289,7 +289,7 @@ def test_halo_chunk_table_serves_every_halo_cell(lib, f, r, L, nbhd, passes):
     assert np.array_equal(hoff[:nhalo], prog["halo_off"])
     nch, cs = int(info[0]), info[1:11].astype(np.int64)
     if prog["TW"] != 64:
-        assert nch == 0 and info[11] == 0
+        assert nch == 0
         return
     assert nch > 0 and cs[0] == 0 and cs[ndirs] == nch and np.all(np.diff(cs) >= 0)
     assert np.all(cs[ndirs:] == nch)
@@ -312,25 +312,42 @@ def test_halo_chunk_table_serves_every_halo_cell(lib, f, r, L, nbhd, passes):
     assert np.all(seen == 1)
 
 
+RECORD_CASES = CHUNK_CASES + [(I.VICSEK, 7, 4, oracle.MOORE), (I.TRIANGLE, 9, 5, VON_NEUMANN),
+                              (I.TRIANGLE, 8, 3, ONE_SIDED), (I.FULL2, 6, 4, oracle.MOORE),
+                              (DIAG2, 8, 4, oracle.MOORE)]
+
+
 @pytest.mark.parametrize("passes", [1, 4, 8])
-@pytest.mark.parametrize("f,r,L,nbhd", CHUNK_CASES[:4],
-                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in CHUNK_CASES[:4]])
+@pytest.mark.parametrize("f,r,L,nbhd", RECORD_CASES,
+                         ids=["%s-r%d-L%d-%x" % (f.name, r, L, m) for f, r, L, m in RECORD_CASES])
 def test_border_records_carry_every_halo_word(lib, f, r, L, nbhd, passes):
-    """64-wide rows read their halo from the adjacent tiles' border records:
-    emulate a launch writing every tile's record from its packed words (the
-    record table's slots) and the next reading them (its halo words), and
-    compare each halo word with the direct gather through halo_off."""
+    """The tiled step reads its halo from the adjacent tiles' border records:
+    emulate a launch writing every tile's record from its final words (kept
+    for the exported cells only) and the next reading them (its halo words),
+    and compare each halo word with the direct gather through halo_off."""
     prog = program(lib, f, r, L, nbhd, passes=passes)
     if prog is None:
         return
     rc, info, table, hoff, hdir = chunk_table(lib, f, r, L, nbhd, passes)
     assert rc == 0
     nhalo, ndirs, nch = prog["nhalo"], len(prog["dir_list"]), int(info[0])
-    R, seg = int(info[11]), info[12:22].astype(np.int64)
+    R, seg, nexp = int(info[11]), info[12:22].astype(np.int64), int(info[22])
+    if nhalo == 0:
+        assert R == 0
+        return
     assert R > 0 and seg[0] == 0 and seg[ndirs] == R and np.all(seg[ndirs:] == R)
-    rtab = table[2 * nch + 1 + nhalo:2 * nch + 1 + nhalo + 32 * R].astype(np.int64)
+    base = 2 * nch + 1 + nhalo if nch else 0
+    rtab = table[base:base + 32 * R].astype(np.int64)
+    exp_slot = table[base + 32 * R:base + 32 * R + nexp].astype(np.int64)
+    packed = table[base + 32 * R + nexp:base + 32 * R + nexp + (prog["slots"] + 1) // 2]
+    exp_of = np.stack([packed & 0xFFFF, packed >> 16], axis=1).reshape(-1)[:prog["slots"]]
     pad = rtab == 0xFFFFFFFF
-    slot_of, h_of = rtab & 0xFFFF, rtab >> 16
+    e_of, h_of = rtab & 0xFFFF, rtab >> 16
+    # the exported cells: distinct slots, each mapped back to its number
+    assert 0 < nexp <= nhalo and len(set(exp_slot.tolist())) == nexp
+    assert np.array_equal(exp_of[exp_slot], np.arange(nexp))
+    assert np.sum(exp_of != 0xFFFF) == nexp and np.all(e_of[~pad] < nexp)
+    slot_of = np.where(pad, 0, exp_slot[np.where(pad, 0, e_of)])
     # every halo word once, in its own direction's segment, ring by ring
     assert sorted(h_of[~pad].tolist()) == list(range(nhalo))
     for j in range(ndirs):

@@ -84,7 +84,7 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   B.slots_cap = z.slots;
   B.halo_cap = z.halo;
   B.passes = passes;
-  std::vector<uint32_t> chunks(4 * z.halo + 289);
+  std::vector<uint32_t> chunks(5 * z.halo + z.slots / 2 + 300);
   B.chunks = chunks.data();
   TileSpec sp;
   const int rc = sq_tile_build(f, L, B, sp);
@@ -103,12 +103,14 @@ int tile_program(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_
   return SQUEEZE_OK;
 }
 
-// The halo chunk and border-record tables of the level-L program (built for
-// 64-wide rows only): info = (nchunks, chunk_start[0..9], rec_words,
-// rec_seg[0..9]); table = nchunks chunk offsets, nchunks + 1 cell ranges,
-// nhalo cells (halo word | byte << 16), then 32 * rec_words record bits (slot
-// | halo word << 16, or ~0), 4 * halo + 289 words at most; halo_off and
-// halo_dir as in tile_program.
+// The halo chunk table (64-wide rows only) and the border-record tables of
+// the level-L program: info = (nchunks, chunk_start[0..9], rec_words,
+// rec_seg[0..9], rec_nexp); table = nchunks chunk offsets, nchunks + 1 cell
+// ranges, nhalo cells (halo word | byte << 16) -- absent for other widths --
+// then 32 * rec_words record bits (exported cell | halo word << 16, or ~0),
+// rec_nexp exported slots and the export number of every slot (16 bits, two
+// per word): 5 * halo + slots / 2 + 300 words at most; halo_off and halo_dir
+// as in tile_program.
 int tile_chunks(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t L,
                 uint32_t nbhd, uint32_t passes, uint32_t *info, uint32_t *table,
                 uint32_t *halo_off, uint8_t *halo_dir) {
@@ -131,6 +133,7 @@ int tile_chunks(uint32_t s, uint32_t k, const uint8_t *off, uint32_t r, uint32_t
   memcpy(info + 1, sp.chunk_start, sizeof(sp.chunk_start));
   info[11] = sp.rec_words;
   memcpy(info + 12, sp.rec_seg, sizeof(sp.rec_seg));
+  info[22] = sp.rec_nexp;
   return SQUEEZE_OK;
 }
 
