@@ -323,15 +323,23 @@ int squeeze_batch_info(const squeeze_batch *b, uint32_t *grid, uint32_t *threads
                        uint32_t *smem_bytes);
 
 /* squeeze_batch_run -- n_steps steps of every instance on `stream`, one
- * launch per instantiation and step, pair or quadruple of steps (up to four
+ * launch per instantiation and group of 1, 2, 4 or 8 steps (up to eight
  * steps per launch where the programs allow; the launch count keeps the
- * parity of n_steps);
- * with graphs on, the launches are captured once
- * (per distinct n_steps and starting buffer) and replayed.  The batch keeps
- * the step count across calls: every instance's state is in d_buf0 after an
- * even total number of steps since squeeze_batch_create and in d_buf1 after
- * an odd one. */
+ * parity of n_steps), after one launch per instantiation that writes the
+ * border records of the states (the halo of the first step) unless the
+ * previous run of the batch left them current; with graphs on, the launches
+ * are captured once (per distinct n_steps, starting buffer and whether the
+ * records are written) and replayed.  The batch keeps the step count across
+ * calls: every instance's state is in d_buf0 after an even total number of
+ * steps since squeeze_batch_create and in d_buf1 after an odd one.  Between
+ * runs the batch owns its items' states: a caller that writes one calls
+ * squeeze_batch_states_written before the next run. */
 int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream);
+
+/* squeeze_batch_states_written -- the caller wrote items' states after the
+ * last run: the next run rewrites the border records first.  INVALID_ARG for
+ * a null batch. */
+int squeeze_batch_states_written(squeeze_batch *b);
 
 /* squeeze_batch_destroy -- free the batch (not the handles or buffers). */
 int squeeze_batch_destroy(squeeze_batch *b);

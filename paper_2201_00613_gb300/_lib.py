@@ -100,6 +100,7 @@ _SIGS = {
     "squeeze_batch_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_uint32)] * 3, ctypes.c_int),
     "squeeze_batch_run": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
     "squeeze_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "squeeze_batch_states_written": ([ctypes.c_void_p], ctypes.c_int),
     "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
@@ -343,6 +344,10 @@ def squeeze_batch_info(b):
 
 def squeeze_batch_run(b, n_steps: int, stream=None):
     _check(_load().squeeze_batch_run(b, n_steps, _stream(stream)), "squeeze_batch_run")
+
+
+def squeeze_batch_states_written(b):
+    _check(_load().squeeze_batch_states_written(b), "squeeze_batch_states_written")
 
 
 def squeeze_batch_destroy(b):

@@ -49,9 +49,10 @@ struct squeeze_batch {
   int device;
   TiledDev *d_devs;
   uint8_t **d_buf0, **d_buf1;
-  uint32_t *d_rec;          // border records of the items with 64-wide rows, two per item
+  uint32_t *d_rec;          // border records of the items, two per item
+  bool rec_valid;           // the records of the current states are written (after a run)
   cudaStream_t capture;     // stream the graphs are captured on
-  std::map<uint64_t, cudaGraphExec_t> graphs;  // (n_steps, parity) -> executable graph
+  std::map<uint64_t, cudaGraphExec_t> graphs;  // (n_steps, parity, records) -> executable graph
 };
 
 namespace {
@@ -149,6 +150,7 @@ void stride_schedule(std::vector<BatchWork> &work, const std::vector<uint32_t> &
 
 int setup(squeeze_batch *b) {
   release(b);
+  b->rec_valid = false;
   const uint32_t count = (uint32_t)b->items.size();
   std::vector<TiledDev> devs(count);
   std::vector<TileSpec> specs(count);
@@ -264,16 +266,20 @@ int setup(squeeze_batch *b) {
 // Launches of n_steps steps: up to eight steps per launch where every plan
 // can, with a launch count of n_steps' parity (each launch swaps the
 // buffers; the state after an even number of steps belongs in buffer 0).
-int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
+int launch_steps(squeeze_batch *b, uint64_t n_steps, bool rec_current, cudaStream_t st) {
   uint32_t passes = kBatchPasses;
   for (const BatchPlan &p : b->plans) passes = p.passes < passes ? p.passes : passes;
   uint64_t counts[4];
   sq_launch_plan(n_steps, passes, counts);
   const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
-  // The launches read their halo from border records: first those of the
-  // input (one records-only launch per instantiation whose items have any)
+  // Launches of several steps read their halo from border records: first
+  // those of the input (one records-only launch per instantiation whose items
+  // have any) unless they are current; one-step launches can gather it from
+  // the states instead.
+  const bool boot = !rec_current && counts[1] + counts[2] + counts[3] != 0;
+  bool live = rec_current || boot;
   for (const BatchPlan &p : b->plans) {
-    if (!p.records || !total) continue;
+    if (!boot || !p.records || !total) continue;
     int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay, p.grid,
                              p.threads, p.life, p.kind, 1, (uint32_t)(b->parity & 1u), 1, st);
     if (rc) return rc;
@@ -288,9 +294,11 @@ int launch_steps(squeeze_batch *b, uint64_t n_steps, cudaStream_t st) {
     const uint32_t steps = 1u << i;
     for (const BatchPlan &p : b->plans) {
       int rc = sq_batch_launch(b->d_devs, b->d_buf0, b->d_buf1, p.d_work, p.d_sched, p.lay,
-                               p.grid, p.threads, p.life, p.kind, steps, parity, 0, st);
+                               p.grid, p.threads, p.life, p.kind, steps, parity, live ? 0 : 2,
+                               st);
       if (rc) return rc;
     }
+    live = true;
   }
   return SQUEEZE_OK;
 }
@@ -358,18 +366,22 @@ int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream) {
   if (!b) return SQUEEZE_ERR_INVALID_ARG;
   if (!n_steps) return SQUEEZE_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  // The records of the states are rewritten only when they are not known to
+  // be current (the first run, or after squeeze_batch_states_written).
+  const bool current = b->rec_valid;
   if (!b->use_graph) {
-    int rc = launch_steps(b, n_steps, st);
+    int rc = launch_steps(b, n_steps, current, st);
     if (rc == SQUEEZE_OK) b->parity ^= (uint32_t)(n_steps & 1u);
+    b->rec_valid = rc == SQUEEZE_OK;
     return rc;
   }
-  const uint64_t key = n_steps * 2 + b->parity;
+  const uint64_t key = (n_steps * 2 + b->parity) * 2 + (current ? 0u : 1u);
   auto found = b->graphs.find(key);
   if (found == b->graphs.end()) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     SQ_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_steps(b, n_steps, b->capture);
+    int rc = launch_steps(b, n_steps, current, b->capture);
     cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -380,8 +392,16 @@ int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream) {
     if (e != cudaSuccess) return sq_cuda_fail(e);
     found = b->graphs.emplace(key, exec).first;
   }
+  b->rec_valid = false;
   SQ_CUDA(cudaGraphLaunch(found->second, st));
   b->parity ^= (uint32_t)(n_steps & 1u);
+  b->rec_valid = true;
+  return SQUEEZE_OK;
+}
+
+int squeeze_batch_states_written(squeeze_batch *b) {
+  if (!b) return SQUEEZE_ERR_INVALID_ARG;
+  b->rec_valid = false;
   return SQUEEZE_OK;
 }
 

@@ -236,10 +236,11 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
   uint64_t counts[4] = {n_steps, 0, 0, 0};
   if (kind == SQUEEZE_STEP_TILED) sq_launch_plan(n_steps, sq_tiled_passes(h), counts);
   const uint64_t total = counts[0] + counts[1] + counts[2] + counts[3];
-  // 64-wide rows: the border records of the input first (one extra launch)
+  // the border records of the input first (one extra launch) when a launch of
+  // several steps will read them
   int extra = 0;
   if (kind == SQUEEZE_STEP_TILED && total) {
-    const int rc = sq_tiled_begin(h, d_buf0, st, &extra);
+    const int rc = sq_tiled_begin(h, d_buf0, counts[1] + counts[2] + counts[3] != 0, st, &extra);
     if (rc) return rc;
   }
   uint8_t *a = d_buf0, *b = d_buf1;
@@ -252,7 +253,7 @@ int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n
     const uint32_t steps = 1u << i;
     int rc;
     switch (kind) {
-      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, steps, st); break;
+      case SQUEEZE_STEP_TILED: rc = sq_launch_step_tiled(h, a, b, steps, t + 1 == total, st); break;
       case SQUEEZE_MAP_TC_BF16: rc = sq_launch_step_tc(h, a, b, st); break;
       default: rc = sq_launch_step_alu(h, a, b, st); break;
     }

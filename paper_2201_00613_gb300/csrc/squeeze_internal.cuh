@@ -360,12 +360,15 @@ int sq_launch_step_alu(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
                        cudaStream_t st);
 int sq_tiled_prepare(squeeze_handle *h);
 // One launch of the handle's tiled program: steps = 1, 2, 4 or 8, at most the
-// passes the program was built for (sq_tiled_passes).
+// passes the program was built for (sq_tiled_passes); `last`: no later launch
+// of the call reads the border records of its output.
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
-                         uint32_t steps, cudaStream_t st);
-// Border records of a squeeze_step call's input (before its tiled launches;
-// *launches = 1 if a records-only launch was made).
-int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, int *launches);
+                         uint32_t steps, bool last, cudaStream_t st);
+// Border records of a squeeze_step call's input, before its tiled launches,
+// when some launch advances several steps (multi); *launches = 1 if a
+// records-only launch was made.
+int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, bool multi, cudaStream_t st,
+                   int *launches);
 uint32_t sq_tiled_passes(const squeeze_handle *h);
 // Launches of n steps at up to `passes` steps each: counts[i] launches of
 // 2^i steps (i = 0..3), with a launch count of n's parity (every launch swaps

@@ -49,6 +49,7 @@ struct TiledProgram {
   // input (the launches of a call alternate, like the buffers).
   uint32_t *d_rec[2];
   int rec_cur;
+  bool rec_live;            // d_rec[rec_cur] holds the records of the next launch's input
 };
 
 namespace sq {
@@ -703,25 +704,31 @@ int sq_tiled_prepare(squeeze_handle *h) {
 }
 
 int sq_launch_step_tiled(const squeeze_handle *h, const uint8_t *in, uint8_t *out,
-                         uint32_t steps, cudaStream_t st) {
+                         uint32_t steps, bool last, cudaStream_t st) {
   TiledProgram *p = h->tiled;
   if (!p) return SQUEEZE_ERR_INVALID_ARG;
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
   if (h->wait_ns) d.wait_ns = h->wait_ns;
   d.fault = h->fault;
-  if (p->spec.rec_words) {   // records of the input, and of the output for the next launch
-    d.rec[0] = p->d_rec[p->rec_cur];
-    d.rec[1] = p->d_rec[p->rec_cur ^ 1];
+  if (p->spec.rec_words) {   // records of the input (else gathered), and of the output
+    d.rec[0] = p->rec_live ? p->d_rec[p->rec_cur] : nullptr;
+    d.rec[1] = last ? nullptr : p->d_rec[p->rec_cur ^ 1];
   }
   const int rc = sq_tile_launch(d, p->spec, in, out, steps, st);
-  if (rc == SQUEEZE_OK) p->rec_cur ^= 1;
+  if (rc == SQUEEZE_OK) {
+    p->rec_cur ^= 1;
+    p->rec_live = p->spec.rec_words != 0 && !last;
+  }
   return rc;
 }
 
 // Before the launches of a squeeze_step call: the border records of its input
-// (one records-only launch; nothing for programs without records).
-int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, int *launches) {
+// when a launch of several steps will read them (one records-only launch);
+// one-step launches gather the halo from the state instead (and write the
+// records of their output, which later launches of the call read).
+int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, bool multi, cudaStream_t st,
+                   int *launches) {
   TiledProgram *p = h->tiled;
   *launches = 0;
   if (!p || !p->spec.rec_words) return SQUEEZE_OK;
@@ -729,15 +736,19 @@ int sq_tiled_begin(const squeeze_handle *h, const uint8_t *in, cudaStream_t st, 
   const size_t rec_bytes = (size_t)p->spec.rec_words * p->spec.tiles_x * p->spec.tiles_y * 4;
   for (int i = 0; i < 2; ++i)
     if (!p->d_rec[i]) SQ_CUDA(cudaMalloc(&p->d_rec[i], rec_bytes));
+  p->rec_cur = 0;
+  p->rec_live = false;
+  if (!multi) return SQUEEZE_OK;
   TiledDev d = sq_tiled_dev(h->f, h->rule, p->spec, p->d_refs, p->d_halo_off, p->d_halo_dir,
                             p->d_adj, h->d_status);
   if (h->wait_ns) d.wait_ns = h->wait_ns;
   d.fault = h->fault;
   d.rec[1] = p->d_rec[0];
   d.mode = 1;
-  p->rec_cur = 0;
   *launches = 1;
-  return sq_tile_launch(d, p->spec, in, const_cast<uint8_t *>(in), 1, st);
+  const int rc = sq_tile_launch(d, p->spec, in, const_cast<uint8_t *>(in), 1, st);
+  p->rec_live = rc == SQUEEZE_OK;
+  return rc;
 }
 
 uint32_t sq_tiled_passes(const squeeze_handle *h) { return h->tiled ? h->tiled->spec.passes : 1u; }

@@ -1118,8 +1118,9 @@ __global__ void __launch_bounds__(kTW == 64 ? 256 : kTiledMaxThreads) step_tiled
 // kT steps (1, 2, 4 or 8) of many instances (each with its own fractal, level
 // and buffers) that share one tile-row instantiation, in a single persistent
 // launch.  parity selects the launch's input: buffer 0 or buffer 1 (and the
-// border records of that buffer, for 64-wide rows); mode 1 writes only the
-// input's records (before the first step of a run).  CTA c
+// border records of that buffer); mode 1 writes only the input's records
+// (before the first step of a run), mode 2 (one step per launch) gathers the
+// halo from the state instead of the records and writes the output's.  CTA c
 // walks its schedule entries, each a run of groups of one instance (g_first,
 // g_first + g_stride, ... below g_end); the instance's description is copied
 // to shared memory for the run (its fields are read throughout the group
@@ -1146,8 +1147,8 @@ __global__ void __launch_bounds__(kTiledMaxThreads, 3) step_batch_kernel(
     const uint8_t *in = parity ? buf1[w.instance] : buf0[w.instance];
     uint8_t *out = parity ? buf0[w.instance] : buf1[w.instance];
     run_groups<kLife, kTW, kT>(s_dev, lay, in, out, w.g_first, w.g_end, w.g_stride, smem, keep, rot,
-                               it, mode ? nullptr : s_dev.rec[parity],
-                               s_dev.rec[mode ? parity : parity ^ 1u], mode == 1u);
+                               it, mode == 0u ? s_dev.rec[parity] : nullptr,
+                               s_dev.rec[mode == 1u ? parity : parity ^ 1u], mode == 1u);
   }
   bulk_wait_all();
   settle_abort();

@@ -171,3 +171,49 @@ def test_items_sharing_a_handle_keep_their_own_states(steps):
     finally:
         for h in handles.values():
             h.close()
+
+
+def test_runs_reuse_current_records_and_states_written_renews_them():
+    """A second run of a batch reads the records its first run left (no
+    records launch); after the caller rewrites a state and says so, the next
+    run writes the records again: every result equals the solo run of the
+    state the batch was given."""
+    shapes = [(I.TRIANGLE, 10), (I.CARPET, 6), (I.VICSEK, 7)]
+    handles = [sq.Handle(f, r) for f, r in shapes]
+    try:
+        bufs = []
+        for i, h in enumerate(handles):
+            a = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+            bufs.append((a, torch.empty_like(a)))
+            sq.squeeze_init_bernoulli(h.h, a, 40 + i, I.p_q24(0.5))
+        start = [a.clone() for a, _ in bufs]
+        batch = sq.squeeze_batch_create([(h.h, a, b) for h, (a, b) in zip(handles, bufs)])
+        sq.squeeze_batch_run(batch, 5)
+        sq.squeeze_batch_run(batch, 6)          # 11 steps, state in buffer 1
+        torch.cuda.synchronize()
+        for h, (a, b), s0, (f, r) in zip(handles, bufs, start, shapes):
+            want = solo_from(h, s0, 11)
+            assert torch.equal(b, want), f.name
+        # rewrite the states (in buffer 1, where the batch keeps them now)
+        for i, (h, (a, b)) in enumerate(zip(handles, bufs)):
+            sq.squeeze_init_bernoulli(h.h, b, 90 + i, I.p_q24(0.4))
+        fresh = [b.clone() for _, b in bufs]
+        sq.squeeze_batch_states_written(batch)
+        sq.squeeze_batch_run(batch, 7)          # 18 steps in all, state in buffer 0
+        torch.cuda.synchronize()
+        for h, (a, b), s0, (f, r) in zip(handles, bufs, fresh, shapes):
+            assert torch.equal(a, solo_from(h, s0, 7)), f.name
+        sq.squeeze_batch_destroy(batch)
+        with pytest.raises(sq.SqueezeError):
+            sq.squeeze_batch_states_written(None)
+    finally:
+        for h in handles:
+            h.close()
+
+
+def solo_from(h, state, steps):
+    a = state.clone()
+    b = torch.empty_like(a)
+    sq.squeeze_step(h.h, a, b, steps, sq.SQUEEZE_STEP_TILED)
+    torch.cuda.synchronize()
+    return (b if steps % 2 else a).clone()

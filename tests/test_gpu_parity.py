@@ -469,6 +469,8 @@ def test_launch_plan_puts_the_result_in_the_right_buffer(steps):
         c0 = I.bernoulli_bytes(5, h.cells, 0.5)
         got = run_steps(h, c0, steps, sq.SQUEEZE_STEP_TILED)
         _, launches, by = sq.squeeze_last_step_info(h.h)
-        assert launches == sum(by) + 1 and sum(by) % 2 == steps % 2   # + the records launch
+        # + the launch that writes the input's border records, when a launch
+        # of several steps reads them
+        assert launches == sum(by) + (1 if sum(by[1:]) else 0) and sum(by) % 2 == steps % 2
         assert sum(c << i for i, c in enumerate(by)) == steps
         assert np.array_equal(got, oracle.run_compact(f, r, c0, steps))
