@@ -340,6 +340,13 @@ int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_pe
                             int use_graph) {
   if (!b || threads % 32 || (threads && threads < 64) || threads > 384)
     return SQUEEZE_ERR_INVALID_ARG;
+  if ((int)threads == b->threads && (int)ctas_per_sm == b->ctas_per_sm) {
+    // same launch shape: keep the plans (and the current records)
+    if (!b->graphs.empty()) SQ_CUDA(cudaDeviceSynchronize());
+    release_graphs(b);
+    b->use_graph = use_graph != 0;
+    return SQUEEZE_OK;
+  }
   SQ_CUDA(cudaDeviceSynchronize());
   b->threads = (int)threads;
   b->ctas_per_sm = (int)ctas_per_sm;
