@@ -47,6 +47,7 @@ struct squeeze_batch {
   bool use_graph;
   uint32_t parity;          // 0: states are in buffer 0, 1: in buffer 1
   int device;
+  unsigned char *d_arena;   // one device allocation: the tables below, then the records
   TiledDev *d_devs;
   uint8_t **d_buf0, **d_buf1;
   uint32_t *d_rec;          // border records of the items, two per item
@@ -64,16 +65,10 @@ void release_graphs(squeeze_batch *b) {
 
 void release(squeeze_batch *b) {
   release_graphs(b);
-  for (BatchPlan &p : b->plans) {
-    cudaFree(p.d_work);
-    cudaFree(p.d_sched);
-  }
   b->plans.clear();
-  cudaFree(b->d_devs);
-  cudaFree(b->d_buf0);
-  cudaFree(b->d_buf1);
-  cudaFree(b->d_rec);
+  cudaFree(b->d_arena);   // the plans' schedules, descriptions and records live in it
   if (b->capture) cudaStreamDestroy(b->capture);
+  b->d_arena = nullptr;
   b->d_rec = nullptr;
   b->d_devs = nullptr;
   b->d_buf0 = b->d_buf1 = nullptr;
@@ -226,40 +221,55 @@ int setup(squeeze_batch *b) {
     starts.push_back(start);
   }
 
-  // Border records (64-wide rows): two buffers per item, of this batch alone
-  // (items may share a handle, each with its own states).
+  // One device allocation and one copy for the batch: the items'
+  // descriptions and buffer pointers, each plan's schedule, then the border
+  // records (two buffers per item, of this batch alone: items may share a
+  // handle, each with its own states).
+  auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t off = 0;
+  const size_t o_devs = off;
+  off = align(off + sizeof(TiledDev) * count);
+  const size_t o_buf0 = off;
+  off = align(off + sizeof(uint8_t *) * count);
+  const size_t o_buf1 = off;
+  off = align(off + sizeof(uint8_t *) * count);
+  std::vector<size_t> o_work(b->plans.size()), o_sched(b->plans.size());
+  for (size_t k = 0; k < b->plans.size(); ++k) {
+    o_work[k] = off;
+    off = align(off + sizeof(BatchWork) * (works[k].size() ? works[k].size() : 1));
+    o_sched[k] = off;
+    off = align(off + sizeof(uint32_t) * starts[k].size());
+  }
+  const size_t table_bytes = off;
   size_t rec_total = 0;
   for (uint32_t i = 0; i < count; ++i)
     rec_total += 2ull * specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
-  if (rec_total) {
-    SQ_CUDA(cudaMalloc(&b->d_rec, rec_total * 4));
-    size_t off = 0;
-    for (uint32_t i = 0; i < count; ++i) {
-      const size_t n = (size_t)specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
-      devs[i].rec[0] = n ? b->d_rec + off : nullptr;          // records of buffer 0
-      devs[i].rec[1] = n ? b->d_rec + off + n : nullptr;      // and of buffer 1
-      off += 2 * n;
-    }
+  SQ_CUDA(cudaMalloc(&b->d_arena, table_bytes + rec_total * 4));
+  unsigned char *base = b->d_arena;
+  b->d_rec = rec_total ? reinterpret_cast<uint32_t *>(base + table_bytes) : nullptr;
+  size_t roff = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const size_t n = (size_t)specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
+    devs[i].rec[0] = n ? b->d_rec + roff : nullptr;          // records of buffer 0
+    devs[i].rec[1] = n ? b->d_rec + roff + n : nullptr;      // and of buffer 1
+    roff += 2 * n;
   }
-  SQ_CUDA(cudaMalloc(&b->d_devs, sizeof(TiledDev) * count));
-  SQ_CUDA(cudaMalloc(&b->d_buf0, sizeof(uint8_t *) * count));
-  SQ_CUDA(cudaMalloc(&b->d_buf1, sizeof(uint8_t *) * count));
-  SQ_CUDA(cudaMemcpy(b->d_devs, devs.data(), sizeof(TiledDev) * count, cudaMemcpyHostToDevice));
-  SQ_CUDA(cudaMemcpy(b->d_buf0, buf0.data(), sizeof(uint8_t *) * count, cudaMemcpyHostToDevice));
-  SQ_CUDA(cudaMemcpy(b->d_buf1, buf1.data(), sizeof(uint8_t *) * count, cudaMemcpyHostToDevice));
+  std::vector<unsigned char> host(table_bytes, 0);
+  memcpy(host.data() + o_devs, devs.data(), sizeof(TiledDev) * count);
+  memcpy(host.data() + o_buf0, buf0.data(), sizeof(uint8_t *) * count);
+  memcpy(host.data() + o_buf1, buf1.data(), sizeof(uint8_t *) * count);
   for (size_t k = 0; k < b->plans.size(); ++k) {
     BatchPlan &p = b->plans[k];
-    const std::vector<BatchWork> &work = works[k];
-    const std::vector<uint32_t> &start = starts[k];
-    SQ_CUDA(cudaMalloc(&p.d_work, sizeof(BatchWork) * (work.size() ? work.size() : 1)));
-    SQ_CUDA(cudaMalloc(&p.d_sched, sizeof(uint32_t) * start.size()));
-    if (work.size())
-      SQ_CUDA(cudaMemcpy(p.d_work, work.data(), sizeof(BatchWork) * work.size(),
-                         cudaMemcpyHostToDevice));
-    SQ_CUDA(cudaMemcpy(p.d_sched, start.data(), sizeof(uint32_t) * start.size(),
-                       cudaMemcpyHostToDevice));
+    if (works[k].size())
+      memcpy(host.data() + o_work[k], works[k].data(), sizeof(BatchWork) * works[k].size());
+    memcpy(host.data() + o_sched[k], starts[k].data(), sizeof(uint32_t) * starts[k].size());
+    p.d_work = reinterpret_cast<BatchWork *>(base + o_work[k]);
+    p.d_sched = reinterpret_cast<uint32_t *>(base + o_sched[k]);
   }
-  SQ_CUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+  b->d_devs = reinterpret_cast<TiledDev *>(base + o_devs);
+  b->d_buf0 = reinterpret_cast<uint8_t **>(base + o_buf0);
+  b->d_buf1 = reinterpret_cast<uint8_t **>(base + o_buf1);
+  SQ_CUDA(cudaMemcpy(base, host.data(), table_bytes, cudaMemcpyHostToDevice));
   return SQUEEZE_OK;
 }
 
@@ -385,6 +395,7 @@ int squeeze_batch_run(squeeze_batch *b, uint64_t n_steps, void *stream) {
   const uint64_t key = (n_steps * 2 + b->parity) * 2 + (current ? 0u : 1u);
   auto found = b->graphs.find(key);
   if (found == b->graphs.end()) {
+    if (!b->capture) SQ_CUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     SQ_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));

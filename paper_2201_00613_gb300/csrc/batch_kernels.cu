@@ -33,9 +33,7 @@ using namespace sq;
 
 int sq_batch_occupancy(bool life, int kind, uint32_t steps, int threads, uint32_t smem) {
   const void *fn = batch_kernel_for(life, kind, steps);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
+  if (sq_allow_smem(fn, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 0;
   return n;

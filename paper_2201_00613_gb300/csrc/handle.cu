@@ -7,7 +7,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "squeeze_internal.cuh"
 
@@ -65,6 +68,24 @@ int sq_fill_fractal(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r, 
 
 void sq_set_error_text(const char *text) {
   snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s", text);
+}
+
+// The dynamic shared memory a kernel may use is an attribute of the function
+// (per device), shared by every handle and batch that launches it: it is only
+// ever raised, so that a program with less shared memory does not lower it
+// under a program with more that launches the same kernel.
+cudaError_t sq_allow_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> allowed;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = allowed[std::make_pair(dev, fn)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 int sq_cuda_fail(cudaError_t e) {

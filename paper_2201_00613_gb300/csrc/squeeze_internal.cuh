@@ -341,6 +341,9 @@ struct squeeze_handle {
 
 // Error plumbing and descriptor validation (handle.cu).
 int sq_cuda_fail(cudaError_t e);
+// Allow a kernel `bytes` of dynamic shared memory on the current device
+// (raised only; see handle.cu).
+cudaError_t sq_allow_smem(const void *fn, size_t bytes);
 void sq_set_error_text(const char *text);
 int sq_fill_fractal(uint32_t s, uint32_t k, const uint8_t *offsets, uint32_t r, sq::FracDev &f);
 #define SQ_CUDA(call)                                 \

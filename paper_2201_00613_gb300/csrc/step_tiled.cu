@@ -21,10 +21,11 @@
 // cells per bitwise operation); the inverse transpose and an unaligned,
 // merged unpack return the bytes to the staging rows, and TMA bulk stores
 // write them back.  Rows 8 or 16 cells wide share a word (4 or 2 rows per
-// word); rows 64 cells wide take two words.  Only halo bytes are read with
-// single-byte loads; for 64-wide rows (whose tiles start on 64-byte
-// boundaries) the halo comes in 16-byte chunks of the adjacent tiles, one load
-// serving every halo cell of the chunk.
+// word); rows 64 cells wide take two words.  A launch of several steps reads
+// its halo from border records, a few words per tile that the previous launch
+// wrote for its neighbours; a one-step launch can instead read the halo bytes
+// from the state (single bytes, or for 64-wide rows, whose tiles start on
+// 64-byte boundaries, 16-byte chunks of the adjacent tiles).
 //
 // Bit order of a packed row word: bit 8b + j holds tile-row byte 4j + b (the
 // order the pack produces for free); the neighbour program is built in that
@@ -44,9 +45,9 @@ struct TiledProgram {
   uint32_t *d_halo_off;     // nhalo byte offsets inside a tile (ly * W + lx)
   uint8_t *d_halo_dir;      // nhalo indices into dir_list
   uint32_t *d_adj;          // ndirs x tiles: adjacent tile index, or ~0 (hole / off the box)
-  // Border records (64-wide rows): tiles x rec_words words each, one per state
-  // buffer of a squeeze_step call; rec_cur is the one of the next launch's
-  // input (the launches of a call alternate, like the buffers).
+  // Border records: tiles x rec_words words each, one per state buffer of a
+  // squeeze_step call; rec_cur is the one of the next launch's input (the
+  // launches of a call alternate, like the buffers).
   uint32_t *d_rec[2];
   int rec_cur;
   bool rec_live;            // d_rec[rec_cur] holds the records of the next launch's input
@@ -575,7 +576,7 @@ int sq_tile_launch_config(TileSpec &sp, int device) {
   for (uint32_t steps = 1; steps <= sp.passes; steps *= 2)
     for (int life = 0; life < 2; ++life) {
       const void *fn = tiled_kernel_for(life != 0, sp.TW, sp.rpw, steps);
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
+      e = sq_allow_smem(fn, sp.smem);
       int n = 0;
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, sp.threads, sp.smem);

@@ -523,7 +523,7 @@ int sq3_tile_prepare(const Frac3Dev &f, uint32_t L, int device, Tile3Program **o
   const void *fn = TX == 16 ? (const void *)tile3_kernel<16> : (const void *)tile3_kernel<8>;
   int n = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = sq_allow_smem(fn, smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kT3Threads, smem);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess || n < 1) {

@@ -5,6 +5,7 @@
 #include "nbb3d.cu"
 
 int sq_cuda_fail(cudaError_t) { return SQUEEZE_ERR_CUDA; }   // never reached: no CUDA calls here
+cudaError_t sq_allow_smem(const void *, size_t) { return cudaSuccess; }
 // The tile kernel (tile3d.cu) is not part of this host library; the step
 // entry point that would reach it is never called here.
 bool sq3_tile_shape(const Frac3Dev &, uint32_t, uint32_t &, uint32_t &, uint32_t &, uint32_t &,

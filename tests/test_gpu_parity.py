@@ -474,3 +474,20 @@ def test_launch_plan_puts_the_result_in_the_right_buffer(steps):
         assert launches == sum(by) + (1 if sum(by[1:]) else 0) and sum(by) % 2 == steps % 2
         assert sum(c << i for i, c in enumerate(by)) == steps
         assert np.array_equal(got, oracle.run_compact(f, r, c0, steps))
+
+
+def test_handles_sharing_a_kernel_with_less_shared_memory_do_not_break_each_other():
+    """The eight-ring program's two-step launches need more shared memory than
+    a two-ring program's launches of the same kernel: preparing the smaller
+    one after the larger must not take shared memory away from the larger."""
+    f, r = I.TRIANGLE, 10
+    c0 = I.bernoulli_bytes(77, f.k ** r, 0.5)
+    want = oracle.run_compact(f, r, c0, 10)
+    with sq.Handle(f, r) as big, sq.Handle(f, r) as small:
+        assert np.array_equal(run_steps(big, c0, 10, sq.SQUEEZE_STEP_TILED), want)  # 8 + 2
+        sq.squeeze_set_max_steps_per_launch(small.h, 2)
+        assert np.array_equal(run_steps(small, c0, 10, sq.SQUEEZE_STEP_TILED), want)
+        assert np.array_equal(run_steps(big, c0, 10, sq.SQUEEZE_STEP_TILED), want)
+        assert sq.squeeze_last_step_info(big.h)[2][1] == 1   # the two-step launch ran
+        assert_status_ok(big)
+        assert_status_ok(small)
