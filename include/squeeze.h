@@ -171,6 +171,18 @@ int squeeze_init_bernoulli(const squeeze_handle *h, uint8_t *d_state, uint64_t s
 int squeeze_step(squeeze_handle *h, uint8_t *d_buf0, uint8_t *d_buf1, uint64_t n_steps,
                  int kind, void *stream);
 
+/* squeeze_record_bytes -- bytes of one border-record buffer of the handle's
+ * tiled program (0 when its tiles have no halo): the states of the cells that
+ * adjacent tiles read as halo, 4 bytes per 32 such cells and direction per
+ * tile.  Prepares the tiled program if needed. */
+int squeeze_record_bytes(squeeze_handle *h, uint64_t *bytes);
+
+/* squeeze_write_records -- the border records of the compact state d_state
+ * (16-byte aligned) into d_rec (squeeze_record_bytes bytes, 4-byte aligned),
+ * one launch on `stream`; nothing for a program without records. */
+int squeeze_write_records(squeeze_handle *h, const uint8_t *d_state, uint32_t *d_rec,
+                          void *stream);
+
 /* squeeze_set_max_steps_per_launch -- the most steps one launch of the tiled
  * kernel may advance: 1, 2, 4 or 8, or 0 for the default (the most whose
  * kernel keeps the CTAs per SM of the one-step kernel, or 3 if that has
@@ -307,6 +319,18 @@ typedef struct {
  * together need more shared memory than one CTA may use; OOM / CUDA when a
  * device allocation or copy fails (nothing is left allocated then). */
 int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out);
+
+/* squeeze_batch_create_with_records -- squeeze_batch_create with the items'
+ * border records in the caller's buffers: d_rec[2 i] holds the records of
+ * item i's d_buf0 and d_rec[2 i + 1] those of its d_buf1, squeeze_record_bytes
+ * bytes each (4-byte aligned; ignored, and may be null, for an item whose
+ * program has none).  The records of every d_buf0 must be current (written by
+ * squeeze_write_records, or by a run of a batch that used the same buffers),
+ * so the first run makes no records-only launch; runs keep each item's records
+ * in step with its states.  Errors as squeeze_batch_create, and INVALID_ARG for
+ * a missing or misaligned record buffer. */
+int squeeze_batch_create_with_records(const squeeze_batch_item *items, uint32_t count,
+                                      uint32_t *const *d_rec, squeeze_batch **out);
 
 /* squeeze_batch_configure -- launch shape chosen by the autotuner: threads per
  * CTA (0 = each instantiation's own choice, the one squeeze_step makes; else a

@@ -101,6 +101,11 @@ _SIGS = {
     "squeeze_batch_run": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
     "squeeze_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "squeeze_batch_states_written": ([ctypes.c_void_p], ctypes.c_int),
+    "squeeze_batch_create_with_records": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "squeeze_record_bytes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "squeeze_write_records": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                              ctypes.c_int),
     "squeeze_step_noalloc": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p], ctypes.c_int),
@@ -328,6 +333,32 @@ def squeeze_batch_create(items):
     _check(_load().squeeze_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(items),
                                         ctypes.byref(out)), "squeeze_batch_create")
     return out.value
+
+
+def squeeze_batch_create_with_records(items, records):
+    """items: sequence of (handle, d_buf0, d_buf1); records: sequence of
+    (d_rec0, d_rec1) per item (None where the program has no records), the
+    records of d_buf0 current; returns the batch pointer."""
+    arr = (_BatchItem * len(items))(*[_BatchItem(h, _ptr(a), _ptr(b)) for h, a, b in items])
+    recs = (ctypes.c_void_p * (2 * len(items)))(
+        *[_ptr(r) if r is not None else None for pair in records for r in pair])
+    out = ctypes.c_void_p()
+    _check(_load().squeeze_batch_create_with_records(ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                                     ctypes.cast(recs, ctypes.c_void_p),
+                                                     ctypes.byref(out)),
+           "squeeze_batch_create_with_records")
+    return out.value
+
+
+def squeeze_record_bytes(h) -> int:
+    v = ctypes.c_uint64()
+    _check(_load().squeeze_record_bytes(h, ctypes.byref(v)), "squeeze_record_bytes")
+    return int(v.value)
+
+
+def squeeze_write_records(h, d_state, d_rec, stream=None):
+    _check(_load().squeeze_write_records(h, _ptr(d_state), _ptr(d_rec), _stream(stream)),
+           "squeeze_write_records")
 
 
 def squeeze_batch_configure(b, threads: int, ctas_per_sm: int = 0, use_graph: bool = True):

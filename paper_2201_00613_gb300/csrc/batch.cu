@@ -42,6 +42,7 @@ struct BatchPlan {
 
 struct squeeze_batch {
   std::vector<squeeze_batch_item> items;
+  std::vector<uint32_t *> caller_rec;  // 2 per item (records of d_buf0, d_buf1), or empty
   std::vector<BatchPlan> plans;
   int threads, ctas_per_sm;   // 0: each plan's own CTA size / the occupancy limit
   bool use_graph;
@@ -242,7 +243,8 @@ int setup(squeeze_batch *b) {
   }
   const size_t table_bytes = off;
   size_t rec_total = 0;
-  for (uint32_t i = 0; i < count; ++i)
+  const bool own_rec = b->caller_rec.empty();
+  for (uint32_t i = 0; i < count && own_rec; ++i)
     rec_total += 2ull * specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
   SQ_CUDA(cudaMalloc(&b->d_arena, table_bytes + rec_total * 4));
   unsigned char *base = b->d_arena;
@@ -250,6 +252,11 @@ int setup(squeeze_batch *b) {
   size_t roff = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const size_t n = (size_t)specs[i].rec_words * specs[i].tiles_x * specs[i].tiles_y;
+    if (!own_rec) {   // the caller's buffers (checked at creation)
+      devs[i].rec[0] = n ? b->caller_rec[2 * i] : nullptr;
+      devs[i].rec[1] = n ? b->caller_rec[2 * i + 1] : nullptr;
+      continue;
+    }
     devs[i].rec[0] = n ? b->d_rec + roff : nullptr;          // records of buffer 0
     devs[i].rec[1] = n ? b->d_rec + roff + n : nullptr;      // and of buffer 1
     roff += 2 * n;
@@ -313,11 +320,10 @@ int launch_steps(squeeze_batch *b, uint64_t n_steps, bool rec_current, cudaStrea
   return SQUEEZE_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out) {
+// A batch of `count` items; d_rec (2 per item: the records of d_buf0 and of
+// d_buf1, those of d_buf0 current) or null for records of the batch's own.
+int create_batch(const squeeze_batch_item *items, uint32_t count, uint32_t *const *d_rec,
+                 squeeze_batch **out) {
   if (!out || !items || !count) return SQUEEZE_ERR_INVALID_ARG;
   *out = nullptr;
   for (uint32_t i = 0; i < count; ++i) {
@@ -327,10 +333,19 @@ int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeez
     uint64_t n = it.h->f.cells;
     if (it.d_buf0 < it.d_buf1 ? it.d_buf0 + n > it.d_buf1 : it.d_buf1 + n > it.d_buf0)
       return SQUEEZE_ERR_INVALID_ARG;
+    if (d_rec) {   // every item whose program has records needs two aligned buffers
+      uint64_t bytes = 0;
+      int rc = squeeze_record_bytes(it.h, &bytes);
+      if (rc) return rc;
+      for (int k = 0; k < 2; ++k)
+        if (bytes && (!d_rec[2 * i + k] || ((uintptr_t)d_rec[2 * i + k] & 3u)))
+          return SQUEEZE_ERR_INVALID_ARG;
+    }
   }
   squeeze_batch *b = new (std::nothrow) squeeze_batch();
   if (!b) return SQUEEZE_ERR_OOM;
   b->items.assign(items, items + count);
+  if (d_rec) b->caller_rec.assign(d_rec, d_rec + 2 * (size_t)count);
   b->threads = 0;
   b->ctas_per_sm = 0;
   b->use_graph = true;
@@ -342,8 +357,23 @@ int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeez
     delete b;
     return rc;
   }
+  b->rec_valid = d_rec != nullptr;   // the caller wrote the records of the states in d_buf0
   *out = b;
   return SQUEEZE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int squeeze_batch_create(const squeeze_batch_item *items, uint32_t count, squeeze_batch **out) {
+  return create_batch(items, count, nullptr, out);
+}
+
+int squeeze_batch_create_with_records(const squeeze_batch_item *items, uint32_t count,
+                                      uint32_t *const *d_rec, squeeze_batch **out) {
+  if (!d_rec) return SQUEEZE_ERR_INVALID_ARG;
+  return create_batch(items, count, d_rec, out);
 }
 
 int squeeze_batch_configure(squeeze_batch *b, uint32_t threads, uint32_t ctas_per_sm,

@@ -376,6 +376,35 @@ int squeeze_last_step_info(const squeeze_handle *h, int *kind, uint64_t *launche
   return SQUEEZE_OK;
 }
 
+int squeeze_record_bytes(squeeze_handle *h, uint64_t *bytes) {
+  if (check_handle(h) || !bytes) return SQUEEZE_ERR_INVALID_ARG;
+  *bytes = 0;
+  int rc = sq_tiled_prepare(h);
+  if (rc) return rc;
+  sq::TiledDev d;
+  sq::TileSpec sp;
+  rc = sq_tiled_describe(h, &d, &sp);
+  if (rc) return rc;
+  *bytes = (uint64_t)sp.rec_words * sp.tiles_x * sp.tiles_y * 4;
+  return SQUEEZE_OK;
+}
+
+int squeeze_write_records(squeeze_handle *h, const uint8_t *d_state, uint32_t *d_rec,
+                          void *stream) {
+  if (check_handle(h) || !d_state || !d_rec) return SQUEEZE_ERR_INVALID_ARG;
+  if (((uintptr_t)d_state & 15u) || ((uintptr_t)d_rec & 3u)) return SQUEEZE_ERR_INVALID_ARG;
+  int rc = sq_tiled_prepare(h);
+  if (rc) return rc;
+  sq::TiledDev d;
+  sq::TileSpec sp;
+  rc = sq_tiled_describe(h, &d, &sp);
+  if (rc || !sp.rec_words) return rc;
+  d.rec[0] = nullptr;
+  d.rec[1] = d_rec;   // the records-only launch writes the input's records here
+  d.mode = 1;
+  return sq_tile_launch(d, sp, d_state, const_cast<uint8_t *>(d_state), 1, (cudaStream_t)stream);
+}
+
 int squeeze_set_max_steps_per_launch(squeeze_handle *h, uint32_t steps) {
   if (check_handle(h) || (steps != 0 && steps != 1 && steps != 2 && steps != 4 && steps != 8))
     return SQUEEZE_ERR_INVALID_ARG;

@@ -50,6 +50,7 @@ class DeviceBackend:
         from . import inputs as I
         self.torch, self.sq, self.I = torch, sq, I
         self.device = torch.device(device)
+        self._rec_bytes = {}   # handle pointer -> bytes of one border-record buffer
 
     def free_bytes(self) -> int:
         # Blocks that torch's caching allocator holds but no tensor uses are
@@ -75,10 +76,23 @@ class DeviceBackend:
         a = self.torch.empty(handle.cells, dtype=self.torch.uint8, device=self.device)
         b = self.torch.empty_like(a)
         self.sq.squeeze_init_bernoulli(handle.h, a, inst.seed, self.I.p_q24(inst.p))
+        # Each state buffer carries the border records of its contents, written
+        # once here for the start and kept current by every batched run, so a
+        # rebuilt batch needs no records-only launch.
+        n = self._rec_bytes.get(handle.h)
+        if n is None:
+            n = self._rec_bytes[handle.h] = self.sq.squeeze_record_bytes(handle.h)
+        a._sq_rec = b._sq_rec = None
+        if n:
+            a._sq_rec = self.torch.empty(n // 4, dtype=self.torch.int32, device=self.device)
+            b._sq_rec = self.torch.empty_like(a._sq_rec)
+            self.sq.squeeze_write_records(handle.h, a, a._sq_rec)
         return a, b
 
     def batch(self, slots):
-        batch = self.sq.squeeze_batch_create([(s.handle.h, s.cur, s.other) for s in slots])
+        batch = self.sq.squeeze_batch_create_with_records(
+            [(s.handle.h, s.cur, s.other) for s in slots],
+            [(s.cur._sq_rec, s.other._sq_rec) for s in slots])
         self.sq.squeeze_batch_configure(batch, 0, 0, False)  # round lengths vary: no graphs
         return batch
 
@@ -90,6 +104,7 @@ class DeviceBackend:
         self.sq.squeeze_batch_destroy(batch)
 
     def close_handle(self, handle):
+        self._rec_bytes.pop(handle.h, None)
         handle.close()
 
 

@@ -6,6 +6,7 @@
 
 int sq_cuda_fail(cudaError_t) { return SQUEEZE_ERR_CUDA; }
 cudaError_t sq_allow_smem(const void *, size_t) { return cudaSuccess; }
+extern "C" int squeeze_record_bytes(squeeze_handle *, uint64_t *) { return SQUEEZE_ERR_UNSUPPORTED; }
 int sq_tiled_prepare(squeeze_handle *) { return SQUEEZE_ERR_UNSUPPORTED; }
 int sq_tiled_describe(const squeeze_handle *, sq::TiledDev *, sq::TileSpec *) {
   return SQUEEZE_ERR_UNSUPPORTED;

@@ -217,3 +217,46 @@ def solo_from(h, state, steps):
     sq.squeeze_step(h.h, a, b, steps, sq.SQUEEZE_STEP_TILED)
     torch.cuda.synchronize()
     return (b if steps % 2 else a).clone()
+
+
+def test_batch_with_caller_records_matches_solo_runs():
+    """Items whose border records the caller keeps (written once by
+    squeeze_write_records, then kept current by the runs) give the same
+    results as solo runs, across runs and a rebuilt batch."""
+    shapes = [(I.CARPET, 6), (I.TRIANGLE, 9), (I.VICSEK, 7), (I.SINGLE, 3)]
+    handles = [sq.Handle(f, r) for f, r in shapes]
+    try:
+        states, recs, starts = [], [], []
+        for i, h in enumerate(handles):
+            a = torch.empty(h.cells, dtype=torch.uint8, device="cuda")
+            b = torch.empty_like(a)
+            sq.squeeze_init_bernoulli(h.h, a, 500 + i, I.p_q24(0.5))
+            n = sq.squeeze_record_bytes(h.h)
+            assert n % 4 == 0 and (n > 0) == (shapes[i][0] is not I.SINGLE)
+            ra = torch.empty(max(n, 4) // 4, dtype=torch.int32, device="cuda") if n else None
+            rb = torch.empty_like(ra) if n else None
+            if n:
+                sq.squeeze_write_records(h.h, a, ra)
+            states.append([a, b])
+            recs.append([ra, rb])
+            starts.append(a.clone())
+        done = 0
+        for run in (5, 8, 3):   # a new batch each time, buffers swapped after odd runs
+            batch = sq.squeeze_batch_create_with_records(
+                [(h.h, s[0], s[1]) for h, s in zip(handles, states)], [tuple(r) for r in recs])
+            sq.squeeze_batch_run(batch, run)
+            torch.cuda.synchronize()
+            sq.squeeze_batch_destroy(batch)
+            done += run
+            if run % 2:
+                for s, r in zip(states, recs):
+                    s.reverse()
+                    r.reverse()
+            for h, s, s0, (f, rr) in zip(handles, states, starts, shapes):
+                assert torch.equal(s[0], solo_from(h, s0, done)), (f.name, done)
+        with pytest.raises(sq.SqueezeError):   # a program with records needs its buffers
+            sq.squeeze_batch_create_with_records([(handles[0].h, states[0][0], states[0][1])],
+                                                 [(None, None)])
+    finally:
+        for h in handles:
+            h.close()
