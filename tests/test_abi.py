@@ -59,7 +59,11 @@ def test_null_handle_is_rejected():
     assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
     for call in (lambda: sq.squeeze_set_wait_limit(None, 0),
                  lambda: sq.squeeze_set_fault_injection(None, 0),
-                 lambda: sq.squeeze_last_step_info(None)):
+                 lambda: sq.squeeze_last_step_info(None),
+                 lambda: sq.squeeze_record_bytes(None),
+                 lambda: sq.squeeze_write_records(None, 16, 16, 0),
+                 lambda: sq.squeeze_batch_states_written(None),
+                 lambda: sq.squeeze_batch_create_with_records([], [])):
         with pytest.raises(sq.SqueezeError) as e:
             call()
         assert e.value.code == sq.SQUEEZE_ERR_INVALID_ARG
